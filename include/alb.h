@@ -1,0 +1,253 @@
+/*
+ * alb.h -- C ABI of libalb.so, the GB300 (sm_103a) augmentation hot path of
+ * Buslaev et al., "Albumentations: fast and flexible image augmentations"
+ * (arXiv 1809.06839).
+ *
+ * The paper's method: a transform with sampled parameters is applied to an
+ * image and, "in the same way", to its targets -- segmentation masks and
+ * bounding boxes (Sec. II, Sec. II-A, Sec. II-B); Table I (Sec. III) lists
+ * the benchmarked transforms.  The paper defines none of the operations
+ * mathematically; the definitions this library implements (coordinate
+ * conventions, border mode, rounding, sampling) are written out with each
+ * entry point below and in the project's design notes.
+ *
+ * Conventions for every call
+ *  - Images are uint8, HWC, channels interleaved, rows `row_stride` bytes
+ *    apart (row_stride >= w*c).  Image data pointers are DEVICE pointers,
+ *    owned by the caller.  RGB images have c == 3; masks have c >= 1.
+ *  - Boxes are float32 [n][4] (x1, y1, x2, y2) in pixel-edge coordinates:
+ *    the image covers [0, w] x [0, h].
+ *  - Unless stated otherwise the library allocates nothing.  Scratch memory
+ *    comes from a caller-provided device `workspace` of at least the size
+ *    the matching *_workspace_size call returns.
+ *  - Launches are asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ *    default stream).  Every call returns an alb_status; on failure nothing
+ *    was launched and alb_last_error() (thread-local) holds a message.
+ *    Errors found by kernels (a parameter record that does not fit its
+ *    image, a box buffer that is too small) are written to the optional
+ *    device word `dev_status` (first error wins; the caller zeroes it).
+ *  - No call falls back to the CPU.
+ */
+#ifndef ALB_H
+#define ALB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define ALB_API __attribute__((visibility("default")))
+#else
+#define ALB_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+typedef enum alb_status {
+  ALB_OK = 0,
+  ALB_EINVAL = 1,     /* bad argument (null pointer, unknown id, c != 3 for RGB ops) */
+  ALB_ESHAPE = 2,     /* sizes inconsistent with the parameters (e.g. crop > image) */
+  ALB_EALIGN = 3,     /* misaligned pointer or stride */
+  ALB_ECAPACITY = 4,  /* box buffer or batch capacity exceeded */
+  ALB_ECUDA = 5,      /* a CUDA runtime call failed */
+  ALB_ETIMEOUT = 6,   /* a bounded device wait gave up */
+  ALB_EWORKSPACE = 7  /* workspace missing or smaller than required */
+} alb_status;
+
+/* ---- transform ids (Table I of the paper plus the transforms of Sec. II) ---- */
+typedef enum alb_tid {
+  ALB_HFLIP = 1,                 /* Table I "HorizontalFlip" */
+  ALB_VFLIP = 2,                 /* Table I "VerticalFlip" */
+  ALB_RANDOM_CROP = 3,           /* Table I "RandomCrop64" */
+  ALB_PAD_TO_SIZE = 4,           /* Table I "PadToSize512" */
+  ALB_BRIGHTNESS = 5,            /* Table I "Brightness" */
+  ALB_CONTRAST = 6,              /* Sec. II, Fig. 1 "contrast" */
+  ALB_BRIGHTNESS_CONTRAST = 7,   /* brightness and contrast as one table */
+  ALB_GAMMA = 8,                 /* Table I "Gamma" */
+  ALB_SHIFT_RGB = 9,             /* Table I "ShiftRGB" */
+  ALB_SHIFT_HSV = 10,            /* Table I "ShiftHSV" */
+  ALB_GRAYSCALE = 11,            /* Table I "Grayscale" */
+  ALB_EQUALIZE = 12,             /* per-channel histogram equalisation */
+  ALB_ROTATE = 13,               /* Table I "Rotate" */
+  ALB_SHIFT_SCALE_ROTATE = 14,   /* Table I "ShiftScaleRotate" */
+  ALB_RESIZE = 15,               /* Sec. II-B "scaling" */
+  ALB_RANDOM_SIZED_CROP = 16,    /* Sec. II-A, Fig. 2 "random sized crop" */
+  ALB_RANDOM_RESIZED_CROP = 17,  /* crop of sampled area and aspect, resized */
+  ALB_TRANSPOSE = 18,            /* Sec. II-B, Dih4 element */
+  ALB_ROT90 = 19,                /* Sec. II-B, Dih4 rotations */
+  ALB_CHAIN = 20                 /* the fused ragged-batch chain (alb_apply_batch) */
+} alb_tid;
+
+/* One image (or mask) in device memory.  32 bytes. */
+typedef struct alb_image {
+  void* data;           /* device pointer to byte (0,0,0); caller-owned */
+  int32_t h, w, c;      /* rows, columns, interleaved channels */
+  int32_t reserved;     /* must be 0 */
+  int64_t row_stride;   /* bytes from one row to the next, >= w*c */
+} alb_image;
+
+/* The sampled parameters of one transform for one image (Sec. II: "the
+ * parameters of transformation").  Produced by alb_sample_params[_batch];
+ * callers may also fill it themselves.  Fields unused by a transform are 0
+ * (scale, alpha, gamma and sat default to 1).  232 bytes. */
+typedef struct alb_params {
+  int32_t tid;           /* alb_tid */
+  int32_t apply;         /* 1 = applied, 0 = identity (the probability draw failed) */
+  int32_t in_h, in_w;    /* input size the record was sampled for */
+  int32_t out_h, out_w;  /* output size */
+  int32_t y0, x0;        /* crop window origin; PadToSize: top/left padding */
+  int32_t ch, cw;        /* crop window size (RandomCrop, Resize, RSC, RRC, chain) */
+  int32_t flip;          /* chain: 1 = horizontal flip */
+  int32_t k;             /* ROT90: quarter turns counter-clockwise */
+  double alpha;          /* contrast gain; chain: contrast factor */
+  double beta;           /* brightness shift (pixel units); chain: brightness factor */
+  double gamma;          /* gamma exponent */
+  double sat;            /* chain: saturation factor */
+  double shift[3];       /* ShiftRGB per channel; ShiftHSV (hue half-degrees, sat, val /255) */
+  double angle;          /* warp angle, degrees, counter-clockwise on screen */
+  double scale;          /* warp scale */
+  double dx, dy;         /* warp shift, fractions of w and h */
+  double m[6];           /* forward map src -> dst, pixel-centre coordinates, row-major 2x3 */
+  int64_t q[6];          /* inverse map dst -> src, Q16 fixed point (round half even) */
+} alb_params;
+
+/* Sampling configuration of one transform.  Meaning of the ranges:
+ *  BRIGHTNESS lo/hi[0] = beta;  CONTRAST [0] = alpha;  BRIGHTNESS_CONTRAST
+ *  [0] = alpha, [1] = beta;  GAMMA [0] = gamma;  SHIFT_RGB [0..2] per channel;
+ *  SHIFT_HSV [0] hue, [1] sat, [2] val;  ROTATE [0] angle;
+ *  SHIFT_SCALE_ROTATE [0] shift (each axis), [1] scale, [2] angle;
+ *  RANDOM_SIZED_CROP [0] side as a fraction of min(h, w);
+ *  RANDOM_RESIZED_CROP / CHAIN [0] area fraction, [1] aspect w/h,
+ *  CHAIN [2] brightness, contrast and saturation factors.
+ *  out_h/out_w: crop / pad / resize target size. */
+typedef struct alb_sample_cfg {
+  int32_t tid, out_h, out_w, reserved;
+  double p;              /* probability the transform is applied */
+  double lo[4], hi[4];
+} alb_sample_cfg;
+
+/* Configuration of the fused chain (alb_apply_batch). */
+typedef struct alb_chain_cfg {
+  int32_t out_h, out_w;  /* output size (224 x 224 for the ImageNet-style chain) */
+  double mean[3];        /* Normalize mean per channel (fraction of 255) */
+  double std[3];         /* Normalize std per channel (fraction of 255) */
+  int32_t tile_h, tile_w;/* fused-kernel output tile (tile_w a multiple of 8); 0 = autotuned */
+  int32_t ctas_per_sm;   /* fused-kernel residency; 0 = autotuned */
+  int32_t reserved;
+} alb_chain_cfg;        /* 72 bytes */
+
+enum { ALB_MODE_FUSED = 0, ALB_MODE_PLAIN = 1 };
+
+/* ------------------------------------------------------------------ */
+/* Parameter sampling (Sec. II: transforms applied "with sampled
+ * parameters").  Philox4x32-10 (Salmon et al., SC'11): the word stream of
+ * image `index` is Philox blocks with counter (j, index, stream_id lo,
+ * stream_id hi) and key seed; uniform doubles take 27+26 bits of two words;
+ * integers use Lemire's multiply-shift with rejection.  The probability draw
+ * comes first; size-changing transforms are always applied.  Host only;
+ * `out` is a host pointer.  Returns ALB_ESHAPE when the transform cannot fit
+ * (crop larger than the image). */
+ALB_API alb_status alb_sample_params(const alb_sample_cfg* cfg, uint64_t seed, uint64_t stream_id,
+                             uint32_t index, int32_t h, int32_t w, alb_params* out);
+
+/* The same sampler as a device kernel for n images: image i uses index
+ * first_index + i and the size in images_dev[i].  images_dev and params_dev
+ * are device arrays of n entries.  A record that cannot fit writes
+ * ALB_ESHAPE to dev_status (if non-NULL) and an identity record. */
+ALB_API alb_status alb_sample_params_batch(const alb_sample_cfg* cfg, uint64_t seed, uint64_t stream_id,
+                                   uint32_t first_index, int32_t n, const alb_image* images_dev,
+                                   alb_params* params_dev, int32_t* dev_status, void* stream);
+
+/* Output size of a transform with parameters p applied to an h x w input. */
+ALB_API alb_status alb_output_shape(const alb_params* p, int32_t h, int32_t w, int32_t* out_h, int32_t* out_w);
+
+/* Scratch bytes alb_apply / alb_apply_ragged need for n images of transform tid. */
+ALB_API size_t alb_workspace_size(int32_t tid, int32_t n);
+
+/* ------------------------------------------------------------------ */
+/* Apply one transform to one image and, optionally, its mask and boxes
+ * (Sec. II-A: masks and boxes are transformed together with the image;
+ * Sec. II-B: masks "in the same way as the original image").
+ *  params:  HOST pointer to one record.
+ *  in/out:  HOST structs describing DEVICE images; out must have the size
+ *           alb_output_shape gives and the same c.  NULL out skips the image.
+ *           In-place (out->data == in->data) is allowed only for transforms
+ *           that keep the size and move no pixels (LUT ops, ShiftHSV,
+ *           Grayscale, Equalize).
+ *  mask_in/mask_out: optional (NULL) mask of any c, same h x w as the image;
+ *           geometric transforms resample it with nearest-neighbour, the
+ *           others copy it unchanged.
+ *  boxes_in: DEVICE float [n_boxes][4]; boxes_out: DEVICE float [n_boxes][4];
+ *           n_boxes_out: DEVICE int32, the number of boxes kept (boxes left
+ *           with no area after clipping are dropped, order kept).
+ *  workspace: DEVICE scratch of alb_workspace_size(params->tid, 1) bytes. */
+ALB_API alb_status alb_apply(const alb_params* params, const alb_image* in, const alb_image* out,
+                     const alb_image* mask_in, const alb_image* mask_out,
+                     const float* boxes_in, int32_t n_boxes, float* boxes_out, int32_t* n_boxes_out,
+                     void* workspace, size_t workspace_bytes, void* stream);
+
+/* Apply transform tid to a ragged batch of n images in one pass (the plain,
+ * one-transform-per-launch GPU path).  All arrays are DEVICE arrays of n
+ * entries: params_dev[i].tid must equal tid; out_dev[i] must have the
+ * output size of params_dev[i].  Masks (optional, NULL) as in alb_apply.
+ * Boxes (optional, NULL): boxes_dev is float [n][box_cap][4] with
+ * n_boxes_dev[i] valid entries; results go to boxes_out_dev (same layout)
+ * and n_boxes_out_dev. */
+ALB_API alb_status alb_apply_ragged(int32_t tid, int32_t n, const alb_params* params_dev,
+                            const alb_image* in_dev, const alb_image* out_dev,
+                            const alb_image* mask_in_dev, const alb_image* mask_out_dev,
+                            const float* boxes_dev, const int32_t* n_boxes_dev, int32_t box_cap,
+                            float* boxes_out_dev, int32_t* n_boxes_out_dev,
+                            void* workspace, size_t workspace_bytes, int32_t* dev_status, void* stream);
+
+/* ------------------------------------------------------------------ */
+/* The fused ragged-batch chain: per image, RandomResizedCrop window
+ * resized (Q5 bilinear, half-pixel) to out_h x out_w, h-flip if
+ * params.flip, brightness factor beta then contrast factor alpha about a
+ * fixed pivot 128 as one per-image table, saturation blend in float32 with
+ * factor sat, Normalize with float32 constants 1/(255 std), -mean/std,
+ * bfloat16 round-to-nearest-even, written NCHW to out_bf16
+ * [n][3][out_h][out_w].
+ *  mode ALB_MODE_FUSED: one persistent kernel, each output pixel written
+ *  once.  ALB_MODE_PLAIN: one kernel per step with materialised
+ *  intermediates; bit-identical output.
+ *  params_dev / in_dev: DEVICE arrays of n entries (params tid = ALB_CHAIN). */
+ALB_API size_t alb_batch_workspace_size(const alb_chain_cfg* cfg, int32_t n, int32_t mode);
+ALB_API alb_status alb_apply_batch(const alb_chain_cfg* cfg, int32_t n, const alb_params* params_dev,
+                           const alb_image* in_dev, void* out_bf16, int32_t mode,
+                           void* workspace, size_t workspace_bytes, int32_t* dev_status, void* stream);
+
+/* ------------------------------------------------------------------ */
+/* Differentiable float32 path.  x: DEVICE float [B][C][H][W] (NCHW, values
+ * nominally in [0,1]); prm: DEVICE float [B][4] = (angle in degrees, scale,
+ * tx, ty) for the warp, [B][3] = (alpha, beta, gamma) for the photometric op.
+ * Warp: the C6 map of the u8 warps in float32 with bilinear sampling and a
+ * zero border.  Photometric: y = clamp(alpha x + beta, 0, 1)^gamma.
+ * Backward kernels recompute sampling coordinates from prm (nothing is
+ * stored by the forward), write the input gradient gx (same layout as x)
+ * and ACCUMULATE nothing: gprm [B][4] / [B][3] is overwritten. */
+ALB_API size_t alb_f32_workspace_size(int32_t B, int32_t C, int32_t H, int32_t W);
+ALB_API alb_status alb_warp_affine_f32_fwd(int32_t B, int32_t C, int32_t H, int32_t W, const float* x,
+                                   const float* prm, float* y, void* stream);
+ALB_API alb_status alb_warp_affine_f32_bwd(int32_t B, int32_t C, int32_t H, int32_t W, const float* x,
+                                   const float* prm, const float* gy, float* gx, float* gprm,
+                                   void* workspace, size_t workspace_bytes, void* stream);
+ALB_API alb_status alb_photometric_f32_fwd(int32_t B, int32_t C, int32_t H, int32_t W, const float* x,
+                                   const float* prm, float* y, void* stream);
+ALB_API alb_status alb_photometric_f32_bwd(int32_t B, int32_t C, int32_t H, int32_t W, const float* x,
+                                   const float* prm, const float* gy, float* gx, float* gprm,
+                                   void* workspace, size_t workspace_bytes, void* stream);
+
+/* ------------------------------------------------------------------ */
+/* Thread-local message for the last failing call on this thread. */
+ALB_API const char* alb_last_error(void);
+/* Library version, e.g. "alb 1.0 sm_103a". */
+ALB_API const char* alb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ALB_H */

@@ -1,0 +1,118 @@
+// alb_common.cuh -- internal helpers shared by the libalb kernels (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "alb.h"
+
+static_assert(sizeof(alb_image) == 32, "alb_image layout");
+static_assert(sizeof(alb_params) == 232, "alb_params layout");
+static_assert(sizeof(alb_sample_cfg) == 88, "alb_sample_cfg layout");
+static_assert(sizeof(alb_chain_cfg) == 72, "alb_chain_cfg layout");
+
+#define ALB_HD __host__ __device__ __forceinline__
+#define ALB_D __device__ __forceinline__
+
+namespace alb {
+
+// ------------------------------------------------------------------ errors
+void set_error(const char* fmt, ...);
+alb_status cuda_status(cudaError_t e, const char* what);
+#define ALB_CUDA(call)                                              \
+  do {                                                              \
+    cudaError_t e_ = (call);                                        \
+    if (e_ != cudaSuccess) return ::alb::cuda_status(e_, #call);    \
+  } while (0)
+#define ALB_REQUIRE(cond, code, ...)                                \
+  do {                                                              \
+    if (!(cond)) { ::alb::set_error(__VA_ARGS__); return (code); }  \
+  } while (0)
+
+int sm_count();     // SMs of the current device (cached per device)
+
+// record the first device-side error in the caller's status word
+ALB_D void dev_fail(int32_t* status, int code) {
+  if (status) atomicCAS(status, 0, code);
+}
+
+// ------------------------------------------------------------------ integer helpers
+ALB_HD int64_t floor_div(int64_t a, int64_t b) {  // b > 0
+  int64_t q = a / b, r = a % b;
+  return (r < 0) ? q - 1 : q;
+}
+
+// reflect-101 border (edge sample not repeated), any integer i, n >= 1
+ALB_HD int32_t reflect101(int64_t i, int32_t n) {
+  if (n == 1) return 0;
+  if (i >= 0 && i < n) return (int32_t)i;
+  int64_t period = 2 * (int64_t)(n - 1);
+  int64_t m = i % period;
+  if (m < 0) m += period;
+  if (m >= n) m = period - m;
+  return (int32_t)m;
+}
+
+ALB_HD int32_t imin(int32_t a, int32_t b) { return a < b ? a : b; }
+ALB_HD int32_t imax(int32_t a, int32_t b) { return a > b ? a : b; }
+
+// ------------------------------------------------------------------ batch views
+// A ragged batch: either device arrays (ptr != nullptr) or one inline entry
+// passed by value (single-image alb_apply), so that no host->device copy is
+// needed for the single-image call.
+struct ImgList {
+  const alb_image* dev;
+  alb_image one;
+  ALB_D alb_image get(int i) const { return dev ? dev[i] : one; }
+};
+struct PrmList {
+  const alb_params* dev;
+  alb_params one;
+  ALB_D const alb_params& get(int i) const { return dev ? dev[i] : one; }
+};
+
+// Work plan of a ragged launch: image b owns items [prefix[b], prefix[b+1]);
+// each item covers rows_per_item[b] output rows.
+struct Plan {
+  const int32_t* prefix;        // n + 1
+  const int32_t* rows_per_item; // n
+  int32_t n;
+};
+
+// Blocked distribution of the plan's items over the grid: CTA j takes a
+// contiguous range, so consecutive items mostly belong to the same image.
+ALB_D void item_range(const Plan& p, int32_t& begin, int32_t& end) {
+  int64_t total = p.prefix[p.n];
+  begin = (int32_t)(total * blockIdx.x / gridDim.x);
+  end = (int32_t)(total * (blockIdx.x + 1) / gridDim.x);
+}
+
+// image owning `item` (largest b with prefix[b] <= item)
+ALB_D int32_t item_image(const Plan& p, int32_t item) {
+  int32_t lo = 0, hi = p.n - 1;
+  while (lo < hi) {
+    int32_t mid = (lo + hi + 1) >> 1;
+    if (p.prefix[mid] <= item) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// ------------------------------------------------------------------ workspace carving
+struct Carve {
+  char* base;
+  size_t used, cap;
+  template <class T>
+  T* take(size_t count) {
+    size_t off = (used + 255) & ~size_t(255);
+    used = off + count * sizeof(T);
+    return (used <= cap && base) ? reinterpret_cast<T*>(base + off) : nullptr;
+  }
+};
+
+constexpr size_t plan_bytes(int32_t n) { return 256 + ((size_t)(n + 1) * 4 + 255) / 256 * 256 + ((size_t)n * 4 + 255) / 256 * 256 + 256; }
+
+// host launcher for the plan kernel (alb_geom.cu)
+alb_status launch_plan(const ImgList& out, int32_t n, int32_t target_bytes, int32_t* prefix,
+                       int32_t* rows_per_item, cudaStream_t st);
+
+}  // namespace alb

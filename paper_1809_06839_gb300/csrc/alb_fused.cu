@@ -1,0 +1,273 @@
+// alb_fused.cu -- the ragged-batch chain: RandomResizedCrop -> Q5 bilinear resize
+// to out_h x out_w -> h-flip -> brightness/contrast table -> saturation (float32)
+// -> Normalize -> bfloat16 NCHW.  (The paper's Sec. II-A example combines a flip
+// with a random sized crop; Sec. II-C uses colour transforms; the chain is the
+// ImageNet-style training pipeline built from them.)
+//
+// ALB_MODE_FUSED: one persistent kernel; CTAs pull (image, band of output rows)
+// items from an atomic queue, every output value is computed from the source
+// crop in registers and written once.
+// ALB_MODE_PLAIN: five kernels with materialised intermediates (u8 resize, u8
+// flip, u8 table, f32 saturation, bf16 normalise), the comparison path.
+// Both modes call the same __device__ step functions, so outputs are identical.
+#include <cuda_bf16.h>
+
+#include "alb_common.cuh"
+#include "alb_kernels.cuh"
+
+namespace alb {
+
+struct ChainK {
+  float k[3], m[3];  // Normalize: y = fma(x, k_c, m_c)
+  int32_t oh, ow;
+};
+
+ALB_D uint8_t sat_rne_d(double v) {
+  double r = rint(v);
+  r = r < 0.0 ? 0.0 : (r > 255.0 ? 255.0 : r);
+  return (uint8_t)r;
+}
+
+// ---------------------------------------------------------------- step functions
+ALB_D int32_t chain_q5(int32_t d, int32_t n_in, int32_t n_out) {
+  int64_t num = 32 * ((int64_t)(2 * d + 1) * n_in - n_out) + n_out;
+  int64_t xq = floor_div(num, 2 * (int64_t)n_out);
+  if (xq < 0) xq = 0;
+  if ((xq >> 5) >= n_in - 1) xq = 32 * (int64_t)(n_in - 1);
+  return (int32_t)xq;
+}
+
+// Q5 bilinear sample (3 channels) of the crop window at Q5 coordinates (xq, yq).
+ALB_D void chain_bilinear(const uint8_t* __restrict__ win, int64_t stride, int32_t ch, int32_t cw, int32_t xq,
+                          int32_t yq, uint32_t rgb[3]) {
+  const int32_t ix = xq >> 5, fx = xq & 31, iy = yq >> 5, fy = yq & 31;
+  const int32_t ixb = imin(ix + 1, cw - 1), iyb = imin(iy + 1, ch - 1);
+  const uint8_t* ra = win + (int64_t)iy * stride;
+  const uint8_t* rb = win + (int64_t)iyb * stride;
+  const int32_t w00 = (32 - fx) * (32 - fy), w01 = fx * (32 - fy), w10 = (32 - fx) * fy, w11 = fx * fy;
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    const int32_t acc = w00 * __ldg(ra + 3 * ix + c) + w01 * __ldg(ra + 3 * ixb + c) +
+                        w10 * __ldg(rb + 3 * ix + c) + w11 * __ldg(rb + 3 * ixb + c);
+    rgb[c] = (uint32_t)((acc + 512) >> 10);
+  }
+}
+
+// saturation blend with the BT.601 grey value, float32, clamped, not rounded
+ALB_D void chain_saturate(const uint32_t rgb[3], float s, float out[3]) {
+  const float r = (float)rgb[0], g = (float)rgb[1], b = (float)rgb[2];
+  const float grey = __fmaf_rn(0.114f, b, __fmaf_rn(0.587f, g, __fmul_rn(0.299f, r)));
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    float v = __fmaf_rn(s, __fsub_rn((float)rgb[c], grey), grey);
+    out[c] = fminf(fmaxf(v, 0.0f), 255.0f);
+  }
+}
+
+ALB_D __nv_bfloat16 chain_normalize(float v, float k, float m) { return __float2bfloat16_rn(__fmaf_rn(v, k, m)); }
+
+// per-image brightness-then-contrast table c (b v - 128) + 128 (float64, half even)
+__global__ void k_chain_luts(int32_t n, const alb_params* __restrict__ prm, uint8_t* __restrict__ luts) {
+  const int b = blockIdx.x, v = threadIdx.x;
+  if (b >= n) return;
+  const alb_params& p = prm[b];
+  const double bv = p.beta * (double)v;
+  const double d = bv - 128.0;
+  const double cd = p.alpha * d;
+  luts[(int64_t)b * 256 + v] = sat_rne_d(cd + 128.0);
+}
+
+// ---------------------------------------------------------------- fused kernel
+// Item = (image, band of `band` output rows).  Queue: one global counter.
+__global__ void __launch_bounds__(256) k_chain_fused(int32_t n, const alb_params* __restrict__ prm,
+                                                     const alb_image* __restrict__ imgs,
+                                                     const uint8_t* __restrict__ luts, ChainK K, int32_t band,
+                                                     int32_t* __restrict__ queue, __nv_bfloat16* __restrict__ out) {
+  __shared__ int32_t s_item;
+  __shared__ uint8_t s_lut[256];
+  __shared__ int32_t s_col[1024];
+  __shared__ int32_t s_b;
+  const int32_t bands = (K.oh + band - 1) / band;
+  const int64_t total = (int64_t)n * bands;
+  const int64_t plane = (int64_t)K.oh * K.ow;
+  int32_t cached = -1;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(queue, 1);
+    __syncthreads();
+    const int32_t item = s_item;
+    if (item >= total) break;
+    const int32_t b = item / bands, r0 = (item - b * bands) * band, r1 = imin(r0 + band, K.oh);
+    const alb_params& p = prm[b];
+    if (b != cached) {
+      for (int i = threadIdx.x; i < 256; i += blockDim.x) s_lut[i] = luts[(int64_t)b * 256 + i];
+      for (int x = threadIdx.x; x < K.ow; x += blockDim.x) {
+        const int32_t xr = p.flip ? K.ow - 1 - x : x;  // output column x shows resized column xr
+        s_col[x] = chain_q5(xr, p.cw, K.ow);
+      }
+      if (threadIdx.x == 0) s_b = b;
+      cached = b;
+    }
+    __syncthreads();
+    const alb_image im = imgs[b];
+    const uint8_t* win = (const uint8_t*)im.data + (int64_t)p.y0 * im.row_stride + 3 * (int64_t)p.x0;
+    const float s = (float)p.sat;
+    __nv_bfloat16* ob = out + (int64_t)b * 3 * plane;
+    const int32_t npx = (r1 - r0) * K.ow;
+    for (int32_t i = threadIdx.x; i < npx; i += blockDim.x) {
+      const int32_t y = r0 + i / K.ow, x = i - (i / K.ow) * K.ow;
+      const int32_t yq = chain_q5(y, p.ch, K.oh);
+      uint32_t rgb[3];
+      chain_bilinear(win, im.row_stride, p.ch, p.cw, s_col[x], yq, rgb);
+#pragma unroll
+      for (int c = 0; c < 3; c++) rgb[c] = s_lut[rgb[c]];
+      float v[3];
+      chain_saturate(rgb, s, v);
+#pragma unroll
+      for (int c = 0; c < 3; c++) ob[c * plane + (int64_t)y * K.ow + x] = chain_normalize(v[c], K.k[c], K.m[c]);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- plain path
+__global__ void k_plain_resize(int32_t n, const alb_params* __restrict__ prm, const alb_image* __restrict__ imgs,
+                               ChainK K, uint8_t* __restrict__ out) {
+  const int64_t total = (int64_t)n * K.oh * K.ow;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t b = (int32_t)(i / ((int64_t)K.oh * K.ow));
+    const int32_t r = (int32_t)(i - (int64_t)b * K.oh * K.ow);
+    const int32_t y = r / K.ow, x = r - y * K.ow;
+    const alb_params& p = prm[b];
+    const alb_image im = imgs[b];
+    const uint8_t* win = (const uint8_t*)im.data + (int64_t)p.y0 * im.row_stride + 3 * (int64_t)p.x0;
+    uint32_t rgb[3];
+    chain_bilinear(win, im.row_stride, p.ch, p.cw, chain_q5(x, p.cw, K.ow), chain_q5(y, p.ch, K.oh), rgb);
+    for (int c = 0; c < 3; c++) out[3 * i + c] = (uint8_t)rgb[c];
+  }
+}
+
+__global__ void k_plain_flip(int32_t n, const alb_params* __restrict__ prm, ChainK K, const uint8_t* __restrict__ in,
+                             uint8_t* __restrict__ out) {
+  const int64_t total = (int64_t)n * K.oh * K.ow;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t b = (int32_t)(i / ((int64_t)K.oh * K.ow));
+    const int32_t x = (int32_t)(i % K.ow);
+    const int64_t src = prm[b].flip ? i - x + (K.ow - 1 - x) : i;
+    for (int c = 0; c < 3; c++) out[3 * i + c] = in[3 * src + c];
+  }
+}
+
+__global__ void k_plain_lut(int32_t n, ChainK K, const uint8_t* __restrict__ luts, const uint8_t* __restrict__ in,
+                            uint8_t* __restrict__ out) {
+  const int64_t total = (int64_t)n * K.oh * K.ow * 3;
+  const int64_t per = (int64_t)K.oh * K.ow * 3;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = luts[(i / per) * 256 + in[i]];
+}
+
+__global__ void k_plain_saturate(int32_t n, const alb_params* __restrict__ prm, ChainK K,
+                                 const uint8_t* __restrict__ in, float* __restrict__ out) {
+  const int64_t total = (int64_t)n * K.oh * K.ow;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t b = (int32_t)(i / ((int64_t)K.oh * K.ow));
+    const uint32_t rgb[3] = {in[3 * i], in[3 * i + 1], in[3 * i + 2]};
+    float v[3];
+    chain_saturate(rgb, (float)prm[b].sat, v);
+    for (int c = 0; c < 3; c++) out[3 * i + c] = v[c];
+  }
+}
+
+__global__ void k_plain_normalize(int32_t n, ChainK K, const float* __restrict__ in, __nv_bfloat16* __restrict__ out) {
+  const int64_t plane = (int64_t)K.oh * K.ow;
+  const int64_t total = (int64_t)n * plane;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = i / plane, r = i - b * plane;
+    for (int c = 0; c < 3; c++) out[(b * 3 + c) * plane + r] = chain_normalize(in[3 * i + c], K.k[c], K.m[c]);
+  }
+}
+
+// ---------------------------------------------------------------- launcher
+size_t chain_workspace(const alb_chain_cfg& cfg, int32_t n, int32_t mode) {
+  size_t px = (size_t)n * cfg.out_h * cfg.out_w;
+  size_t b = 4096 + (size_t)n * 256;
+  if (mode == ALB_MODE_PLAIN) b += 2 * px * 3 + px * 3 * 4 + 1024;
+  return b;
+}
+
+static ChainK make_consts(const alb_chain_cfg& cfg) {
+  ChainK K;
+  for (int c = 0; c < 3; c++) {
+    K.k[c] = (float)(1.0 / (255.0 * cfg.std[c]));
+    K.m[c] = (float)(-cfg.mean[c] / cfg.std[c]);
+  }
+  K.oh = cfg.out_h;
+  K.ow = cfg.out_w;
+  return K;
+}
+
+alb_status launch_chain(const alb_chain_cfg& cfg, int32_t n, const alb_params* params, const alb_image* in,
+                        void* out, int32_t mode, Carve& ws, int32_t* status, cudaStream_t st) {
+  const ChainK K = make_consts(cfg);
+  int32_t* queue = ws.take<int32_t>(64);
+  uint8_t* luts = ws.take<uint8_t>((size_t)n * 256);
+  ALB_REQUIRE(queue && luts, ALB_EWORKSPACE, "alb_apply_batch: workspace too small");
+  k_chain_luts<<<n, 256, 0, st>>>(n, params, luts);
+  ALB_CUDA(cudaGetLastError());
+  __nv_bfloat16* o = (__nv_bfloat16*)out;
+  if (mode == ALB_MODE_FUSED) {
+    ALB_REQUIRE(cfg.out_w <= 1024, ALB_ESHAPE, "alb_apply_batch: fused mode supports out_w <= 1024");
+    const int32_t band = cfg.tile_h > 0 ? cfg.tile_h : 4;
+    int per_sm = cfg.ctas_per_sm;
+    if (per_sm <= 0) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chain_fused, 256, 0);
+      if (per_sm < 1) per_sm = 1;
+    }
+    ALB_CUDA(cudaMemsetAsync(queue, 0, sizeof(int32_t), st));
+    k_chain_fused<<<per_sm * sm_count(), 256, 0, st>>>(n, params, in, luts, K, band, queue, o);
+    ALB_CUDA(cudaGetLastError());
+    return ALB_OK;
+  }
+  const size_t px = (size_t)n * cfg.out_h * cfg.out_w;
+  uint8_t* a = ws.take<uint8_t>(px * 3);
+  uint8_t* b = ws.take<uint8_t>(px * 3);
+  float* f = ws.take<float>(px * 3);
+  ALB_REQUIRE(a && b && f, ALB_EWORKSPACE, "alb_apply_batch: workspace too small for plain mode");
+  const int grid = 8 * sm_count();
+  k_plain_resize<<<grid, 256, 0, st>>>(n, params, in, K, a);
+  ALB_CUDA(cudaGetLastError());
+  k_plain_flip<<<grid, 256, 0, st>>>(n, params, K, a, b);
+  ALB_CUDA(cudaGetLastError());
+  k_plain_lut<<<grid, 256, 0, st>>>(n, K, luts, b, a);
+  ALB_CUDA(cudaGetLastError());
+  k_plain_saturate<<<grid, 256, 0, st>>>(n, params, K, a, f);
+  ALB_CUDA(cudaGetLastError());
+  k_plain_normalize<<<grid, 256, 0, st>>>(n, K, f, o);
+  ALB_CUDA(cudaGetLastError());
+  return ALB_OK;
+}
+
+}  // namespace alb
+
+using namespace alb;
+
+extern "C" size_t alb_batch_workspace_size(const alb_chain_cfg* cfg, int32_t n, int32_t mode) {
+  if (!cfg || n <= 0) return 4096;
+  return chain_workspace(*cfg, n, mode);
+}
+
+extern "C" alb_status alb_apply_batch(const alb_chain_cfg* cfg, int32_t n, const alb_params* params_dev,
+                                      const alb_image* in_dev, void* out_bf16, int32_t mode, void* workspace,
+                                      size_t workspace_bytes, int32_t* dev_status, void* stream) {
+  ALB_REQUIRE(cfg, ALB_EINVAL, "alb_apply_batch: null cfg");
+  ALB_REQUIRE(n >= 0, ALB_EINVAL, "alb_apply_batch: negative n");
+  if (n == 0) return ALB_OK;
+  ALB_REQUIRE(params_dev && in_dev && out_bf16, ALB_EINVAL, "alb_apply_batch: null device array");
+  ALB_REQUIRE(mode == ALB_MODE_FUSED || mode == ALB_MODE_PLAIN, ALB_EINVAL, "alb_apply_batch: bad mode %d", mode);
+  ALB_REQUIRE(cfg->out_h > 0 && cfg->out_w > 0, ALB_ESHAPE, "alb_apply_batch: bad output size");
+  for (int c = 0; c < 3; c++) ALB_REQUIRE(cfg->std[c] > 0, ALB_EINVAL, "alb_apply_batch: std must be > 0");
+  ALB_REQUIRE(workspace && workspace_bytes >= chain_workspace(*cfg, n, mode), ALB_EWORKSPACE,
+              "alb_apply_batch: workspace of %zu bytes is smaller than %zu", workspace_bytes,
+              chain_workspace(*cfg, n, mode));
+  Carve cv{(char*)workspace, 0, workspace_bytes};
+  return launch_chain(*cfg, n, params_dev, in_dev, out_bf16, mode, cv, dev_status, (cudaStream_t)stream);
+}

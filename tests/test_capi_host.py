@@ -1,0 +1,105 @@
+"""CPU-side checks of the C ABI (no GPU): the library loads, exports every
+symbol include/alb.h declares, the host sampler and shape logic agree with the
+oracle, and argument errors are reported before any CUDA call."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+import oracle as O
+from helpers import EXTRA_CFGS, cfg_to_lib, same_params, suite_cfgs
+
+from paper_1809_06839_gb300 import alb, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return alb.load()
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "alb.h")).read()
+    return sorted(set(re.findall(r"ALB_API\s+[\w\s\*]+?\b(alb_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for must in ("alb_sample_params", "alb_apply", "alb_apply_batch", "alb_apply_ragged", "alb_sample_params_batch",
+                 "alb_warp_affine_f32_bwd", "alb_photometric_f32_bwd", "alb_last_error"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(L):
+    for name in declared_symbols():
+        assert hasattr(L, name), name
+
+
+def test_version(L):
+    assert alb.alb_version().startswith("alb ")
+
+
+ALL = {**suite_cfgs(), **EXTRA_CFGS}
+
+
+@pytest.mark.parametrize("name", sorted(ALL))
+def test_host_sampler_matches_oracle(L, name):
+    oc = ALL[name]
+    lc = cfg_to_lib(oc, alb)
+    for i in range(60):
+        h, w = 333 + (i * 29) % 168, 333 + (i * 53) % 168
+        op = O.sample_params(oc, 1809, oc.tid, i, h, w)
+        lp = alb.alb_sample_params(lc, 1809, oc.tid, i, h, w)
+        err = same_params(op, lp)
+        assert err is None, (name, i, err)
+
+
+def test_chain_sampler_matches_oracle(L):
+    from helpers import CHAIN_CFG
+    oc = O.make_cfg(O.CHAIN, **CHAIN_CFG)
+    lc = cfg_to_lib(oc, alb)
+    for i in range(200):
+        h, w = 256 + (i * 37) % 769, 256 + (i * 91) % 769
+        err = same_params(O.sample_params(oc, 7, 20, i, h, w), alb.alb_sample_params(lc, 7, 20, i, h, w))
+        assert err is None, (i, err)
+
+
+@pytest.mark.parametrize("name", sorted(ALL))
+def test_output_shape_matches_oracle(L, name):
+    oc = ALL[name]
+    op = O.sample_params(oc, 3, 1, 0, 400, 450)
+    from helpers import to_lib
+    assert alb.alb_output_shape(to_lib(op, alb), 400, 450) == O.output_shape(op, 400, 450)
+
+
+def test_sampler_rejects_crop_larger_than_image(L):
+    with pytest.raises(alb.AlbError) as e:
+        alb.alb_sample_params(alb.sample_cfg(alb.RANDOM_CROP, out_h=64, out_w=64), 1, 1, 0, 32, 100)
+    assert e.value.code == alb.ALB_ESHAPE
+
+
+def test_argument_errors_are_reported_without_cuda(L):
+    assert L.alb_apply(None, None, None, None, None, None, 0, None, None, None, 0, None) == alb.ALB_EINVAL
+    assert "required" in alb.alb_last_error()
+    assert L.alb_apply_ragged(99, 1, None, None, None, None, None, None, None, 0, None, None, None, 0, None,
+                              None) == alb.ALB_EINVAL
+    assert L.alb_apply_ragged(alb.HFLIP, -1, None, None, None, None, None, None, None, 0, None, None, None, 0, None,
+                              None) == alb.ALB_EINVAL
+    assert L.alb_apply_batch(None, 1, None, None, None, 0, None, 0, None, None) == alb.ALB_EINVAL
+    cfg = alb.chain_cfg()
+    assert L.alb_apply_batch(C.byref(cfg), 4, None, None, None, 0, None, 0, None, None) == alb.ALB_EINVAL
+    assert L.alb_warp_affine_f32_fwd(1, 0, 4, 4, None, None, None, None) == alb.ALB_ESHAPE
+    # zero-sized batches are a no-op
+    assert L.alb_apply_ragged(alb.HFLIP, 0, None, None, None, None, None, None, None, 0, None, None, None, 0, None,
+                              None) == alb.ALB_OK
+
+
+def test_workspace_sizes(L):
+    assert alb.alb_workspace_size(alb.EQUALIZE, 2000) > alb.alb_workspace_size(alb.BRIGHTNESS, 2000)
+    assert alb.alb_workspace_size(alb.BRIGHTNESS, 2000) > alb.alb_workspace_size(alb.HFLIP, 2000)
+    cfg = alb.chain_cfg()
+    assert alb.alb_batch_workspace_size(cfg, 64, alb.MODE_PLAIN) > alb.alb_batch_workspace_size(cfg, 64,
+                                                                                                alb.MODE_FUSED)

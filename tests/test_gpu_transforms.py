@@ -1,0 +1,183 @@
+"""GPU parity of every per-image transform (images, masks, boxes) and of the
+device sampler against the oracle, through the C ABI.  Bit-exact for copies,
+LUT/integer ops, Q5 warps/resizes and nearest masks; ShiftHSV (float32 on the
+GPU, float64 in the oracle) within 1 LSB on at most 0.1 % of pixels; boxes
+within 1e-4 px."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from helpers import EXTRA_CFGS, cfg_to_lib, same_params, suite_cfgs, to_lib
+
+from paper_1809_06839_gb300 import alb, synth
+from paper_1809_06839_gb300.ragged import DeviceBatch, mask_output_batch, output_batch, to_device
+
+pytestmark = pytest.mark.gpu
+
+ALL = {**suite_cfgs(), **EXTRA_CFGS}
+# sizes spanning several work items and ragged tails, plus degenerate 1-px axes
+SIZES = [(333, 500), (129, 200), (64, 64), (17, 509), (300, 251), (1, 97), (88, 1), (1, 1), (257, 65)]
+CROP_SIZES = [(333, 500), (129, 200), (64, 64), (300, 251), (65, 64), (500, 333)]
+
+
+def sizes_for(name):
+    return CROP_SIZES if name == "RandomCrop64" else SIZES
+
+
+def hsv_ok(got, ref):
+    d = np.abs(got.astype(np.int32) - ref.astype(np.int32))
+    return d.max() <= 1 and (d > 0).mean() <= 1e-3
+
+
+@pytest.fixture(scope="module")
+def dev():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    alb.load()
+    return torch.device("cuda")
+
+
+def run_ragged(name, sizes, seed, dev, with_mask=True, with_boxes=True):
+    oc = ALL[name]
+    rb = synth.ragged_noise(sizes, seed=seed)
+    masks = synth.ragged_masks(sizes, seed=seed)
+    ops = [O.sample_params(oc, seed, oc.tid, i, h, w) for i, (h, w) in enumerate(sizes)]
+    lps = [to_lib(p, alb) for p in ops]
+    din = DeviceBatch(to_device(rb, dev))
+    dout = output_batch(lps, rb.shapes, dev)
+    prm = alb.params_to_device(lps, dev)
+    n = len(sizes)
+    dmi = dmo = None
+    if with_mask:
+        dmi = DeviceBatch(to_device(masks, dev))
+        dmo = mask_output_batch(lps, masks.shapes, dev)
+    cap = 50
+    boxes = np.zeros((n, cap, 4), np.float32)
+    nb = np.zeros(n, np.int32)
+    for i, (h, w) in enumerate(sizes):
+        b = synth.random_boxes(h, w, i, seed)[:cap]
+        boxes[i, :len(b)] = b
+        nb[i] = len(b)
+    bd = torch.from_numpy(boxes).to(dev)
+    nbd = torch.from_numpy(nb).to(dev)
+    bo = torch.zeros_like(bd)
+    nbo = torch.zeros_like(nbd)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    ws = alb.workspace(alb.alb_workspace_size(oc.tid, n), dev)
+    alb.alb_apply_ragged(oc.tid, n, prm, din.dev, dout.dev, dmi.dev if dmi else None, dmo.dev if dmo else None,
+                         bd if with_boxes else None, nbd if with_boxes else None, cap if with_boxes else 0,
+                         bo if with_boxes else None, nbo if with_boxes else None, ws, status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    return rb, masks, ops, dout, dmo, boxes, nb, bo.cpu().numpy(), nbo.cpu().numpy()
+
+
+@pytest.mark.parametrize("name", sorted(ALL))
+def test_ragged_transform_matches_oracle(dev, name):
+    sizes = sizes_for(name)
+    rb, masks, ops, dout, dmo, boxes, nb, bo, nbo = run_ragged(name, sizes, 1809, dev)
+    for i, (h, w) in enumerate(sizes):
+        img = rb.image(i).numpy()
+        ref = O.apply_image(ops[i], img)
+        got = dout.rb.image(i).cpu().numpy()
+        assert got.shape == ref.shape
+        if ops[i].tid == O.SHIFT_HSV:
+            assert hsv_ok(got, ref), (name, i)
+        else:
+            assert np.array_equal(got, ref), (name, i, (got != ref).sum())
+        mref = O.apply_mask(ops[i], masks.image(i).numpy())
+        assert np.array_equal(dmo.rb.image(i).cpu().numpy(), mref), (name, "mask", i)
+        bref = O.apply_boxes(ops[i], h, w, boxes[i, :nb[i]])
+        assert nbo[i] == len(bref), (name, "boxes", i)
+        assert np.abs(bo[i, :nbo[i]] - bref).max(initial=0) <= 1e-4
+
+
+@pytest.mark.parametrize("name", sorted(ALL))
+def test_device_sampler_matches_oracle(dev, name):
+    oc = ALL[name]
+    sizes = [(333 + (i * 29) % 168, 333 + (i * 53) % 168) for i in range(300)]
+    descs = []
+    for h, w in sizes:
+        d = alb.Image()
+        d.h, d.w, d.c, d.row_stride = h, w, 3, 3 * w
+        descs.append(d)
+    ddev = alb.descs_to_device(descs, dev)
+    pdev = torch.zeros(len(sizes) * 232, dtype=torch.uint8, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    alb.alb_sample_params_batch(cfg_to_lib(oc, alb), 1809, oc.tid, 0, len(sizes), ddev, pdev, status)
+    got = alb.params_from_device(pdev)
+    assert int(status.item()) == 0
+    for i, (h, w) in enumerate(sizes):
+        ref = O.sample_params(oc, 1809, oc.tid, i, h, w)
+        # cos/sin/log/exp on the device may differ from the host libm in the last
+        # ulp: the forward matrix is compared to 1e-12; Q16 integers and every
+        # other field must be identical
+        err = same_params(ref, got[i], rel_m=1e-12)
+        assert err is None, (name, i, err)
+
+
+def test_single_image_apply_and_in_place(dev):
+    img = synth.value_noise_image(77, 91, 3)
+    op = O.sample_params(ALL["Gamma"], 5, 8, 0, 77, 91)
+    g = img.to(dev)
+    out, _, _, _ = alb.alb_apply(to_lib(op, alb), g)
+    assert np.array_equal(out.cpu().numpy(), O.apply_image(op, img.numpy()))
+    alb.alb_apply(to_lib(op, alb), g, out=g)            # in place
+    assert np.array_equal(g.cpu().numpy(), O.apply_image(op, img.numpy()))
+    with pytest.raises(alb.AlbError):
+        hp = O.sample_params(ALL["HorizontalFlip"], 5, 1, 0, 77, 91)
+        alb.alb_apply(to_lib(hp, alb), g, out=g)       # geometric in place is rejected
+
+
+def test_empty_and_strided_images(dev):
+    # zero-row image: a no-op; a padded row stride (a column slice) is honoured
+    e = torch.empty((0, 5, 3), dtype=torch.uint8, device=dev)
+    op = O.sample_params(ALL["VerticalFlip"], 1, 2, 0, 0 + 1, 5)
+    alb.alb_apply(to_lib(op, alb), e, out=torch.empty_like(e))
+    base = synth.value_noise_image(40, 80, 4)
+    view = base.to(dev)[:, 10:60]                       # row stride 240 > 50*3
+    op = O.sample_params(ALL["Rotate"], 1, 13, 0, 40, 50)
+    out, _, _, _ = alb.alb_apply(to_lib(op, alb), view)
+    assert np.array_equal(out.cpu().numpy(), O.apply_image(op, np.ascontiguousarray(base.numpy()[:, 10:60])))
+
+
+def test_multichannel_mask_planes(dev):
+    # N instance planes interleaved (c = 5) follow the image geometry bit-exactly
+    h, w = 120, 150
+    planes = torch.stack([synth.blob_mask(h, w, i, n_classes=2) for i in range(5)], dim=2).contiguous()
+    img = synth.value_noise_image(h, w, 1)
+    for name in ("ShiftScaleRotate", "RandomSizedCrop512", "PadToSize512", "HorizontalFlip", "Transpose"):
+        op = O.sample_params(ALL[name], 3, 4, 0, h, w)
+        _, mo, _, _ = alb.alb_apply(to_lib(op, alb), img.to(dev), mask=planes.to(dev))
+        assert np.array_equal(mo.cpu().numpy(), O.apply_mask(op, planes.numpy())), name
+
+
+def test_small_plain_workload_full_size(dev):
+    """64 x 256x256 images + masks: HFlip -> Brightness/Contrast -> RandomCrop 224,
+    bit-exact against the oracle for every image (the oracle takes seconds)."""
+    n, seed = 64, 1809
+    sizes = [(256, 256)] * n
+    rb = synth.ragged_noise(sizes, seed=seed)
+    masks = synth.ragged_masks(sizes, seed=seed)
+    steps = [O.make_cfg(O.HFLIP, p=0.5), O.make_cfg(O.BRIGHTNESS_CONTRAST, lo=(0.8, -20.0), hi=(1.2, 20.0)),
+             O.make_cfg(O.RANDOM_CROP, out_h=224, out_w=224)]
+    cur = DeviceBatch(to_device(rb, dev))
+    curm = DeviceBatch(to_device(masks, dev))
+    ref = [rb.image(i).numpy() for i in range(n)]
+    refm = [masks.image(i).numpy() for i in range(n)]
+    for k, oc in enumerate(steps):
+        shapes = cur.rb.shapes
+        ops = [O.sample_params(oc, seed, 100 + k, i, s[0], s[1]) for i, s in enumerate(shapes)]
+        lps = [to_lib(p, alb) for p in ops]
+        nxt = output_batch(lps, shapes, dev)
+        nxtm = mask_output_batch(lps, curm.rb.shapes, dev)
+        ws = alb.workspace(alb.alb_workspace_size(oc.tid, n), dev)
+        alb.alb_apply_ragged(oc.tid, n, alb.params_to_device(lps, dev), cur.dev, nxt.dev, curm.dev, nxtm.dev,
+                             ws=ws)
+        ref = [O.apply_image(ops[i], ref[i]) for i in range(n)]
+        refm = [O.apply_mask(ops[i], refm[i]) for i in range(n)]
+        cur, curm = nxt, nxtm
+    torch.cuda.synchronize()
+    for i in range(n):
+        assert np.array_equal(cur.rb.image(i).cpu().numpy(), ref[i]), i
+        assert np.array_equal(curm.rb.image(i).cpu().numpy(), refm[i]), i
