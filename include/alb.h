@@ -202,6 +202,21 @@ ALB_API alb_status alb_apply_ragged(int32_t tid, int32_t n, const alb_params* pa
                             float* boxes_out_dev, int32_t* n_boxes_out_dev,
                             void* workspace, size_t workspace_bytes, int32_t* dev_status, void* stream);
 
+/* Allocation-free variant of alb_apply_ragged (images only: no masks, no
+ * boxes).  The paper has no counterpart: this exists for callers that cannot
+ * allocate device memory (an allocator callback, a process whose device
+ * memory another framework has fully reserved, a real-time loop that forbids
+ * allocation), so they cannot provide a workspace.  Scratch comes from one
+ * static 8 MiB device array inside the library (held by every GPU that loads
+ * the library until exit); at most 2048 images per call, more returns
+ * ALB_ECAPACITY.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) and should come before any stream capture.
+ * All calls share the array: calls that overlap on the GPU race and must be
+ * ordered by the caller.  Arguments as in alb_apply_ragged; allocates nothing. */
+ALB_API alb_status alb_apply_ragged_static(int32_t tid, int32_t n, const alb_params* params_dev,
+                                           const alb_image* in_dev, const alb_image* out_dev,
+                                           int32_t* dev_status, void* stream);
+
 /* ------------------------------------------------------------------ */
 /* The fused ragged-batch chain: per image, RandomResizedCrop window
  * resized (Q5 bilinear, half-pixel) to out_h x out_w, h-flip if

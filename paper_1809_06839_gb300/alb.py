@@ -98,6 +98,8 @@ def _declare(L):
     L.alb_apply_ragged.argtypes = [C.c_int32, C.c_int32, vp, vp, vp, vp, vp, vp, vp, C.c_int32, vp, vp, vp,
                                    C.c_size_t, vp, vp]
     L.alb_apply_ragged.restype = st
+    L.alb_apply_ragged_static.argtypes = [C.c_int32, C.c_int32, vp, vp, vp, vp, vp]
+    L.alb_apply_ragged_static.restype = st
     L.alb_batch_workspace_size.argtypes = [P(ChainCfg), C.c_int32, C.c_int32]
     L.alb_batch_workspace_size.restype = C.c_size_t
     L.alb_apply_batch.argtypes = [P(ChainCfg), C.c_int32, vp, vp, vp, C.c_int32, vp, C.c_size_t, vp, vp]
@@ -299,6 +301,13 @@ def alb_apply_ragged(tid: int, n: int, params_dev, in_dev, out_dev, mask_in_dev=
                                    _ptr(mask_out_dev), _ptr(boxes_dev), _ptr(n_boxes_dev), box_cap,
                                    _ptr(boxes_out_dev), _ptr(n_boxes_out_dev), _ptr(ws),
                                    0 if ws is None else ws.numel(), _ptr(dev_status), _stream(stream)))
+
+
+def alb_apply_ragged_static(tid: int, n: int, params_dev, in_dev, out_dev, dev_status=None, stream=None):
+    """alb_apply_ragged without a workspace: for callers that cannot allocate
+    device memory; scratch is a static array inside libalb (<= 2048 images)."""
+    _check(load().alb_apply_ragged_static(tid, n, _ptr(params_dev), _ptr(in_dev), _ptr(out_dev), _ptr(dev_status),
+                                          _stream(stream)))
 
 
 def alb_batch_workspace_size(cfg: ChainCfg, n: int, mode: int) -> int:
