@@ -145,16 +145,19 @@ def ev_time(fn, stream, reps=1):
 class Suite:
     """The per-transform suite on one GPU: resident inputs, per-op params/outputs."""
 
-    def __init__(self, dev, rank=0, n=SUITE_N):
+    def __init__(self, dev, rank=0, n=SUITE_N, only=None):
         from paper_1809_06839_gb300 import alb as A, synth
         from paper_1809_06839_gb300.ragged import DeviceBatch, output_batch
         self.A = A
         self.dev = dev
         self.n = n
+        self.seed = SEED + rank
         self.sizes = synth.uniform_sizes(n, SUITE_LO, SUITE_HI, seed=SEED + rank)
         self.inp = DeviceBatch(synth.ragged_noise(self.sizes, seed=SEED + rank, device=dev))
         self.ops = []
         for name, tid, kw in suite_table():
+            if only and name not in only:
+                continue
             cfg = A.sample_cfg(tid, **kw)
             pdev = torch.zeros(n * 232, dtype=torch.uint8, device=dev)
             A.alb_sample_params_batch(cfg, SEED + rank, tid, 0, n, self.inp.dev, pdev)
@@ -177,8 +180,8 @@ class Suite:
     def run_op(self, op, stream, sample=True):
         A = self.A
         if sample:
-            A.alb_sample_params_batch(op["cfg"], SEED, op["tid"], 0, self.n, self.inp.dev, op["pdev"], self.status,
-                                      stream)
+            A.alb_sample_params_batch(op["cfg"], self.seed, op["tid"], 0, self.n, self.inp.dev, op["pdev"],
+                                      self.status, stream)
         A.alb_apply_ragged(op["tid"], self.n, op["pdev"], self.inp.dev, op["out"].dev, ws=op["ws"],
                            dev_status=self.status, stream=stream)
 
@@ -482,6 +485,9 @@ def main():
     ap.add_argument("--ref-images", type=int, default=400)
     ap.add_argument("--skip-extra", action="store_true", help="headline suite only")
     ap.add_argument("--cpu-images", type=int, default=2000)
+    ap.add_argument("--only", default="", help="comma-separated suite transforms (profiling runs)")
+    ap.add_argument("--n", type=int, default=SUITE_N, help="suite images (profiling runs)")
+    ap.add_argument("--skip-e2e", action="store_true")
     args = ap.parse_args()
     ws, rank, local, dist = dist_setup(args)
     if args.impl == "reference":
@@ -497,7 +503,7 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    suite = Suite(dev, rank)
+    suite = Suite(dev, rank, n=args.n, only=set(args.only.split(",")) if args.only else None)
     hbm, peak_kind = peaks()
     clk = ClockSampler(local)
     clk.start()
@@ -520,8 +526,14 @@ def main():
     achieved = dom["alg_bytes"] / ops_t[dom["name"]] / 1e9
     status = int(suite.status.item())
     host_images = [suite.inp.rb.image(i).cpu().numpy() for i in range(min(args.cpu_images, suite.n))]
-    e2e = suite_e2e(suite, stream, max(2, args.steps // 3))
-    e2e_val = ws * suite.n * len(suite.ops) * max(2, args.steps // 3) / e2e["t"]
+    if args.skip_e2e:
+        e2e = dict(t=float("nan"), wall=float("nan"), bi=0, bo=0)
+        e2e_val = None
+    else:
+        e2e = suite_e2e(suite, stream, max(2, args.steps // 3))
+        e2e_val = ws * suite.n * len(suite.ops) * max(2, args.steps // 3) / e2e["t"]
+    launches = args.steps * suite.launches_per_step()
+    n_ops = len(suite.ops)
     extra = {}
     if not args.skip_extra:
         del suite
@@ -530,7 +542,7 @@ def main():
         extra["detection"] = detection(dev, stream)
         extra["differentiable"] = differentiable(dev, stream)
     cpu = None
-    if rank == 0 and ws == 1:
+    if rank == 0 and ws == 1 and args.cpu_images > 0:
         # the oracle on the same resident workload, copied to the host
         host = host_images
         v, thr, done, dt = oracle_suite_sample(min(args.cpu_images, len(host)), imgs=host)
@@ -554,7 +566,7 @@ def main():
                 "gpu_launches": None,
                 "device_status": status,
                 "cpu_baseline": cpu, **extra}
-        line["gpu_launches"] = args.steps * sum(1 + launches_per_op(tid) for _, tid, _ in suite_table())
+        line["gpu_launches"] = launches
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

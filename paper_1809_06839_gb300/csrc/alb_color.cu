@@ -287,28 +287,18 @@ alb_status launch_photometric(int32_t tid, int32_t n, const Plan& plan, const Im
     case ALB_BRIGHTNESS: case ALB_CONTRAST: case ALB_BRIGHTNESS_CONTRAST: case ALB_GAMMA: case ALB_SHIFT_RGB: {
       k_build_luts<<<n, 256, 0, st>>>(n, prm, luts);
       ALB_CUDA(cudaGetLastError());
-      k_apply_lut<<<grid_for((const void*)k_apply_lut, 256), 256, 0, st>>>(plan, in, out, luts);
-      ALB_CUDA(cudaGetLastError());
-      return ALB_OK;
+      return launch_stream_lut(plan, in, out, luts, st);
     }
     case ALB_EQUALIZE: {
       ALB_CUDA(cudaMemsetAsync(hist, 0, (size_t)n * 768 * sizeof(uint32_t), st));
-      k_histogram<<<grid_for((const void*)k_histogram, 256), 256, 0, st>>>(plan, in, hist);
-      ALB_CUDA(cudaGetLastError());
+      alb_status rc = launch_stream_hist(plan, in, hist, st);
+      if (rc != ALB_OK) return rc;
       k_equalize_luts<<<n, 256, 0, st>>>(n, prm, hist, luts);
       ALB_CUDA(cudaGetLastError());
-      k_apply_lut<<<grid_for((const void*)k_apply_lut, 256), 256, 0, st>>>(plan, in, out, luts);
-      ALB_CUDA(cudaGetLastError());
-      return ALB_OK;
+      return launch_stream_lut(plan, in, out, luts, st);
     }
-    case ALB_GRAYSCALE:
-      k_pixel<0><<<grid_for((const void*)k_pixel<0>, 256), 256, 0, st>>>(plan, in, out, prm);
-      ALB_CUDA(cudaGetLastError());
-      return ALB_OK;
-    case ALB_SHIFT_HSV:
-      k_pixel<1><<<grid_for((const void*)k_pixel<1>, 256), 256, 0, st>>>(plan, in, out, prm);
-      ALB_CUDA(cudaGetLastError());
-      return ALB_OK;
+    case ALB_GRAYSCALE: case ALB_SHIFT_HSV:
+      return launch_stream_pixel(tid, plan, in, out, prm, st);
     default:
       set_error("launch_photometric: transform %d is not photometric", tid);
       return ALB_EINVAL;

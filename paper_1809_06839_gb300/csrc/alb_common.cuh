@@ -44,8 +44,10 @@ ALB_HD int64_t floor_div(int64_t a, int64_t b) {  // b > 0
 
 // reflect-101 border (edge sample not repeated), any integer i, n >= 1
 ALB_HD int32_t reflect101(int64_t i, int32_t n) {
-  if (n == 1) return 0;
   if (i >= 0 && i < n) return (int32_t)i;
+  if (n == 1) return 0;
+  if (i < 0 && i > -(int64_t)n) return (int32_t)(-i);                       // one fold at the left edge
+  if (i >= n && i < 2 * (int64_t)n - 1) return (int32_t)(2 * (int64_t)(n - 1) - i);  // one fold at the right edge
   int64_t period = 2 * (int64_t)(n - 1);
   int64_t m = i % period;
   if (m < 0) m += period;

@@ -392,6 +392,8 @@ static alb_status launch_items(K kernel, const Plan& plan, const ImgList& in, co
 alb_status launch_geometric(int32_t tid, const Plan& plan, const ImgList& in, const ImgList& out,
                             const PrmList& prm, int32_t channels, bool mask, int32_t* status, cudaStream_t st) {
   const bool c3 = channels == 3, c1 = channels == 1;
+  if (launch_stream_geometric(tid, plan, in, out, prm, channels, st) == ALB_OK) return ALB_OK;
+  if (launch_tile_geometric(tid, plan, in, out, prm, channels, mask, st) == ALB_OK) return ALB_OK;
   switch (tid) {
     case ALB_HFLIP: case ALB_VFLIP: case ALB_RANDOM_CROP: case ALB_PAD_TO_SIZE: case ALB_TRANSPOSE:
     case ALB_ROT90:

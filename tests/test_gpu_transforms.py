@@ -181,3 +181,40 @@ def test_small_plain_workload_full_size(dev):
     for i in range(n):
         assert np.array_equal(cur.rb.image(i).cpu().numpy(), ref[i]), i
         assert np.array_equal(curm.rb.image(i).cpu().numpy(), refm[i]), i
+
+
+@pytest.mark.parametrize("kind,arg", [("ssr", 0.3), ("ssr", 0.45), ("ssr", 1.7), ("rot", 45.0), ("rot", -90.0),
+                                      ("resize", (37, 61)), ("resize", (700, 20)), ("resize", (1, 1)),
+                                      ("resize", (333, 500))])
+def test_resample_extremes(dev, kind, arg):
+    """Footprints that overflow the staged box (strong down-scaling) take the
+    direct-gather fallback inside the tiled kernel; both paths are exact."""
+    sizes = [(333, 500), (129, 200), (64, 64), (17, 509), (1, 97)]
+    rb = synth.ragged_noise(sizes, seed=4)
+    masks = synth.ragged_masks(sizes, seed=4)
+    ops = []
+    for i, (h, w) in enumerate(sizes):
+        p = O.Params()
+        p.apply, p.scale, p.alpha, p.gamma, p.sat = 1, 1.0, 1.0, 1.0, 1.0
+        if kind in ("ssr", "rot"):
+            p.tid = O.SHIFT_SCALE_ROTATE
+            p.angle = 17.0 + 11 * i if kind == "ssr" else arg
+            p.scale = arg if kind == "ssr" else 1.0
+            p.dx, p.dy = 0.03, -0.05
+            O.warp_geometry(p, h, w)
+        else:
+            p.tid = O.RESIZE
+            p.out_h, p.out_w, p.ch, p.cw = arg[0], arg[1], h, w
+        ops.append(p)
+    lps = [to_lib(p, alb) for p in ops]
+    din = DeviceBatch(to_device(rb, dev))
+    dmi = DeviceBatch(to_device(masks, dev))
+    dout = output_batch(lps, rb.shapes, dev)
+    dmo = mask_output_batch(lps, masks.shapes, dev)
+    ws = alb.workspace(alb.alb_workspace_size(ops[0].tid, len(sizes)), dev)
+    alb.alb_apply_ragged(ops[0].tid, len(sizes), alb.params_to_device(lps, dev), din.dev, dout.dev, dmi.dev, dmo.dev,
+                         ws=ws)
+    torch.cuda.synchronize()
+    for i in range(len(sizes)):
+        assert np.array_equal(dout.rb.image(i).cpu().numpy(), O.apply_image(ops[i], rb.image(i).numpy())), (kind, i)
+        assert np.array_equal(dmo.rb.image(i).cpu().numpy(), O.apply_mask(ops[i], masks.image(i).numpy())), (kind, i)
