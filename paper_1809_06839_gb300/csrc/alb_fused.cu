@@ -30,27 +30,66 @@ ALB_D uint8_t sat_rne_d(double v) {
 
 // ---------------------------------------------------------------- step functions
 ALB_D int32_t chain_q5(int32_t d, int32_t n_in, int32_t n_out) {
-  int64_t num = 32 * ((int64_t)(2 * d + 1) * n_in - n_out) + n_out;
-  int64_t xq = floor_div(num, 2 * (int64_t)n_out);
+  int64_t xq;
+  if (n_in <= 2048 && n_out <= 2048) {    // |numerator| < 2^29: exact in 32-bit
+    const int32_t num = 32 * ((2 * d + 1) * n_in - n_out) + n_out, den = 2 * n_out;
+    const int32_t q = num / den;
+    xq = (num % den != 0 && num < 0) ? q - 1 : q;
+  } else {
+    xq = floor_div(32 * ((int64_t)(2 * d + 1) * n_in - n_out) + n_out, 2 * (int64_t)n_out);
+  }
   if (xq < 0) xq = 0;
   if ((xq >> 5) >= n_in - 1) xq = 32 * (int64_t)(n_in - 1);
   return (int32_t)xq;
 }
 
-// Q5 bilinear sample (3 channels) of the crop window at Q5 coordinates (xq, yq).
+// The 6 bytes at p (pixels ix, ix + 1 of a row) as lo = bytes 0..3, hi = 4..5,
+// read as aligned words; the third word only when it holds a needed byte.
+ALB_D void chain_pair(const uint8_t* p, uint32_t& lo, uint32_t& hi) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+  const uint32_t* w = reinterpret_cast<const uint32_t*>(a & ~uintptr_t(3));
+  const int s = (int)(a & 3);
+  const uint32_t w0 = __ldg(w), w1 = __ldg(w + 1), w2 = s == 3 ? __ldg(w + 2) : 0u;
+  lo = __funnelshift_r(w0, w1, 8 * s);
+  hi = __funnelshift_r(w1, w2, 8 * s);
+}
+
+// Q5 bilinear sample (3 channels) of the crop window at Q5 coordinates
+// (xq, yq): (sum w_ij p_ij + 512) >> 10, evaluated exactly as
+// ((32 - fy) h_top + fy h_bot + 512) >> 10, h = (32 - fx) p0 + fx p1, with
+// dp4a for the horizontal pairs and dp2a for the vertical pair.
 ALB_D void chain_bilinear(const uint8_t* __restrict__ win, int64_t stride, int32_t ch, int32_t cw, int32_t xq,
                           int32_t yq, uint32_t rgb[3]) {
-  const int32_t ix = xq >> 5, fx = xq & 31, iy = yq >> 5, fy = yq & 31;
-  const int32_t ixb = imin(ix + 1, cw - 1), iyb = imin(iy + 1, ch - 1);
+  int32_t ix = xq >> 5;
+  const int32_t fx = xq & 31, iy = yq >> 5, fy = yq & 31;
+  const int32_t iyb = imin(iy + 1, ch - 1);
   const uint8_t* ra = win + (int64_t)iy * stride;
   const uint8_t* rb = win + (int64_t)iyb * stride;
-  const int32_t w00 = (32 - fx) * (32 - fy), w01 = fx * (32 - fy), w10 = (32 - fx) * fy, w11 = fx * fy;
-#pragma unroll
-  for (int c = 0; c < 3; c++) {
-    const int32_t acc = w00 * __ldg(ra + 3 * ix + c) + w01 * __ldg(ra + 3 * ixb + c) +
-                        w10 * __ldg(rb + 3 * ix + c) + w11 * __ldg(rb + 3 * ixb + c);
-    rgb[c] = (uint32_t)((acc + 512) >> 10);
+  uint32_t wx = (uint32_t)(32 - fx) | ((uint32_t)fx << 8);
+  const uint32_t wy = (uint32_t)(32 - fy) | ((uint32_t)fy << 8);
+  uint32_t tl, th, bl, bh;
+  if (cw >= 2) {
+    if (ix + 1 >= cw) {   // clamped last column (fx = 0): pair (ix - 1, ix), weights swapped
+      ix -= 1;
+      wx = 32u << 8;
+    }
+    chain_pair(ra + 3 * ix, tl, th);
+    chain_pair(rb + 3 * ix, bl, bh);
+  } else {                // one-column window: both horizontal taps are that column
+    const uint32_t t = (uint32_t)ra[0] | ((uint32_t)ra[1] << 8) | ((uint32_t)ra[2] << 16);
+    const uint32_t u = (uint32_t)rb[0] | ((uint32_t)rb[1] << 8) | ((uint32_t)rb[2] << 16);
+    tl = t | (t << 24); th = t >> 8; bl = u | (u << 24); bh = u >> 8;
+    wx = 32u;
   }
+  const uint32_t ht_r = __dp4a(__byte_perm(tl, th, 0x0030), wx, 0u);
+  const uint32_t hb_r = __dp4a(__byte_perm(bl, bh, 0x0030), wx, 0u);
+  const uint32_t ht_g = __dp4a(__byte_perm(tl, th, 0x0041), wx, 0u);
+  const uint32_t hb_g = __dp4a(__byte_perm(bl, bh, 0x0041), wx, 0u);
+  const uint32_t ht_b = __dp4a(__byte_perm(tl, th, 0x0052), wx, 0u);
+  const uint32_t hb_b = __dp4a(__byte_perm(bl, bh, 0x0052), wx, 0u);
+  rgb[0] = __dp2a_lo(__byte_perm(ht_r, hb_r, 0x5410), wy, 512u) >> 10;
+  rgb[1] = __dp2a_lo(__byte_perm(ht_g, hb_g, 0x5410), wy, 512u) >> 10;
+  rgb[2] = __dp2a_lo(__byte_perm(ht_b, hb_b, 0x5410), wy, 512u) >> 10;
 }
 
 // saturation blend with the BT.601 grey value, float32, clamped, not rounded
@@ -78,7 +117,12 @@ __global__ void k_chain_luts(int32_t n, const alb_params* __restrict__ prm, uint
 }
 
 // ---------------------------------------------------------------- fused kernel
-// Item = (image, band of `band` output rows).  Queue: one global counter.
+// Item = (image, band of `band` output rows), pulled from one global counter.
+// Per image the column coordinates (flip folded in) and the colour table live
+// in shared memory; per band the row coordinates are computed once.  A thread
+// produces two horizontally adjacent pixels, stored as one bf16x2 per channel.
+constexpr int kBandMax = 32;
+
 __global__ void __launch_bounds__(256) k_chain_fused(int32_t n, const alb_params* __restrict__ prm,
                                                      const alb_image* __restrict__ imgs,
                                                      const uint8_t* __restrict__ luts, ChainK K, int32_t band,
@@ -86,10 +130,11 @@ __global__ void __launch_bounds__(256) k_chain_fused(int32_t n, const alb_params
   __shared__ int32_t s_item;
   __shared__ uint8_t s_lut[256];
   __shared__ int32_t s_col[1024];
-  __shared__ int32_t s_b;
+  __shared__ int32_t s_row[kBandMax];
   const int32_t bands = (K.oh + band - 1) / band;
   const int64_t total = (int64_t)n * bands;
   const int64_t plane = (int64_t)K.oh * K.ow;
+  const bool pairs = (K.ow & 1) == 0;
   int32_t cached = -1;
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(queue, 1);
@@ -104,26 +149,50 @@ __global__ void __launch_bounds__(256) k_chain_fused(int32_t n, const alb_params
         const int32_t xr = p.flip ? K.ow - 1 - x : x;  // output column x shows resized column xr
         s_col[x] = chain_q5(xr, p.cw, K.ow);
       }
-      if (threadIdx.x == 0) s_b = b;
       cached = b;
     }
+    if (threadIdx.x < r1 - r0) s_row[threadIdx.x] = chain_q5(r0 + threadIdx.x, p.ch, K.oh);
     __syncthreads();
     const alb_image im = imgs[b];
     const uint8_t* win = (const uint8_t*)im.data + (int64_t)p.y0 * im.row_stride + 3 * (int64_t)p.x0;
     const float s = (float)p.sat;
     __nv_bfloat16* ob = out + (int64_t)b * 3 * plane;
-    const int32_t npx = (r1 - r0) * K.ow;
-    for (int32_t i = threadIdx.x; i < npx; i += blockDim.x) {
-      const int32_t y = r0 + i / K.ow, x = i - (i / K.ow) * K.ow;
-      const int32_t yq = chain_q5(y, p.ch, K.oh);
-      uint32_t rgb[3];
-      chain_bilinear(win, im.row_stride, p.ch, p.cw, s_col[x], yq, rgb);
+    if (pairs) {
+      const int32_t hw = K.ow >> 1;
+      const int32_t npair = (r1 - r0) * hw;
+      for (int32_t i = threadIdx.x; i < npair; i += blockDim.x) {
+        const int32_t yy = i / hw, x = 2 * (i - yy * hw), y = r0 + yy;
+        const int32_t yq = s_row[yy];
+        uint32_t a[3], c[3];
+        chain_bilinear(win, im.row_stride, p.ch, p.cw, s_col[x], yq, a);
+        chain_bilinear(win, im.row_stride, p.ch, p.cw, s_col[x + 1], yq, c);
 #pragma unroll
-      for (int c = 0; c < 3; c++) rgb[c] = s_lut[rgb[c]];
-      float v[3];
-      chain_saturate(rgb, s, v);
+        for (int q = 0; q < 3; q++) { a[q] = s_lut[a[q]]; c[q] = s_lut[c[q]]; }
+        float va[3], vc[3];
+        chain_saturate(a, s, va);
+        chain_saturate(c, s, vc);
+        const int64_t o = (int64_t)y * K.ow + x;
 #pragma unroll
-      for (int c = 0; c < 3; c++) ob[c * plane + (int64_t)y * K.ow + x] = chain_normalize(v[c], K.k[c], K.m[c]);
+        for (int q = 0; q < 3; q++) {
+          __nv_bfloat162 v2;
+          v2.x = chain_normalize(va[q], K.k[q], K.m[q]);
+          v2.y = chain_normalize(vc[q], K.k[q], K.m[q]);
+          *reinterpret_cast<__nv_bfloat162*>(ob + q * plane + o) = v2;
+        }
+      }
+    } else {
+      const int32_t npx = (r1 - r0) * K.ow;
+      for (int32_t i = threadIdx.x; i < npx; i += blockDim.x) {
+        const int32_t yy = i / K.ow, x = i - yy * K.ow, y = r0 + yy;
+        uint32_t rgb[3];
+        chain_bilinear(win, im.row_stride, p.ch, p.cw, s_col[x], s_row[yy], rgb);
+#pragma unroll
+        for (int q = 0; q < 3; q++) rgb[q] = s_lut[rgb[q]];
+        float v[3];
+        chain_saturate(rgb, s, v);
+#pragma unroll
+        for (int q = 0; q < 3; q++) ob[q * plane + (int64_t)y * K.ow + x] = chain_normalize(v[q], K.k[q], K.m[q]);
+      }
     }
     __syncthreads();
   }
@@ -216,7 +285,7 @@ alb_status launch_chain(const alb_chain_cfg& cfg, int32_t n, const alb_params* p
   __nv_bfloat16* o = (__nv_bfloat16*)out;
   if (mode == ALB_MODE_FUSED) {
     ALB_REQUIRE(cfg.out_w <= 1024, ALB_ESHAPE, "alb_apply_batch: fused mode supports out_w <= 1024");
-    const int32_t band = cfg.tile_h > 0 ? cfg.tile_h : 4;
+    const int32_t band = cfg.tile_h > 0 ? imin(cfg.tile_h, kBandMax) : 8;
     int per_sm = cfg.ctas_per_sm;
     if (per_sm <= 0) {
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chain_fused, 256, 0);
