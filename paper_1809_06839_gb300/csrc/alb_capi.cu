@@ -82,15 +82,19 @@ static alb_status run_ragged(int32_t tid, int32_t n, const PrmList& prm, const I
   ALB_REQUIRE(prefix && rpi && mprefix && mrpi && (!uses_lut(tid) || luts) && (tid != ALB_EQUALIZE || hist),
               ALB_EWORKSPACE, "workspace of %zu bytes is smaller than the %zu required", ws_bytes, ragged_ws(tid, n));
   if (out.dev || out.one.data) {
-    alb_status rc = launch_plan(out, n, kItemBytes, prefix, rpi, st);
+    // ragged image slots are RGB; a single image (validated on the host) may have any c for geometric transforms
+    const int32_t img_c = in.dev ? 3 : in.one.c;
+    const PlanCheck chk{tid, img_c, geo, in, prm, status};
+    alb_status rc = launch_plan(out, n, kItemBytes, prefix, rpi, chk, st);
     if (rc != ALB_OK) return rc;
     Plan plan{prefix, rpi, n};
-    rc = geo ? launch_geometric(tid, plan, in, out, prm, 3, false, status, st)
+    rc = geo ? launch_geometric(tid, plan, in, out, prm, img_c, false, status, st)
              : launch_photometric(tid, n, plan, in, out, prm, luts, hist, status, st);
     if (rc != ALB_OK) return rc;
   }
   if (min_ && mout) {
-    alb_status rc = launch_plan(*mout, n, kItemBytes, mprefix, mrpi, st);
+    const PlanCheck mchk{tid, 0, geo, *min_, prm, status};
+    alb_status rc = launch_plan(*mout, n, kItemBytes, mprefix, mrpi, mchk, st);
     if (rc != ALB_OK) return rc;
     Plan mplan{mprefix, mrpi, n};
     // photometric transforms leave masks unchanged: copy with an identity flip record

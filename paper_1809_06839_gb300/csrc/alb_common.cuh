@@ -113,8 +113,53 @@ struct Carve {
 
 constexpr size_t plan_bytes(int32_t n) { return 256 + ((size_t)(n + 1) * 4 + 255) / 256 * 256 + ((size_t)n * 4 + 255) / 256 * 256 + 256; }
 
-// host launcher for the plan kernel (alb_geom.cu)
+// Output size of a parameter record applied to an h x w input (C-ABI rules).
+ALB_HD void record_out_shape(const alb_params& p, int32_t h, int32_t w, int32_t& oh, int32_t& ow) {
+  oh = h; ow = w;
+  switch (p.tid) {
+    case ALB_RANDOM_CROP: case ALB_PAD_TO_SIZE: case ALB_RESIZE: case ALB_RANDOM_SIZED_CROP:
+    case ALB_RANDOM_RESIZED_CROP: case ALB_CHAIN:
+      oh = p.out_h; ow = p.out_w; break;
+    case ALB_TRANSPOSE: oh = w; ow = h; break;
+    case ALB_ROT90: if (p.apply && (p.k & 1)) { oh = w; ow = h; } break;
+    default: break;
+  }
+}
+
+// Per-image consistency of a ragged launch, checked on the device before any
+// pixel is touched: 0, or the alb_status of the first violation.  want_c = 3
+// for RGB image slots, 0 for masks (any c, equal in and out); geometric =
+// whether the output follows the record's geometry (masks of photometric
+// transforms keep the input size).
+ALB_D int check_image_pair(int32_t tid, const alb_params& p, const alb_image& si, const alb_image& so,
+                           int32_t want_c, bool geometric) {
+  if (p.tid != tid) return ALB_EINVAL;
+  if (si.c != so.c || si.c < 1 || (want_c && si.c != want_c)) return ALB_EINVAL;
+  if (si.h < 0 || si.w < 0 || so.h < 0 || so.w < 0) return ALB_ESHAPE;
+  if (si.row_stride < (int64_t)si.w * si.c || so.row_stride < (int64_t)so.w * so.c) return ALB_ESHAPE;
+  int32_t oh = si.h, ow = si.w;
+  if (geometric) record_out_shape(p, si.h, si.w, oh, ow);
+  if (oh != so.h || ow != so.w) return ALB_ESHAPE;
+  if (geometric && (tid == ALB_RANDOM_CROP || tid == ALB_RESIZE || tid == ALB_RANDOM_SIZED_CROP ||
+                    tid == ALB_RANDOM_RESIZED_CROP)) {
+    if (p.ch < 1 || p.cw < 1 || p.y0 < 0 || p.x0 < 0 || p.y0 + p.ch > si.h || p.x0 + p.cw > si.w) return ALB_ESHAPE;
+    if (tid == ALB_RANDOM_CROP && (p.ch != so.h || p.cw != so.w)) return ALB_ESHAPE;
+  }
+  if (geometric && tid == ALB_PAD_TO_SIZE && (p.y0 < 0 || p.x0 < 0 || p.y0 + si.h > so.h || p.x0 + si.w > so.w))
+    return ALB_ESHAPE;
+  return 0;
+}
+
+// Host launchers for the plan kernels (alb_geom.cu).  Images that fail
+// check_image_pair get no work items and record their status.
+struct PlanCheck {
+  int32_t tid, want_c;
+  bool geometric;
+  ImgList in;
+  PrmList prm;
+  int32_t* status;
+};
 alb_status launch_plan(const ImgList& out, int32_t n, int32_t target_bytes, int32_t* prefix,
-                       int32_t* rows_per_item, cudaStream_t st);
+                       int32_t* rows_per_item, const PlanCheck& chk, cudaStream_t st);
 
 }  // namespace alb

@@ -16,7 +16,7 @@ namespace alb {
 
 // ------------------------------------------------------------------ plan
 __global__ void k_plan(ImgList out, int32_t n, int32_t target, int32_t* __restrict__ prefix,
-                       int32_t* __restrict__ rows_per_item) {
+                       int32_t* __restrict__ rows_per_item, PlanCheck chk) {
   __shared__ int32_t wsum[32];
   __shared__ int32_t carry;
   if (threadIdx.x == 0) carry = 0;
@@ -32,6 +32,8 @@ __global__ void k_plan(ImgList out, int32_t n, int32_t target, int32_t* __restri
       rb = imax(1, imin(rb, imax(im.h, 1)));
       cnt = im.h > 0 && im.w > 0 ? (im.h + rb - 1) / rb : 0;
       rows_per_item[i] = rb;
+      const int bad = check_image_pair(chk.tid, chk.prm.get(i), chk.in.get(i), im, chk.want_c, chk.geometric);
+      if (bad) { cnt = 0; dev_fail(chk.status, bad); }
     }
     int32_t v = cnt;
 #pragma unroll
@@ -61,8 +63,8 @@ __global__ void k_plan(ImgList out, int32_t n, int32_t target, int32_t* __restri
 }
 
 alb_status launch_plan(const ImgList& out, int32_t n, int32_t target_bytes, int32_t* prefix,
-                       int32_t* rows_per_item, cudaStream_t st) {
-  k_plan<<<1, 1024, 0, st>>>(out, n, target_bytes, prefix, rows_per_item);
+                       int32_t* rows_per_item, const PlanCheck& chk, cudaStream_t st) {
+  k_plan<<<1, 1024, 0, st>>>(out, n, target_bytes, prefix, rows_per_item, chk);
   ALB_CUDA(cudaGetLastError());
   return ALB_OK;
 }
@@ -391,9 +393,10 @@ static alb_status launch_items(K kernel, const Plan& plan, const ImgList& in, co
 
 alb_status launch_geometric(int32_t tid, const Plan& plan, const ImgList& in, const ImgList& out,
                             const PrmList& prm, int32_t channels, bool mask, int32_t* status, cudaStream_t st) {
+  const PlanCheck chk{tid, mask ? 0 : channels, true, in, prm, status};
   const bool c3 = channels == 3, c1 = channels == 1;
   if (launch_stream_geometric(tid, plan, in, out, prm, channels, st) == ALB_OK) return ALB_OK;
-  if (launch_tile_geometric(tid, plan, in, out, prm, channels, mask, st) == ALB_OK) return ALB_OK;
+  if (launch_tile_geometric(tid, plan, in, out, prm, channels, mask, chk, st) == ALB_OK) return ALB_OK;
   switch (tid) {
     case ALB_HFLIP: case ALB_VFLIP: case ALB_RANDOM_CROP: case ALB_PAD_TO_SIZE: case ALB_TRANSPOSE:
     case ALB_ROT90:

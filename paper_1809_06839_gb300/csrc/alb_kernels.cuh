@@ -22,7 +22,8 @@ alb_status launch_stream_hist(const Plan& plan, const ImgList& in, uint32_t* his
 
 // alb_resample.cu (tiled warps and resizes)
 alb_status launch_tile_geometric(int32_t tid, const Plan& plan, const ImgList& in, const ImgList& out,
-                                 const PrmList& prm, int32_t channels, bool mask, cudaStream_t st);
+                                 const PrmList& prm, int32_t channels, bool mask, const PlanCheck& chk,
+                                 cudaStream_t st);
 
 // alb_color.cu
 alb_status launch_photometric(int32_t tid, int32_t n, const Plan& plan, const ImgList& in, const ImgList& out,

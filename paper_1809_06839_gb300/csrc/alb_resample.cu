@@ -35,7 +35,7 @@ struct WPitch {
 
 // --------------------------------------------------------------- tile plan
 __global__ void k_plan_tiles(ImgList out, int32_t n, int32_t tile, int32_t* __restrict__ prefix,
-                             int32_t* __restrict__ tiles_x) {
+                             int32_t* __restrict__ tiles_x, PlanCheck chk) {
   __shared__ int32_t wsum[32];
   __shared__ int32_t carry;
   if (threadIdx.x == 0) carry = 0;
@@ -49,6 +49,7 @@ __global__ void k_plan_tiles(ImgList out, int32_t n, int32_t tile, int32_t* __re
       const int32_t tx = (im.w + tile - 1) / tile, ty = (im.h + tile - 1) / tile;
       cnt = im.h > 0 && im.w > 0 ? tx * ty : 0;
       tiles_x[i] = tx > 0 ? tx : 1;
+      if (check_image_pair(chk.tid, chk.prm.get(i), chk.in.get(i), im, chk.want_c, chk.geometric)) cnt = 0;
     }
     int32_t v = cnt;
 #pragma unroll
@@ -420,7 +421,8 @@ static alb_status launch_k(void (*kern)(KArgs...), cudaStream_t st, Args... args
 
 // Returns ALB_EINVAL (nothing launched) when no tiled kernel covers the case.
 alb_status launch_tile_geometric(int32_t tid, const Plan& plan, const ImgList& in, const ImgList& out,
-                                 const PrmList& prm, int32_t channels, bool mask, cudaStream_t st) {
+                                 const PrmList& prm, int32_t channels, bool mask, const PlanCheck& chk,
+                                 cudaStream_t st) {
   const bool affine = tid == ALB_ROTATE || tid == ALB_SHIFT_SCALE_ROTATE;
   const bool resize = tid == ALB_RESIZE || tid == ALB_RANDOM_SIZED_CROP || tid == ALB_RANDOM_RESIZED_CROP;
   if (!affine && !resize) return ALB_EINVAL;
@@ -428,7 +430,7 @@ alb_status launch_tile_geometric(int32_t tid, const Plan& plan, const ImgList& i
   // the row plan's arrays are rewritten as a tile plan (stream-ordered)
   int32_t* prefix = const_cast<int32_t*>(plan.prefix);
   int32_t* tiles_x = const_cast<int32_t*>(plan.rows_per_item);
-  k_plan_tiles<<<1, 1024, 0, st>>>(out, plan.n, WT, prefix, tiles_x);
+  k_plan_tiles<<<1, 1024, 0, st>>>(out, plan.n, WT, prefix, tiles_x, chk);
   ALB_CUDA(cudaGetLastError());
   if (affine) {
     if (mask) return launch_k(k_resample_warp<MAP_AFFINE, true, 1>, st, plan, in, out, prm);

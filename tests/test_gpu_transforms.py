@@ -218,3 +218,38 @@ def test_resample_extremes(dev, kind, arg):
     for i in range(len(sizes)):
         assert np.array_equal(dout.rb.image(i).cpu().numpy(), O.apply_image(ops[i], rb.image(i).numpy())), (kind, i)
         assert np.array_equal(dmo.rb.image(i).cpu().numpy(), O.apply_mask(ops[i], masks.image(i).numpy())), (kind, i)
+
+
+def test_inconsistent_descriptors_are_rejected_on_device(dev):
+    """Descriptors the host cannot inspect (device arrays) are validated per
+    image before any pixel is touched: a wrong output size, a crop window
+    outside its image or a 1-channel image in an RGB slot record a status and
+    the other images are still processed."""
+    sizes = [(64, 80), (50, 70), (90, 40)]
+    rb = synth.ragged_noise(sizes, seed=8)
+    oc = ALL["RandomCrop64"]
+    ops = [O.sample_params(O.make_cfg(O.RANDOM_CROP, out_h=32, out_w=32), 8, 3, i, h, w)
+           for i, (h, w) in enumerate(sizes)]
+    lps = [to_lib(p, alb) for p in ops]
+    lps[1].y0 = 40                                          # window 40..72 outside the 50-row image
+    din = DeviceBatch(to_device(rb, dev))
+    dout = output_batch(lps, rb.shapes, dev)
+    descs = list(dout.descs)
+    descs[2].w = 31                                          # output narrower than the record says
+    out_dev = alb.descs_to_device(descs, dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    ws = alb.workspace(alb.alb_workspace_size(oc.tid, 3), dev)
+    alb.alb_apply_ragged(oc.tid, 3, alb.params_to_device(lps, dev), din.dev, out_dev, ws=ws, dev_status=status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == alb.ALB_ESHAPE
+    assert np.array_equal(dout.rb.image(0).cpu().numpy(), O.apply_image(ops[0], rb.image(0).numpy()))
+    # a single-channel image in an RGB slot of a ragged photometric launch
+    gray = synth.empty_ragged([(20, 30, 1)], device=dev)
+    gin = DeviceBatch(gray)
+    gout = DeviceBatch(synth.empty_ragged([(20, 30, 1)], device=dev))
+    gp = to_lib(O.sample_params(ALL["Gamma"], 1, 8, 0, 20, 30), alb)
+    status.zero_()
+    ws = alb.workspace(alb.alb_workspace_size(alb.GAMMA, 1), dev)
+    alb.alb_apply_ragged(alb.GAMMA, 1, alb.params_to_device([gp], dev), gin.dev, gout.dev, ws=ws, dev_status=status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == alb.ALB_EINVAL
