@@ -4,7 +4,7 @@
  * (arXiv 1809.06839).
  *
  * The paper's method: a transform with sampled parameters is applied to an
- * image and, "in the same way", to its targets -- segmentation masks and
+ * image and, with the same geometry, to its targets -- segmentation masks and
  * bounding boxes (Sec. II, Sec. II-A, Sec. II-B); Table I (Sec. III) lists
  * the benchmarked transforms.  The paper defines none of the operations
  * mathematically; the definitions this library implements (coordinate
@@ -63,7 +63,7 @@ typedef enum alb_tid {
   ALB_RANDOM_CROP = 3,           /* Table I "RandomCrop64" */
   ALB_PAD_TO_SIZE = 4,           /* Table I "PadToSize512" */
   ALB_BRIGHTNESS = 5,            /* Table I "Brightness" */
-  ALB_CONTRAST = 6,              /* Sec. II, Fig. 1 "contrast" */
+  ALB_CONTRAST = 6,              /* Sec. II, Fig. 1 contrast transform */
   ALB_BRIGHTNESS_CONTRAST = 7,   /* brightness and contrast as one table */
   ALB_GAMMA = 8,                 /* Table I "Gamma" */
   ALB_SHIFT_RGB = 9,             /* Table I "ShiftRGB" */
@@ -72,8 +72,8 @@ typedef enum alb_tid {
   ALB_EQUALIZE = 12,             /* per-channel histogram equalisation */
   ALB_ROTATE = 13,               /* Table I "Rotate" */
   ALB_SHIFT_SCALE_ROTATE = 14,   /* Table I "ShiftScaleRotate" */
-  ALB_RESIZE = 15,               /* Sec. II-B "scaling" */
-  ALB_RANDOM_SIZED_CROP = 16,    /* Sec. II-A, Fig. 2 "random sized crop" */
+  ALB_RESIZE = 15,               /* Sec. II-B scaling */
+  ALB_RANDOM_SIZED_CROP = 16,    /* Sec. II-A, Fig. 2 random sized crop */
   ALB_RANDOM_RESIZED_CROP = 17,  /* crop of sampled area and aspect, resized */
   ALB_TRANSPOSE = 18,            /* Sec. II-B, Dih4 element */
   ALB_ROT90 = 19,                /* Sec. II-B, Dih4 rotations */
@@ -88,8 +88,8 @@ typedef struct alb_image {
   int64_t row_stride;   /* bytes from one row to the next, >= w*c */
 } alb_image;
 
-/* The sampled parameters of one transform for one image (Sec. II: "the
- * parameters of transformation").  Produced by alb_sample_params[_batch];
+/* The sampled parameters of one transform for one image (Sec. II: the
+ * transform's parameters).  Produced by alb_sample_params[_batch];
  * callers may also fill it themselves.  Fields unused by a transform are 0
  * (scale, alpha, gamma and sat default to 1).  232 bytes. */
 typedef struct alb_params {
@@ -141,8 +141,8 @@ typedef struct alb_chain_cfg {
 enum { ALB_MODE_FUSED = 0, ALB_MODE_PLAIN = 1 };
 
 /* ------------------------------------------------------------------ */
-/* Parameter sampling (Sec. II: transforms applied "with sampled
- * parameters").  Philox4x32-10 (Salmon et al., SC'11): the word stream of
+/* Parameter sampling (Sec. II: each transform is applied with parameters drawn at
+ * random).  Philox4x32-10 (Salmon et al., SC'11): the word stream of
  * image `index` is Philox blocks with counter (j, index, stream_id lo,
  * stream_id hi) and key seed; uniform doubles take 27+26 bits of two words;
  * integers use Lemire's multiply-shift with rejection.  The probability draw
@@ -169,7 +169,7 @@ ALB_API size_t alb_workspace_size(int32_t tid, int32_t n);
 /* ------------------------------------------------------------------ */
 /* Apply one transform to one image and, optionally, its mask and boxes
  * (Sec. II-A: masks and boxes are transformed together with the image;
- * Sec. II-B: masks "in the same way as the original image").
+ * Sec. II-B: binary masks follow the image geometry).
  *  params:  HOST pointer to one record.
  *  in/out:  HOST structs describing DEVICE images; out must have the size
  *           alb_output_shape gives and the same c.  NULL out skips the image.

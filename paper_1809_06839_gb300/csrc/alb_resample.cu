@@ -1,6 +1,6 @@
 // alb_resample.cu -- tiled resampling for the transforms that move pixels along
 // a continuous map: the affine warps (Table I: Rotate, ShiftScaleRotate) and
-// the resizes (Sec. II-B "scaling"; Sec. II-A random sized crop), for images
+// the resizes (Sec. II-B scaling; Sec. II-A random sized crop), for images
 // (Q5 bilinear) and their masks (nearest), with reflect-101 borders for warps.
 //
 // Work item = one 16 x 16 output tile, owned by ONE warp: there is no
