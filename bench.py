@@ -253,9 +253,10 @@ def suite_e2e(suite, stream, steps):
 
 
 # ------------------------------------------------------------------ sub-workloads
-def fused_pipeline(dev, stream, steps=3, warmup=2):
+def fused_pipeline(dev, stream, steps=3, warmup=2, n=FUSED_N):
     from paper_1809_06839_gb300 import alb as A, synth
     from paper_1809_06839_gb300.ragged import DeviceBatch
+    FUSED_N = n
     sizes = synth.uniform_sizes(FUSED_N, FUSED_LO, FUSED_HI, seed=SEED)
     din = DeviceBatch(synth.ragged_noise(sizes, seed=SEED, device=dev))
     cfg = A.sample_cfg(A.CHAIN, out_h=224, out_w=224, lo=(0.08, 3 / 4, 0.6), hi=(1.0, 4 / 3, 1.4))
@@ -488,6 +489,9 @@ def main():
     ap.add_argument("--only", default="", help="comma-separated suite transforms (profiling runs)")
     ap.add_argument("--n", type=int, default=SUITE_N, help="suite images (profiling runs)")
     ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--extras", default="fused,detection,differentiable",
+                    help="sub-workloads to run after the suite (comma-separated)")
+    ap.add_argument("--fused-n", type=int, default=FUSED_N, help="images of the fused workload (profiling runs)")
     args = ap.parse_args()
     ws, rank, local, dist = dist_setup(args)
     if args.impl == "reference":
@@ -538,9 +542,13 @@ def main():
     if not args.skip_extra:
         del suite
         torch.cuda.empty_cache()
-        extra["fused_pipeline"] = fused_pipeline(dev, stream)
-        extra["detection"] = detection(dev, stream)
-        extra["differentiable"] = differentiable(dev, stream)
+        which = set(args.extras.split(","))
+        if "fused" in which:
+            extra["fused_pipeline"] = fused_pipeline(dev, stream, n=args.fused_n)
+        if "detection" in which:
+            extra["detection"] = detection(dev, stream)
+        if "differentiable" in which:
+            extra["differentiable"] = differentiable(dev, stream)
     cpu = None
     if rank == 0 and ws == 1 and args.cpu_images > 0:
         # the oracle on the same resident workload, copied to the host

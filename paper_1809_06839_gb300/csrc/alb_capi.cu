@@ -84,7 +84,7 @@ static alb_status run_ragged(int32_t tid, int32_t n, const PrmList& prm, const I
   if (out.dev || out.one.data) {
     // ragged image slots are RGB; a single image (validated on the host) may have any c for geometric transforms
     const int32_t img_c = in.dev ? 3 : in.one.c;
-    const PlanCheck chk{tid, img_c, geo, in, prm, status};
+    const PlanCheck chk{tid, img_c, geo, in, prm, status, 0};
     alb_status rc = launch_plan(out, n, kItemBytes, prefix, rpi, chk, st);
     if (rc != ALB_OK) return rc;
     Plan plan{prefix, rpi, n};
@@ -93,20 +93,29 @@ static alb_status run_ragged(int32_t tid, int32_t n, const PrmList& prm, const I
     if (rc != ALB_OK) return rc;
   }
   if (min_ && mout) {
-    const PlanCheck mchk{tid, 0, geo, *min_, prm, status};
-    alb_status rc = launch_plan(*mout, n, kItemBytes, mprefix, mrpi, mchk, st);
-    if (rc != ALB_OK) return rc;
-    Plan mplan{mprefix, mrpi, n};
-    // photometric transforms leave masks unchanged: copy with an identity flip record
-    if (geo) {
-      rc = launch_geometric(tid, mplan, *min_, *mout, prm, mout->dev ? 0 : mout->one.c, true, status, st);
-    } else {
-      PrmList ident{nullptr, {}};
-      ident.one.tid = ALB_HFLIP;
-      ident.one.apply = 0;
-      rc = launch_geometric(ALB_HFLIP, mplan, *min_, *mout, ident, mout->dev ? 0 : mout->one.c, true, status, st);
+    // The masks' channel count is known on the host only for a single image;
+    // a ragged launch runs two mask passes: single-channel masks through the
+    // specialised kernels, every other mask through the general ones (each
+    // pass's plan gives the other pass's masks no items).
+    const int npass = mout->dev ? 2 : 1;
+    for (int pass = 0; pass < npass; pass++) {
+      const int32_t chans = mout->dev ? (pass == 0 ? 1 : 0) : mout->one.c;
+      const int32_t filter = mout->dev ? (pass == 0 ? 1 : -1) : 0;
+      const PlanCheck mchk{tid, 0, geo, *min_, prm, status, filter};
+      alb_status rc = launch_plan(*mout, n, kItemBytes, mprefix, mrpi, mchk, st);
+      if (rc != ALB_OK) return rc;
+      Plan mplan{mprefix, mrpi, n};
+      if (geo) {
+        rc = launch_geometric(tid, mplan, *min_, *mout, prm, chans, true, status, st);
+      } else {
+        // photometric transforms leave masks unchanged: copy with an identity flip record
+        PrmList ident{nullptr, {}};
+        ident.one.tid = ALB_HFLIP;
+        ident.one.apply = 0;
+        rc = launch_geometric(ALB_HFLIP, mplan, *min_, *mout, ident, chans, true, status, st);
+      }
+      if (rc != ALB_OK) return rc;
     }
-    if (rc != ALB_OK) return rc;
   }
   if (boxes && bout && nbout) {
     alb_status rc = launch_boxes(n, prm, in, boxes, nbox, cap, single_n, bout, nbout, status, st);

@@ -158,7 +158,12 @@ struct PlanCheck {
   ImgList in;
   PrmList prm;
   int32_t* status;
+  int32_t filter_c;   // 0: all images; k > 0: only images with c == k; k < 0: only c != -k (others: no items, no error)
 };
+
+ALB_D bool plan_filtered_out(const PlanCheck& chk, const alb_image& im) {
+  return (chk.filter_c > 0 && im.c != chk.filter_c) || (chk.filter_c < 0 && im.c == -chk.filter_c);
+}
 alb_status launch_plan(const ImgList& out, int32_t n, int32_t target_bytes, int32_t* prefix,
                        int32_t* rows_per_item, const PlanCheck& chk, cudaStream_t st);
 

@@ -34,6 +34,7 @@ __global__ void k_plan(ImgList out, int32_t n, int32_t target, int32_t* __restri
       rows_per_item[i] = rb;
       const int bad = check_image_pair(chk.tid, chk.prm.get(i), chk.in.get(i), im, chk.want_c, chk.geometric);
       if (bad) { cnt = 0; dev_fail(chk.status, bad); }
+      if (plan_filtered_out(chk, im)) cnt = 0;
     }
     int32_t v = cnt;
 #pragma unroll
@@ -393,7 +394,7 @@ static alb_status launch_items(K kernel, const Plan& plan, const ImgList& in, co
 
 alb_status launch_geometric(int32_t tid, const Plan& plan, const ImgList& in, const ImgList& out,
                             const PrmList& prm, int32_t channels, bool mask, int32_t* status, cudaStream_t st) {
-  const PlanCheck chk{tid, mask ? 0 : channels, true, in, prm, status};
+  const PlanCheck chk{tid, mask ? 0 : channels, true, in, prm, status, mask ? (channels == 1 ? 1 : -1) : 0};
   const bool c3 = channels == 3, c1 = channels == 1;
   if (launch_stream_geometric(tid, plan, in, out, prm, channels, st) == ALB_OK) return ALB_OK;
   if (launch_tile_geometric(tid, plan, in, out, prm, channels, mask, chk, st) == ALB_OK) return ALB_OK;

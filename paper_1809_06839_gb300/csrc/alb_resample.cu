@@ -50,6 +50,7 @@ __global__ void k_plan_tiles(ImgList out, int32_t n, int32_t tile, int32_t* __re
       cnt = im.h > 0 && im.w > 0 ? tx * ty : 0;
       tiles_x[i] = tx > 0 ? tx : 1;
       if (check_image_pair(chk.tid, chk.prm.get(i), chk.in.get(i), im, chk.want_c, chk.geometric)) cnt = 0;
+      if (plan_filtered_out(chk, im)) cnt = 0;
     }
     int32_t v = cnt;
 #pragma unroll

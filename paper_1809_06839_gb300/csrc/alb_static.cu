@@ -82,7 +82,7 @@ extern "C" alb_status alb_apply_ragged_static(int32_t tid, int32_t n, const alb_
   // every scratch region is fully rewritten by the launches below (the plan by
   // k_plan, the tables by their build kernels, the histograms zeroed first),
   // so nothing left by an earlier call is read
-  const PlanCheck chk{tid, 3, is_geometric(tid), li, prm, dev_status};
+  const PlanCheck chk{tid, 3, is_geometric(tid), li, prm, dev_status, 0};
   rc = launch_plan(lo, n, kStaticItemBytes, prefix, rpi, chk, st);
   if (rc != ALB_OK) return rc;
   Plan plan{prefix, rpi, n};

@@ -253,3 +253,32 @@ def test_inconsistent_descriptors_are_rejected_on_device(dev):
     alb.alb_apply_ragged(alb.GAMMA, 1, alb.params_to_device([gp], dev), gin.dev, gout.dev, ws=ws, dev_status=status)
     torch.cuda.synchronize()
     assert int(status.item()) == alb.ALB_EINVAL
+
+
+@pytest.mark.parametrize("name", ["ShiftScaleRotate", "RandomSizedCrop512", "VerticalFlip", "Gamma"])
+def test_ragged_masks_with_mixed_channel_counts(dev, name):
+    """Ragged masks of 1 and 3 planes in one launch: single-plane masks take the
+    specialised kernels, the others the general ones; all match the oracle."""
+    oc = ALL[name]
+    sizes = [(120, 150), (97, 64), (200, 131)]
+    chans = [1, 3, 1]
+    rb = synth.ragged_noise(sizes, seed=6)
+    mshapes = [(h, w, c) for (h, w), c in zip(sizes, chans)]
+    masks = synth.empty_ragged(mshapes)
+    for i, (h, w) in enumerate(sizes):
+        planes = [synth.blob_mask(h, w, 10 * i + j, n_classes=5) for j in range(chans[i])]
+        masks.image(i).copy_(torch.stack(planes, dim=2))
+    ops = [O.sample_params(oc, 6, oc.tid, i, h, w) for i, (h, w) in enumerate(sizes)]
+    lps = [to_lib(p, alb) for p in ops]
+    din = DeviceBatch(to_device(rb, dev))
+    dout = output_batch(lps, rb.shapes, dev)
+    dmi = DeviceBatch(to_device(masks, dev))
+    dmo = mask_output_batch(lps, masks.shapes, dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    ws = alb.workspace(alb.alb_workspace_size(oc.tid, 3), dev)
+    alb.alb_apply_ragged(oc.tid, 3, alb.params_to_device(lps, dev), din.dev, dout.dev, dmi.dev, dmo.dev, ws=ws,
+                         dev_status=status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    for i in range(3):
+        assert np.array_equal(dmo.rb.image(i).cpu().numpy(), O.apply_mask(ops[i], masks.image(i).numpy())), i
