@@ -36,6 +36,13 @@ sys.path.insert(0, ROOT)
 
 METRIC = "images/s per transform & fused ragged-batch pipeline; HBM GB/s vs GB300 peak"
 UNIT = "images/s"
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per image of the
+# resampling kernel, from one ncu --set full capture of 256 images of the suite
+# workload (same H, W distribution), scaled per image; the roofline's traffic
+# figure is this times the images of one launch.  Only kernels whose code is
+# unchanged since that capture are listed.
+NCU_DRAM_BYTES_PER_IMAGE = {"Resize512": 1120982.0, "ShiftScaleRotate": 965409.0}
 SUITE_N, SUITE_LO, SUITE_HI = 2000, 333, 500
 FUSED_N, FUSED_LO, FUSED_HI = 4096, 256, 1024
 DET_N, DET_HW = 256, 1024
@@ -528,6 +535,8 @@ def main():
                                          gbs=round(gbs, 1), frac=round(gbs / hbm, 4))
     dom = max(suite.ops, key=lambda o: ops_t[o["name"]])
     achieved = dom["alg_bytes"] / ops_t[dom["name"]] / 1e9
+    traffic = NCU_DRAM_BYTES_PER_IMAGE.get(dom["name"])
+    traffic = None if traffic is None else round(traffic * suite.n)
     status = int(suite.status.item())
     host_images = [suite.inp.rb.image(i).cpu().numpy() for i in range(min(args.cpu_images, suite.n))]
     if args.skip_e2e:
@@ -566,7 +575,7 @@ def main():
                            "parallelism": f"replicas x{ws}, no collective"},
                 "roofline": {"bound": "hbm", "kernel": dom["name"], "achieved": round(achieved, 1),
                              "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / hbm, 4),
-                             "traffic": None},
+                             "traffic": traffic},
                 "per_transform": per_transform,
                 "clocks": clocks,
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": e2e["bi"],
