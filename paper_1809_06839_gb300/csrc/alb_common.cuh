@@ -99,6 +99,26 @@ ALB_D int32_t item_image(const Plan& p, int32_t item) {
   return lo;
 }
 
+// Walks the CTA's item range as runs of consecutive items of one image and
+// calls f(b, r0, r1) once per run: output rows [r0, r1) of image b (r1 is not
+// yet clamped to the image height).  A run is CTA-uniform, so f may hold
+// block barriers.  Long runs let the streaming loops keep several vector
+// loads in flight per thread instead of restarting every ~16 KB item.
+template <class F>
+ALB_D void for_each_run(const Plan& p, F&& f) {
+  int32_t it0, it1;
+  item_range(p, it0, it1);
+  if (it0 >= it1) return;
+  int32_t b = item_image(p, it0);
+  for (int32_t item = it0; item < it1;) {
+    while (item >= p.prefix[b + 1]) b++;
+    const int32_t end = p.prefix[b + 1] < it1 ? p.prefix[b + 1] : it1;
+    const int32_t rb = p.rows_per_item[b];
+    f(b, (item - p.prefix[b]) * rb, (end - p.prefix[b]) * rb);
+    item = end;
+  }
+}
+
 // ------------------------------------------------------------------ workspace carving
 struct Carve {
   char* base;

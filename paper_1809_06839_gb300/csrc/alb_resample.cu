@@ -34,7 +34,7 @@ struct WPitch {
 };
 
 // --------------------------------------------------------------- tile plan
-__global__ void k_plan_tiles(ImgList out, int32_t n, int32_t tile, int32_t* __restrict__ prefix,
+__global__ void k_plan_tiles(ImgList out, int32_t n, int32_t tile_w, int32_t tile_h, int32_t* __restrict__ prefix,
                              int32_t* __restrict__ tiles_x, PlanCheck chk) {
   __shared__ int32_t wsum[32];
   __shared__ int32_t carry;
@@ -46,7 +46,7 @@ __global__ void k_plan_tiles(ImgList out, int32_t n, int32_t tile, int32_t* __re
     int32_t cnt = 0;
     if (i < n) {
       const alb_image im = out.get(i);
-      const int32_t tx = (im.w + tile - 1) / tile, ty = (im.h + tile - 1) / tile;
+      const int32_t tx = (im.w + tile_w - 1) / tile_w, ty = (im.h + tile_h - 1) / tile_h;
       cnt = im.h > 0 && im.w > 0 ? tx * ty : 0;
       tiles_x[i] = tx > 0 ? tx : 1;
       if (check_image_pair(chk.tid, chk.prm.get(i), chk.in.get(i), im, chk.want_c, chk.geometric)) cnt = 0;
@@ -410,6 +410,233 @@ __global__ void __launch_bounds__(32 * NWARP, 5) k_resample_warp(Plan plan, ImgL
   cp_async_wait<0>();
 }
 
+// --------------------------------------------------------------- separable resize
+// Bilinear RGB resizes (Resize, RandomSizedCrop, RandomResizedCrop) use the
+// separability of the Q5 weights: out = ((32 - fy) h(iy) + fy h(iy + 1) + 512)
+// >> 10 with h(i) = (32 - fx) p(i, ix) + fx p(i, ix + 1) exact in integers, so
+// h of a source row is computed once per output column and reused by every
+// output row whose tap rows include it.  A warp owns a 32 x 16 output tile,
+// lane j = output column j; it walks the tile's rows top to bottom keeping the
+// two current tap rows' h in registers (for an enlargement most output rows
+// reuse both, or shift by one source row).  The tile's source box (up to
+// RB_X x RB_Y pixels: enlargements and reductions to ~0.95) is staged per warp
+// in shared memory by cp.async, double-buffered; the box is kept small so that
+// ~36 warps fit on an SM (the row chain is latency-bound).  Larger footprints
+// read their taps from global memory.
+constexpr int RT_W = 32, RT_H = 16;   // output tile (columns x rows)
+constexpr int RB_X = 36, RB_Y = 20;   // staged box (source pixels x rows)
+constexpr int RPITCH = 144;           // staged row pitch in bytes
+constexpr int RWARP = 4;              // warps per CTA
+static_assert(RPITCH % 16 == 0, "cp.async destinations must be 16-byte aligned");
+static_assert(RPITCH >= 15 + 3 * (RB_X - 1) + 12, "a tap read (3 words from the pair's word) stays in its row");
+static_assert(RB_Y >= 17 && RB_X >= RT_W + 2, "the box holds an unscaled tile");
+
+struct RImg {          // per-image values of a warp's current image (warp-uniform)
+  int32_t b, prefix, ntiles, tiles_x;
+  int32_t OH, OW, cw, ch, wx0, wy0;
+  const uint8_t* src;
+  uint8_t* dst;
+  int64_t sstride, dstride;
+};
+struct RTile {         // geometry of one tile
+  int32_t ox0, oy0, tw, th, bx0, by0, bw, bh, big;
+};
+
+ALB_D void r_load_img(const Plan& plan, const ImgList& in, const ImgList& out, const PrmList& prm, int32_t b,
+                      RImg& k) {
+  const alb_image si = in.get(b), so = out.get(b);
+  const alb_params& p = prm.get(b);
+  k.b = b; k.prefix = plan.prefix[b]; k.ntiles = plan.prefix[b + 1] - k.prefix; k.tiles_x = plan.rows_per_item[b];
+  k.OH = so.h; k.OW = so.w; k.cw = p.cw; k.ch = p.ch; k.wx0 = p.x0; k.wy0 = p.y0;
+  k.src = (const uint8_t*)si.data; k.dst = (uint8_t*)so.data;
+  k.sstride = si.row_stride; k.dstride = so.row_stride;
+}
+
+// Tile geometry; per lane: vcol = Q5 coordinate of tile column `lane`,
+// vrow = that of tile row `lane` (lanes < RT_H), both clamped to the tile.
+ALB_D void r_tile_geo(const RImg& k, int32_t item, int lane, RTile& g, int32_t& vcol, int32_t& vrow) {
+  const int32_t t = item - k.prefix, ty = t / k.tiles_x, tx = t - ty * k.tiles_x;
+  g.ox0 = tx * RT_W; g.oy0 = ty * RT_H;
+  g.tw = imin(RT_W, k.OW - g.ox0); g.th = imin(RT_H, k.OH - g.oy0);
+  vcol = rs_q5(g.ox0 + imin(lane, g.tw - 1), k.cw, k.OW);
+  vrow = rs_q5(g.oy0 + imin(lane & (RT_H - 1), g.th - 1), k.ch, k.OH);
+  const int32_t c0 = __shfl_sync(0xffffffffu, vcol, 0), c1 = __shfl_sync(0xffffffffu, vcol, g.tw - 1);
+  const int32_t r0 = __shfl_sync(0xffffffffu, vrow, 0), r1 = __shfl_sync(0xffffffffu, vrow, g.th - 1);
+  g.bx0 = c0 >> 5; g.by0 = r0 >> 5;
+  g.bw = imin((c1 >> 5) + 1, k.cw - 1) - g.bx0 + 1;
+  g.bh = imin((r1 >> 5) + 1, k.ch - 1) - g.by0 + 1;
+  g.big = g.bw > RB_X || g.bh > RB_Y;
+}
+
+// Lane r (and r + 32) stages box row r: raw aligned 16-byte chunks, phase kept.
+ALB_D void r_tile_stage(const RImg& k, const RTile& g, int lane, uint8_t* box, int16_t* phase) {
+  if (g.big) return;
+  const int span = 3 * g.bw;
+  for (int r = lane; r < g.bh; r += 32) {
+    const int sy = k.wy0 + g.by0 + r;            // by0 + bh - 1 <= ch - 1: inside the window
+    const uintptr_t first = reinterpret_cast<uintptr_t>(k.src) + (uintptr_t)((int64_t)sy * k.sstride) +
+                            (uintptr_t)(3 * (k.wx0 + g.bx0));
+    const uintptr_t c0 = first & ~uintptr_t(15);
+    const int ph = (int)(first - c0);
+    phase[r] = (int16_t)ph;
+    const int nch = (ph + span + 15) >> 4;
+    uint8_t* d = box + r * RPITCH;
+    for (int j = 0; j < nch; j++) cp_async16(d + 16 * j, reinterpret_cast<const void*>(c0 + 16 * j));
+  }
+}
+
+// h of one tap row for the three channels: (32 - fx) p(ix) + fx p(ix + 1).
+ALB_D void r_hrow(uint32_t lo, uint32_t hi, uint32_t wx, uint32_t (&h)[3]) {
+  h[0] = __dp4a(__byte_perm(lo, hi, 0x0030), wx, 0u);
+  h[1] = __dp4a(__byte_perm(lo, hi, 0x0041), wx, 0u);
+  h[2] = __dp4a(__byte_perm(lo, hi, 0x0052), wx, 0u);
+}
+
+ALB_D uint32_t r_vert(const uint32_t (&ha)[3], const uint32_t (&hb)[3], uint32_t wy) {
+  const uint32_t r = __dp2a_lo(__byte_perm(ha[0], hb[0], 0x5410), wy, 512u) >> 10;
+  const uint32_t g = __dp2a_lo(__byte_perm(ha[1], hb[1], 0x5410), wy, 512u) >> 10;
+  const uint32_t b = __dp2a_lo(__byte_perm(ha[2], hb[2], 0x5410), wy, 512u) >> 10;
+  return r | (g << 8) | (b << 16);
+}
+
+ALB_D void r_tile_compute(const RImg& k, const RTile& g, int lane, int32_t vcol, int32_t vrow,
+                          const uint8_t* __restrict__ box, const int16_t* __restrict__ ph) {
+  const int32_t fx = vcol & 31;
+  const uint32_t wx = (uint32_t)(32 - fx) | ((uint32_t)fx << 8);
+  const bool store = lane < g.tw;
+  uint8_t* od = k.dst + (int64_t)g.oy0 * k.dstride + 3 * (int64_t)(g.ox0 + lane);
+  uint32_t ha[3] = {0u, 0u, 0u}, hb[3] = {0u, 0u, 0u};
+  int32_t ia = -2;                                   // box row whose h is in ha (hb: the row below)
+  if (!g.big) {
+    const int32_t ocol = 3 * ((vcol >> 5) - g.bx0);
+    auto hrow = [&](int32_t i, uint32_t (&h)[3]) {
+      uint32_t lo, hi;
+      taps_row(box, i * RPITCH + ph[i] + ocol, lo, hi);
+      r_hrow(lo, hi, wx, h);
+    };
+    // at a clamped bottom edge the row below the last tap row is not staged
+    // and has weight fy = 0: the last staged row stands in for it
+    const int32_t last = g.bh - 1;
+    if (k.ch <= k.OH) {
+      // enlargement: the top tap row advances by 0 or 1 per output row, so
+      // one new h row per output row, selected without branches
+      {
+        const int32_t rq = __shfl_sync(0xffffffffu, vrow, 0);
+        ia = (rq >> 5) - g.by0;
+        hrow(ia, ha);
+        hrow(imin(ia + 1, last), hb);
+      }
+#pragma unroll 2
+      for (int r = 0; r < g.th; r++, od += k.dstride) {
+        const int32_t rq = __shfl_sync(0xffffffffu, vrow, r);
+        const int32_t iy = (rq >> 5) - g.by0, fy = rq & 31;
+        uint32_t hn[3];
+        hrow(imin(iy + 1, last), hn);
+        const bool adv = iy != ia;
+        ha[0] = adv ? hb[0] : ha[0]; ha[1] = adv ? hb[1] : ha[1]; ha[2] = adv ? hb[2] : ha[2];
+        hb[0] = hn[0]; hb[1] = hn[1]; hb[2] = hn[2];
+        ia = iy;
+        const uint32_t v = r_vert(ha, hb, (uint32_t)(32 - fy) | ((uint32_t)fy << 8));
+        if (store) { od[0] = (uint8_t)v; od[1] = (uint8_t)(v >> 8); od[2] = (uint8_t)(v >> 16); }
+      }
+    } else {
+      for (int r = 0; r < g.th; r++, od += k.dstride) {
+        const int32_t rq = __shfl_sync(0xffffffffu, vrow, r);
+        const int32_t iy = (rq >> 5) - g.by0, fy = rq & 31;
+        if (iy != ia) {                              // warp-uniform
+          if (iy == ia + 1) {
+            ha[0] = hb[0]; ha[1] = hb[1]; ha[2] = hb[2];
+          } else {
+            hrow(iy, ha);
+          }
+          hrow(imin(iy + 1, last), hb);
+          ia = iy;
+        }
+        const uint32_t v = r_vert(ha, hb, (uint32_t)(32 - fy) | ((uint32_t)fy << 8));
+        if (store) { od[0] = (uint8_t)v; od[1] = (uint8_t)(v >> 8); od[2] = (uint8_t)(v >> 16); }
+      }
+    }
+  } else {
+    // footprint larger than the box: taps straight from the source window
+    const int32_t sx0 = k.wx0 + (vcol >> 5), sx1 = k.wx0 + imin((vcol >> 5) + 1, k.cw - 1);
+    auto hrow = [&](int32_t sy, uint32_t (&h)[3]) {
+      const uint8_t* row = k.src + (int64_t)sy * k.sstride;
+      const uint32_t lo = (uint32_t)row[3 * sx0] | ((uint32_t)row[3 * sx0 + 1] << 8) |
+                          ((uint32_t)row[3 * sx0 + 2] << 16) | ((uint32_t)row[3 * sx1] << 24);
+      const uint32_t hi = (uint32_t)row[3 * sx1 + 1] | ((uint32_t)row[3 * sx1 + 2] << 8);
+      r_hrow(lo, hi, wx, h);
+    };
+    for (int r = 0; r < g.th; r++, od += k.dstride) {
+      const int32_t rq = __shfl_sync(0xffffffffu, vrow, r);
+      const int32_t iy = rq >> 5, fy = rq & 31;
+      if (iy != ia) {
+        hrow(k.wy0 + iy, ha);
+        hrow(k.wy0 + imin(iy + 1, k.ch - 1), hb);
+        ia = iy;
+      }
+      const uint32_t v = r_vert(ha, hb, (uint32_t)(32 - fy) | ((uint32_t)fy << 8));
+      if (store) { od[0] = (uint8_t)v; od[1] = (uint8_t)(v >> 8); od[2] = (uint8_t)(v >> 16); }
+    }
+  }
+}
+
+struct RShared {       // dynamic shared memory of k_resize_rows (above the 48 KB static limit)
+  uint8_t box[RWARP][2][RB_Y * RPITCH + 16];   // +16: the last row's tap read past the staged bytes
+  int16_t phase[RWARP][2][RB_Y];
+  RImg simg[RWARP][2];
+  RTile stile[RWARP][2];
+};
+
+__global__ void __launch_bounds__(32 * RWARP) k_resize_rows(Plan plan, ImgList in, ImgList out, PrmList prm) {
+  extern __shared__ __align__(16) uint8_t rs_dyn[];
+  RShared& sm = *reinterpret_cast<RShared*>(rs_dyn);
+  auto& box = sm.box;
+  auto& phase = sm.phase;
+  auto& simg = sm.simg;
+  auto& stile = sm.stile;
+  int32_t it0, it1;
+  item_range(plan, it0, it1);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int32_t item = it0 + w;
+  if (item >= it1) return;
+  int32_t ccol, crow;          // this lane's coordinates of the current tile
+  {
+    RImg k;
+    RTile g;
+    r_load_img(plan, in, out, prm, item_image(plan, item), k);
+    r_tile_geo(k, item, lane, g, ccol, crow);
+    if (lane == 0) { simg[w][0] = k; stile[w][0] = g; }
+    r_tile_stage(k, g, lane, box[w][0], phase[w][0]);
+  }
+  cp_async_commit();
+  int buf = 0;
+  for (; item < it1; item += RWARP, buf ^= 1) {
+    const int32_t nitem = item + RWARP;
+    int32_t ncol = 0, nrow = 0;
+    if (nitem < it1) {
+      __syncwarp();
+      RImg k = simg[w][buf];
+      if (nitem >= k.prefix + k.ntiles) {
+        int32_t b = k.b;
+        while (nitem >= plan.prefix[b + 1]) b++;
+        r_load_img(plan, in, out, prm, b, k);
+      }
+      RTile g;
+      r_tile_geo(k, nitem, lane, g, ncol, nrow);
+      __syncwarp();
+      if (lane == 0) { simg[w][buf ^ 1] = k; stile[w][buf ^ 1] = g; }
+      r_tile_stage(k, g, lane, box[w][buf ^ 1], phase[w][buf ^ 1]);
+    }
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncwarp();
+    r_tile_compute(simg[w][buf], stile[w][buf], lane, ccol, crow, box[w][buf], phase[w][buf]);
+    __syncwarp();      // every lane is done with box[buf] before it is refilled
+    ccol = ncol; crow = nrow;
+  }
+  cp_async_wait<0>();
+}
+
 // --------------------------------------------------------------- launcher
 template <class... KArgs, class... Args>
 static alb_status launch_k(void (*kern)(KArgs...), cudaStream_t st, Args... args) {
@@ -431,7 +658,18 @@ alb_status launch_tile_geometric(int32_t tid, const Plan& plan, const ImgList& i
   // the row plan's arrays are rewritten as a tile plan (stream-ordered)
   int32_t* prefix = const_cast<int32_t*>(plan.prefix);
   int32_t* tiles_x = const_cast<int32_t*>(plan.rows_per_item);
-  k_plan_tiles<<<1, 1024, 0, st>>>(out, plan.n, WT, prefix, tiles_x, chk);
+  if (resize && !mask) {
+    k_plan_tiles<<<1, 1024, 0, st>>>(out, plan.n, RT_W, RT_H, prefix, tiles_x, chk);
+    ALB_CUDA(cudaGetLastError());
+    const int smem = (int)sizeof(RShared);
+    ALB_CUDA(cudaFuncSetAttribute(k_resize_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_resize_rows, 32 * RWARP, smem);
+    k_resize_rows<<<(per_sm < 1 ? 1 : per_sm) * sm_count(), 32 * RWARP, smem, st>>>(plan, in, out, prm);
+    ALB_CUDA(cudaGetLastError());
+    return ALB_OK;
+  }
+  k_plan_tiles<<<1, 1024, 0, st>>>(out, plan.n, WT, WT, prefix, tiles_x, chk);
   ALB_CUDA(cudaGetLastError());
   if (affine) {
     if (mask) return launch_k(k_resample_warp<MAP_AFFINE, true, 1>, st, plan, in, out, prm);

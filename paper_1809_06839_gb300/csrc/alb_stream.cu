@@ -47,51 +47,48 @@ ALB_D void lut_px(const uint8_t* tab, int lb, uint32_t& r, uint32_t& g, uint32_t
   b = tab[lb + 16384 + lut_off(b)];
 }
 
+// 16 RGB pixels of one 48-byte unit through the three tables
+ALB_D void lut_unit(const uint8_t* tab, int lb, const U48& u, uint32_t (&o)[12]) {
+  uint32_t w[12];
+  words48(u, w);
+#pragma unroll
+  for (int m = 0; m < 12; m++) {
+    uint32_t acc = 0;
+#pragma unroll
+    for (int t = 0; t < 4; t++) {
+      const int k = 4 * m + t, c = k % 3;
+      acc |= (uint32_t)tab[lb + 8192 * c + lut_off((w[m] >> (8 * t)) & 0xFFu)] << (8 * t);
+    }
+    o[m] = acc;
+  }
+}
+
 __global__ void __launch_bounds__(256) k_lut_stream(Plan plan, ImgList in, ImgList out,
                                                     const uint8_t* __restrict__ luts) {
   __shared__ __align__(16) uint32_t tab32[kLutBytes / 4];
   __shared__ uint8_t sh768[768];
   const uint8_t* tab = reinterpret_cast<const uint8_t*>(tab32);
-  int32_t it0, it1;
-  item_range(plan, it0, it1);
-  if (it0 >= it1) return;
   const int lb = 4 * (threadIdx.x & 31);
-  int32_t b = item_image(plan, it0);
-  int32_t cached = -1;
-  for (int32_t item = it0; item < it1; item++) {
-    while (item >= plan.prefix[b + 1]) b++;
-    if (b != cached) {
-      __syncthreads();
-      build_lut_copies(luts + (int64_t)b * 768, sh768, tab32);
-      cached = b;
-    }
+  for_each_run(plan, [&](int32_t b, int32_t r0, int32_t r1) {
+    __syncthreads();
+    build_lut_copies(luts + (int64_t)b * 768, sh768, tab32);
     const alb_image si = in.get(b), so = out.get(b);
-    const int32_t rb = plan.rows_per_item[b];
-    const int32_t r0 = (item - plan.prefix[b]) * rb, r1 = imin(r0 + rb, so.h);
+    r1 = imin(r1, so.h);
     const uint8_t* __restrict__ ip = (const uint8_t*)si.data;
     uint8_t* __restrict__ op = (uint8_t*)so.data;
     if (flat_aligned(si) && flat_aligned(so)) {
       const int64_t a = (int64_t)r0 * so.w, e = (int64_t)r1 * so.w;   // pixel range
       const int64_t u0 = (a + 15) >> 4, u1 = e >> 4;                    // whole 16-pixel units
-      for (int64_t u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
-        const uint8_t* src = ip + 48 * u;
-        const uint4 v0 = ldg16(src), v1 = ldg16(src + 16), v2 = ldg16(src + 32);
-        const uint32_t w[12] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w, v2.x, v2.y, v2.z, v2.w};
+      // the next unit's three vectors are in flight while this one is looked up
+      int64_t u = u0 + threadIdx.x;
+      U48 nx;
+      if (u < u1) ld48(ip + 48 * u, nx);
+      for (; u < u1; u += blockDim.x) {
+        const U48 cur = nx;
+        if (u + blockDim.x < u1) ld48(ip + 48 * (u + blockDim.x), nx);
         uint32_t o[12];
-#pragma unroll
-        for (int m = 0; m < 12; m++) {
-          uint32_t acc = 0;
-#pragma unroll
-          for (int t = 0; t < 4; t++) {
-            const int k = 4 * m + t, c = k % 3;
-            acc |= (uint32_t)tab[lb + 8192 * c + lut_off((w[m] >> (8 * t)) & 0xFFu)] << (8 * t);
-          }
-          o[m] = acc;
-        }
-        uint8_t* dst = op + 48 * u;
-        stg16(dst, make_uint4(o[0], o[1], o[2], o[3]));
-        stg16(dst + 16, make_uint4(o[4], o[5], o[6], o[7]));
-        stg16(dst + 32, make_uint4(o[8], o[9], o[10], o[11]));
+        lut_unit(tab, lb, cur, o);
+        st48(op + 48 * u, o);
       }
       const int64_t h1 = u0 * 16 < e ? u0 * 16 : e;
       for (int64_t q = a + threadIdx.x; q < e; q += blockDim.x) {
@@ -111,7 +108,7 @@ __global__ void __launch_bounds__(256) k_lut_stream(Plan plan, ImgList in, ImgLi
         d[0] = (uint8_t)R; d[1] = (uint8_t)G; d[2] = (uint8_t)B;
       }
     }
-  }
+  });
 }
 
 // ================================================================== per-pixel ops
@@ -163,17 +160,27 @@ ALB_D void pixel_op(uint32_t& r, uint32_t& g, uint32_t& b, float dh2, float ds, 
 }
 
 template <int OP>
+ALB_D void pixel_unit(const U48& u, uint32_t (&o)[12], float dh2, float ds, float dv) {
+  uint32_t w[12];
+  words48(u, w);
+#pragma unroll
+  for (int m = 0; m < 12; m++) o[m] = 0;
+#pragma unroll
+  for (int px = 0; px < 16; px++) {
+    uint32_t R = byte_of(w, 3 * px), G = byte_of(w, 3 * px + 1), B = byte_of(w, 3 * px + 2);
+    pixel_op<OP>(R, G, B, dh2, ds, dv);
+    o[(3 * px) >> 2] |= R << (8 * ((3 * px) & 3));
+    o[(3 * px + 1) >> 2] |= G << (8 * ((3 * px + 1) & 3));
+    o[(3 * px + 2) >> 2] |= B << (8 * ((3 * px + 2) & 3));
+  }
+}
+
+template <int OP>
 __global__ void __launch_bounds__(256) k_pixel_stream(Plan plan, ImgList in, ImgList out, PrmList prm) {
-  int32_t it0, it1;
-  item_range(plan, it0, it1);
-  if (it0 >= it1) return;
-  int32_t b = item_image(plan, it0);
-  for (int32_t item = it0; item < it1; item++) {
-    while (item >= plan.prefix[b + 1]) b++;
+  for_each_run(plan, [&](int32_t b, int32_t r0, int32_t r1) {
     const alb_image si = in.get(b), so = out.get(b);
     const alb_params& p = prm.get(b);
-    const int32_t rb = plan.rows_per_item[b];
-    const int32_t r0 = (item - plan.prefix[b]) * rb, r1 = imin(r0 + rb, so.h);
+    r1 = imin(r1, so.h);
     const bool act = p.apply != 0;
     const float dh2 = (float)(2.0 * p.shift[0]), ds = (float)(p.shift[1] / 255.0), dv = (float)(p.shift[2] / 255.0);
     const uint8_t* __restrict__ ip = (const uint8_t*)si.data;
@@ -181,34 +188,23 @@ __global__ void __launch_bounds__(256) k_pixel_stream(Plan plan, ImgList in, Img
     if (flat_aligned(si) && flat_aligned(so)) {
       const int64_t a = (int64_t)r0 * so.w, e = (int64_t)r1 * so.w;   // pixel range
       const int64_t u0 = (a + 15) >> 4, u1 = e >> 4;                    // whole 16-pixel units
-      for (int64_t u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
-        const uint8_t* src = ip + 48 * u;
-        uint4 v0 = ldg16(src), v1 = ldg16(src + 16), v2 = ldg16(src + 32);
+      int64_t u = u0 + threadIdx.x;
+      U48 nx;
+      if (u < u1) ld48(ip + 48 * u, nx);
+      for (; u < u1; u += blockDim.x) {
+        const U48 cur = nx;
+        if (u + blockDim.x < u1) ld48(ip + 48 * (u + blockDim.x), nx);
+        uint32_t o[12];
         if (act) {
-          uint32_t w[12] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w, v2.x, v2.y, v2.z, v2.w};
-          uint32_t o[12] = {0};
-#pragma unroll
-          for (int px = 0; px < 16; px++) {
-            uint32_t R = byte_of(w, 3 * px), G = byte_of(w, 3 * px + 1), B = byte_of(w, 3 * px + 2);
-            pixel_op<OP>(R, G, B, dh2, ds, dv);
-            o[(3 * px) >> 2] |= R << (8 * ((3 * px) & 3));
-            o[(3 * px + 1) >> 2] |= G << (8 * ((3 * px + 1) & 3));
-            o[(3 * px + 2) >> 2] |= B << (8 * ((3 * px + 2) & 3));
-          }
-          v0 = make_uint4(o[0], o[1], o[2], o[3]);
-          v1 = make_uint4(o[4], o[5], o[6], o[7]);
-          v2 = make_uint4(o[8], o[9], o[10], o[11]);
+          pixel_unit<OP>(cur, o, dh2, ds, dv);
+        } else {
+          words48(cur, o);
         }
-        uint8_t* dst = op + 48 * u;
-        stg16(dst, v0); stg16(dst + 16, v1); stg16(dst + 32, v2);
+        st48(op + 48 * u, o);
       }
       const int64_t h1 = u0 * 16 < e ? u0 * 16 : e;
-      for (int64_t q = a + threadIdx.x; q < h1; q += blockDim.x) {
-        uint32_t R = ip[3 * q], G = ip[3 * q + 1], B = ip[3 * q + 2];
-        if (act) pixel_op<OP>(R, G, B, dh2, ds, dv);
-        op[3 * q] = (uint8_t)R; op[3 * q + 1] = (uint8_t)G; op[3 * q + 2] = (uint8_t)B;
-      }
-      for (int64_t q = (u1 * 16 > h1 ? u1 * 16 : h1) + threadIdx.x; q < e; q += blockDim.x) {
+      for (int64_t q = a + threadIdx.x; q < e; q += blockDim.x) {
+        if (q >= h1 && q < u1 * 16) continue;
         uint32_t R = ip[3 * q], G = ip[3 * q + 1], B = ip[3 * q + 2];
         if (act) pixel_op<OP>(R, G, B, dh2, ds, dv);
         op[3 * q] = (uint8_t)R; op[3 * q + 1] = (uint8_t)G; op[3 * q + 2] = (uint8_t)B;
@@ -224,81 +220,172 @@ __global__ void __launch_bounds__(256) k_pixel_stream(Plan plan, ImgList in, Img
         d[0] = (uint8_t)R; d[1] = (uint8_t)G; d[2] = (uint8_t)B;
       }
     }
+  });
+}
+
+// ================================================================== pixel maps
+// HorizontalFlip, VerticalFlip, RandomCrop and PadToSize on RGB images: output
+// pixel (y, x) is source pixel (src_y(y), src_x(x)), with src_x of slope +1
+// or -1 between reflection points.  Flat 16-pixel output units (48 aligned
+// bytes): when src_x over the unit's 16 pixels is one run of slope +1 the
+// unit is a 48-byte source window (realigned with funnel shifts); slope -1 is
+// the same window with the pixel order reversed in registers; a unit that
+// holds a reflection point or a row end takes the per-pixel path.  The next
+// unit's window loads are issued before the current unit is assembled.
+template <int TID>
+struct PixMap {
+  int32_t H, W, x0, y0;
+  bool act;
+  ALB_D int32_t sy(int32_t y) const {
+    if (!act) return y;
+    if (TID == ALB_VFLIP) return H - 1 - y;
+    if (TID == ALB_RANDOM_CROP) return y0 + y;
+    if (TID == ALB_PAD_TO_SIZE) return reflect101(y - y0, H);
+    return y;
+  }
+  ALB_D int32_t sx(int32_t x) const {
+    if (!act) return x;
+    if (TID == ALB_HFLIP) return W - 1 - x;
+    if (TID == ALB_RANDOM_CROP) return x0 + x;
+    if (TID == ALB_PAD_TO_SIZE) return reflect101(x - x0, W);
+    return x;
+  }
+  // How output pixels x .. x + 15 map: 0 = source pixels start .. start + 15,
+  // 1 = the same 16 pixels in reverse order, 2 = neither (a reflection point)
+  ALB_D int run16(int32_t x, int32_t& start) const {
+    start = x;
+    if (!act) return 0;
+    if (TID == ALB_HFLIP) { start = W - 16 - x; return 1; }
+    if (TID == ALB_RANDOM_CROP) { start = x0 + x; return 0; }
+    if (TID == ALB_PAD_TO_SIZE) {
+      const int32_t d = x - x0;
+      if (d >= 0 && d + 15 < W) { start = d; return 0; }
+      if (d + 15 < 0 && d > -W) { start = -(d + 15); return 1; }                   // left border, one fold
+      if (d >= W && d + 15 <= 2 * W - 2) { start = 2 * (W - 1) - (d + 15); return 1; }  // right border, one fold
+      return 2;
+    }
+    return 0;
+  }
+};
+
+ALB_HD constexpr int rev_src(int k) { return 3 * (15 - k / 3) + k % 3; }
+ALB_HD constexpr int rev_word(int k, int j) { return rev_src(4 * k + j) >> 2; }
+ALB_HD constexpr int rev_lo(int k) {
+  int lo = rev_word(k, 0);
+  for (int j = 1; j < 4; j++) lo = rev_word(k, j) < lo ? rev_word(k, j) : lo;
+  return lo;
+}
+
+// The 16 RGB pixels of a 48-byte window in reverse order, channel order kept.
+// Output word k takes its bytes from at most three consecutive source words:
+// one byte permute of the first two, a second one for the third.
+ALB_D void reverse16(const uint32_t (&win)[12], uint32_t (&o)[12]) {
+#pragma unroll
+  for (int k = 0; k < 12; k++) {
+    const int lo = rev_lo(k);
+    uint32_t sel1 = 0, sel2 = 0;
+    bool three = false;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      const int d = rev_word(k, j) - lo, byte = rev_src(4 * k + j) & 3;
+      if (d <= 1) {
+        sel1 |= (uint32_t)(4 * d + byte) << (4 * j);
+        sel2 |= (uint32_t)j << (4 * j);
+      } else {
+        three = true;
+        sel2 |= (uint32_t)(4 + byte) << (4 * j);
+      }
+    }
+    const uint32_t a = __byte_perm(win[lo], win[lo + 1 < 12 ? lo + 1 : 11], sel1);
+    o[k] = three ? __byte_perm(a, win[lo + 2 < 12 ? lo + 2 : 11], sel2) : a;
   }
 }
 
-// ================================================================== horizontal flip
-// Flat 16-pixel units: a unit inside one row reads the mirrored 16 pixels of
-// the same row (a 48-byte window, misaligned by a per-row constant), reverses
-// the pixel order in registers and stores 3 aligned vectors.
-ALB_D constexpr int rev_src(int k) { return 3 * (15 - k / 3) + k % 3; }
-
-__global__ void __launch_bounds__(256) k_hflip_stream(Plan plan, ImgList in, ImgList out, PrmList prm) {
-  int32_t it0, it1;
-  item_range(plan, it0, it1);
-  if (it0 >= it1) return;
-  int32_t b = item_image(plan, it0);
-  for (int32_t item = it0; item < it1; item++) {
-    while (item >= plan.prefix[b + 1]) b++;
+template <int TID>
+__global__ void __launch_bounds__(256, 3) k_pixmap3(Plan plan, ImgList in, ImgList out, PrmList prm) {
+  for_each_run(plan, [&](int32_t b, int32_t r0, int32_t r1) {
     const alb_image si = in.get(b), so = out.get(b);
     const alb_params& p = prm.get(b);
-    const int32_t rb = plan.rows_per_item[b];
-    const int32_t r0 = (item - plan.prefix[b]) * rb, r1 = imin(r0 + rb, so.h);
-    const int32_t W = so.w;
-    const bool act = p.apply != 0;
+    r1 = imin(r1, so.h);
+    PixMap<TID> m{si.h, si.w, p.x0, p.y0, p.apply != 0};
+    const int32_t OW = so.w;
     const uint8_t* __restrict__ ip = (const uint8_t*)si.data;
     uint8_t* __restrict__ op = (uint8_t*)so.data;
-    if (flat_aligned(si) && flat_aligned(so)) {
-      const int64_t a = (int64_t)r0 * W, e = (int64_t)r1 * W;
-      const int64_t u0 = (a + 15) >> 4, u1 = e >> 4;
-      for (int64_t u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
-        const int64_t p0 = 16 * u;
-        const int32_t y = (int32_t)((uint32_t)p0 / (uint32_t)W), x0 = (int32_t)(p0 - (int64_t)y * W);
-        uint8_t* dst = op + 48 * u;
-        if (!act) {
-          stg16(dst, ldg16(ip + 48 * u)); stg16(dst + 16, ldg16(ip + 48 * u + 16));
-          stg16(dst + 32, ldg16(ip + 48 * u + 32));
-        } else if (x0 + 16 <= W) {
-          const int64_t s0 = (int64_t)y * W + (W - 16 - x0);      // first source pixel
-          uint32_t win[12];
-          load_window<12>(ip + 3 * s0, win);
-          uint32_t o[12];
-#pragma unroll
-          for (int m = 0; m < 12; m++) {
-            o[m] = byte_of(win, rev_src(4 * m)) | (byte_of(win, rev_src(4 * m + 1)) << 8) |
-                   (byte_of(win, rev_src(4 * m + 2)) << 16) | (byte_of(win, rev_src(4 * m + 3)) << 24);
-          }
-          stg16(dst, make_uint4(o[0], o[1], o[2], o[3]));
-          stg16(dst + 16, make_uint4(o[4], o[5], o[6], o[7]));
-          stg16(dst + 32, make_uint4(o[8], o[9], o[10], o[11]));
-        } else {      // the unit straddles a row end (rows y, y + 1, ...)
-          int32_t yy = y, xx = x0;
-#pragma unroll 4
-          for (int j = 0; j < 16; j++) {
-            const uint8_t* s = ip + 3 * ((int64_t)yy * W + (W - 1 - xx));
-            dst[3 * j] = s[0]; dst[3 * j + 1] = s[1]; dst[3 * j + 2] = s[2];
-            if (++xx == W) { xx = 0; yy++; }
-          }
-        }
-      }
-      // pixels of the item outside whole units
-      const int64_t h1 = u0 * 16 < e ? u0 * 16 : e;
-      for (int64_t q = a + threadIdx.x; q < e; q += blockDim.x) {
-        if (q >= h1 && q < u1 * 16) continue;
-        const int32_t yy = (int32_t)((uint32_t)q / (uint32_t)W), xx = (int32_t)(q - (int64_t)yy * W);
-        const uint8_t* s = ip + 3 * ((int64_t)yy * W + (act ? W - 1 - xx : xx));
-        op[3 * q] = s[0]; op[3 * q + 1] = s[1]; op[3 * q + 2] = s[2];
-      }
-    } else {
-      const int64_t npx = (int64_t)(r1 - r0) * W;
+    const int64_t ss = si.row_stride;
+    auto src_px = [&](int32_t y, int32_t x) { return ip + (int64_t)m.sy(y) * ss + 3 * (int64_t)m.sx(x); };
+    if (!flat_aligned(so)) {
+      const int64_t npx = (int64_t)(r1 - r0) * OW;
       for (int64_t i = threadIdx.x; i < npx; i += blockDim.x) {
-        const int32_t y = r0 + (int32_t)(i / W), x = (int32_t)(i % W);
-        const uint8_t* s = ip + (int64_t)y * si.row_stride + 3 * (int64_t)(act ? W - 1 - x : x);
+        const int32_t y = r0 + (int32_t)(i / OW), x = (int32_t)(i % OW);
+        const uint8_t* s = src_px(y, x);
         uint8_t* d = op + (int64_t)y * so.row_stride + 3 * (int64_t)x;
         d[0] = s[0]; d[1] = s[1]; d[2] = s[2];
       }
+      return;
     }
-  }
+    const int64_t a = (int64_t)r0 * OW, e = (int64_t)r1 * OW;
+    const int64_t u0 = (a + 15) >> 4, u1 = e >> 4;
+    // kind 0: forward window, 1: reversed window, 2: per pixel
+    auto fetch = [&](int64_t u, RawWin<12>& rw, int& kind) {
+      int32_t y, x;
+      flat_rc(16 * u, OW, y, x);
+      kind = 2;
+      if (x + 16 > OW) return;
+      int32_t start;
+      kind = m.run16(x, start);
+      if (kind == 2) return;
+      raw_load<12>(ip + (int64_t)m.sy(y) * ss + 3 * (int64_t)start, rw);
+    };
+    // every lane of a warp runs the same iterations (the bound is tested per
+    // lane), so the warp can take its per-pixel units together
+    const int lane = threadIdx.x & 31;
+    int64_t ub = u0;
+    RawWin<12> nx;
+    int nkind = 2;
+    if (ub + threadIdx.x < u1) fetch(ub + threadIdx.x, nx, nkind);
+    for (; ub < u1; ub += blockDim.x) {
+      const int64_t u = ub + threadIdx.x;
+      const bool valid = u < u1;
+      const RawWin<12> cur = nx;
+      const int kind = nkind;
+      if (u + blockDim.x < u1) fetch(u + blockDim.x, nx, nkind);
+      if (valid && kind != 2) {
+        uint32_t win[12], o[12];
+        raw_align<12>(cur, win);
+        if (kind == 0) {
+#pragma unroll
+          for (int k = 0; k < 12; k++) o[k] = win[k];
+        } else {
+          reverse16(win, o);
+        }
+        st48(op + 48 * u, o);
+      }
+      // units with a reflection point or a row end inside: lanes 0..15 take
+      // one pixel each of every such unit of the warp
+      uint32_t todo = __ballot_sync(0xffffffffu, valid && kind == 2);
+      while (todo) {
+        const int src = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const int64_t su = __shfl_sync(0xffffffffu, u, src);
+        if (lane < 16) {
+          int32_t y, x;
+          flat_rc(16 * su + lane, OW, y, x);
+          const uint8_t* s = src_px(y, x);
+          uint8_t* d = op + 48 * su + 3 * lane;
+          d[0] = s[0]; d[1] = s[1]; d[2] = s[2];
+        }
+      }
+    }
+    // pixels of the run outside whole units
+    const int64_t h1 = u0 * 16 < e ? u0 * 16 : e;
+    for (int64_t q = a + threadIdx.x; q < e; q += blockDim.x) {
+      if (q >= h1 && q < u1 * 16) continue;
+      int32_t y, x;
+      flat_rc(q, OW, y, x);
+      const uint8_t* s = src_px(y, x);
+      op[3 * q] = s[0]; op[3 * q + 1] = s[1]; op[3 * q + 2] = s[2];
+    }
+  });
 }
 
 // ================================================================== row copies
@@ -384,63 +471,53 @@ __global__ void __launch_bounds__(256) k_rowcopy(Plan plan, ImgList in, ImgList 
 __global__ void __launch_bounds__(256) k_hist_stream(Plan plan, ImgList in, uint32_t* __restrict__ hist) {
   constexpr int NWARP = 8;
   __shared__ uint32_t sh[NWARP][768];
-  int32_t it0, it1;
-  item_range(plan, it0, it1);
-  if (it0 >= it1) return;
-  const int wid = threadIdx.x >> 5;
-  uint32_t* my = sh[wid];
-  int32_t b = item_image(plan, it0);
-  int32_t cur = b;
+  uint32_t* my = sh[threadIdx.x >> 5];
   for (int i = threadIdx.x; i < NWARP * 768; i += blockDim.x) (&sh[0][0])[i] = 0;
   __syncthreads();
-  auto flush = [&](int32_t img) {
-    __syncthreads();
-    for (int i = threadIdx.x; i < 768; i += blockDim.x) {
-      uint32_t s = 0;
-#pragma unroll
-      for (int w = 0; w < NWARP; w++) { s += sh[w][i]; sh[w][i] = 0; }
-      if (s) atomicAdd(&hist[(int64_t)img * 768 + i], s);
-    }
-    __syncthreads();
-  };
-  for (int32_t item = it0; item < it1; item++) {
-    while (item >= plan.prefix[b + 1]) b++;
-    if (b != cur) { flush(cur); cur = b; }
+  for_each_run(plan, [&](int32_t b, int32_t r0, int32_t r1) {
     const alb_image si = in.get(b);
-    const int32_t rb = plan.rows_per_item[b];
-    const int32_t r0 = (item - plan.prefix[b]) * rb, r1 = imin(r0 + rb, si.h);
+    r1 = imin(r1, si.h);
     const uint8_t* __restrict__ ip = (const uint8_t*)si.data;
-    const int64_t L = (int64_t)si.w * 3;
     if (flat_aligned(si)) {
-      const int64_t a = r0 * L, e = r1 * L;
-      const int64_t c0 = (a + 15) >> 4, c1 = e >> 4;
-      for (int64_t k = c0 + threadIdx.x; k < c1; k += blockDim.x) {
-        const uint4 v = ldg16(ip + 16 * k);
-        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-        int c = (int)(k % 3);
+      // 48-byte units start on a pixel: byte k of a unit is channel k % 3
+      const int64_t a = (int64_t)r0 * si.w, e = (int64_t)r1 * si.w;
+      const int64_t u0 = (a + 15) >> 4, u1 = e >> 4;
+      int64_t u = u0 + threadIdx.x;
+      U48 nx;
+      if (u < u1) ld48(ip + 48 * u, nx);
+      for (; u < u1; u += blockDim.x) {
+        const U48 cur = nx;
+        if (u + blockDim.x < u1) ld48(ip + 48 * (u + blockDim.x), nx);
+        uint32_t w[12];
+        words48(cur, w);
 #pragma unroll
-        for (int j = 0; j < 4; j++)
-#pragma unroll
-          for (int t = 0; t < 4; t++) {
-            atomicAdd(&my[256 * c + ((w[j] >> (8 * t)) & 0xFFu)], 1u);
-            c = c == 2 ? 0 : c + 1;
-          }
+        for (int k = 0; k < 48; k++) atomicAdd(&my[256 * (k % 3) + byte_of(w, k)], 1u);
       }
-      const int64_t h1 = 16 * c0 < e ? 16 * c0 : e;
-      for (int64_t i = a + threadIdx.x; i < e; i += blockDim.x) {
-        if (i >= h1 && i < 16 * c1) continue;
-        atomicAdd(&my[256 * (int)(i % 3) + ip[i]], 1u);
+      const int64_t h1 = u0 * 16 < e ? u0 * 16 : e;
+      for (int64_t q = a + threadIdx.x; q < e; q += blockDim.x) {
+        if (q >= h1 && q < u1 * 16) continue;
+#pragma unroll
+        for (int c = 0; c < 3; c++) atomicAdd(&my[256 * c + ip[3 * q + c]], 1u);
       }
     } else {
-      const int64_t n = (int64_t)(r1 - r0) * L;
-      for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-        const int32_t y = r0 + (int32_t)(i / L);
-        const int64_t x = i - (int64_t)(y - r0) * L;
-        atomicAdd(&my[256 * (int)(x % 3) + ip[(int64_t)y * si.row_stride + x]], 1u);
+      const int64_t npx = (int64_t)(r1 - r0) * si.w;
+      for (int64_t i = threadIdx.x; i < npx; i += blockDim.x) {
+        const int32_t y = r0 + (int32_t)(i / si.w), x = (int32_t)(i % si.w);
+        const uint8_t* s = ip + (int64_t)y * si.row_stride + 3 * (int64_t)x;
+#pragma unroll
+        for (int c = 0; c < 3; c++) atomicAdd(&my[256 * c + s[c]], 1u);
       }
     }
-  }
-  flush(cur);
+    // one image per run: merge the warps' copies into its global histogram
+    __syncthreads();
+    for (int i = threadIdx.x; i < 768; i += blockDim.x) {
+      uint32_t sum = 0;
+#pragma unroll
+      for (int w = 0; w < NWARP; w++) { sum += sh[w][i]; sh[w][i] = 0; }
+      if (sum) atomicAdd(&hist[(int64_t)b * 768 + i], sum);
+    }
+    __syncthreads();
+  });
 }
 
 // ================================================================== launchers
@@ -461,20 +538,23 @@ static alb_status launch_k(void (*kern)(KArgs...), cudaStream_t st, Args... args
 // transform/channel combination has none, so the caller uses its general kernel.
 alb_status launch_stream_geometric(int32_t tid, const Plan& plan, const ImgList& in, const ImgList& out,
                                    const PrmList& prm, int32_t channels, cudaStream_t st) {
+  if (channels == 3) {
+    switch (tid) {
+      case ALB_HFLIP: return launch_k(k_pixmap3<ALB_HFLIP>, st, plan, in, out, prm);
+      case ALB_VFLIP: return launch_k(k_pixmap3<ALB_VFLIP>, st, plan, in, out, prm);
+      case ALB_RANDOM_CROP: return launch_k(k_pixmap3<ALB_RANDOM_CROP>, st, plan, in, out, prm);
+      case ALB_PAD_TO_SIZE: return launch_k(k_pixmap3<ALB_PAD_TO_SIZE>, st, plan, in, out, prm);
+      default: break;
+    }
+  }
   switch (tid) {
-    case ALB_HFLIP:
-      if (channels == 3) return launch_k(k_hflip_stream, st, plan, in, out, prm);
-      break;
     case ALB_VFLIP:
-      if (channels == 3) return launch_k(k_rowcopy<3, ALB_VFLIP>, st, plan, in, out, prm);
       if (channels == 1) return launch_k(k_rowcopy<1, ALB_VFLIP>, st, plan, in, out, prm);
       return launch_k(k_rowcopy<0, ALB_VFLIP>, st, plan, in, out, prm);
     case ALB_RANDOM_CROP:
-      if (channels == 3) return launch_k(k_rowcopy<3, ALB_RANDOM_CROP>, st, plan, in, out, prm);
       if (channels == 1) return launch_k(k_rowcopy<1, ALB_RANDOM_CROP>, st, plan, in, out, prm);
       return launch_k(k_rowcopy<0, ALB_RANDOM_CROP>, st, plan, in, out, prm);
     case ALB_PAD_TO_SIZE:
-      if (channels == 3) return launch_k(k_rowcopy<3, ALB_PAD_TO_SIZE>, st, plan, in, out, prm);
       if (channels == 1) return launch_k(k_rowcopy<1, ALB_PAD_TO_SIZE>, st, plan, in, out, prm);
       return launch_k(k_rowcopy<0, ALB_PAD_TO_SIZE>, st, plan, in, out, prm);
     default:
