@@ -46,6 +46,7 @@ NCU_DRAM_BYTES_PER_IMAGE = {"Resize512": 1120982.0, "ShiftScaleRotate": 965409.0
 SUITE_N, SUITE_LO, SUITE_HI = 2000, 333, 500
 FUSED_N, FUSED_LO, FUSED_HI = 4096, 256, 1024
 DET_N, DET_HW = 256, 1024
+LARGE_N = 512
 DIFF_B, DIFF_HW = 256, 512
 SEED = 1809
 
@@ -152,14 +153,15 @@ def ev_time(fn, stream, reps=1):
 class Suite:
     """The per-transform suite on one GPU: resident inputs, per-op params/outputs."""
 
-    def __init__(self, dev, rank=0, n=SUITE_N, only=None):
+    def __init__(self, dev, rank=0, n=SUITE_N, only=None, lo=None, hi=None):
         from paper_1809_06839_gb300 import alb as A, synth
         from paper_1809_06839_gb300.ragged import DeviceBatch, output_batch
         self.A = A
         self.dev = dev
         self.n = n
         self.seed = SEED + rank
-        self.sizes = synth.uniform_sizes(n, SUITE_LO, SUITE_HI, seed=SEED + rank)
+        self.sizes = synth.uniform_sizes(n, SUITE_LO if lo is None else lo, SUITE_HI if hi is None else hi,
+                                         seed=SEED + rank)
         self.inp = DeviceBatch(synth.ragged_noise(self.sizes, seed=SEED + rank, device=dev))
         self.ops = []
         for name, tid, kw in suite_table():
@@ -285,7 +287,10 @@ def fused_pipeline(dev, stream, steps=3, warmup=2, n=FUSED_N):
         A.alb_sample_params_batch(cfg, SEED, 20, 0, FUSED_N, din.dev, pdev, stream=stream)
         A.alb_apply_batch(ccfg, FUSED_N, pdev, din.dev, out, mode, ws, stream=stream)
 
-    res = {}
+    # schedule chosen by the library's autotuner on this batch (outside the
+    # timed region); ccfg keeps zero fields, so the fused runs use the cached pick
+    best = A.alb_autotune_batch(ccfg, FUSED_N, pdev, din.dev, out, wsf, reps=3, stream=stream)
+    res = {"schedule": {"rows_per_item": best.tile_h, "ctas_per_sm": best.ctas_per_sm, "by": "alb_autotune_batch"}}
     for name, mode, ws in (("fused", A.MODE_FUSED, wsf), ("plain", A.MODE_PLAIN, wsp)):
         for _ in range(warmup):
             run(mode, ws)
@@ -311,6 +316,23 @@ def fused_pipeline(dev, stream, steps=3, warmup=2, n=FUSED_N):
     res["speedup_vs_plain"] = res["plain"]["ms"] / res["fused"]["ms"]
     res["workload"] = "4096 ragged u8 RGB images H,W~U[256,1024] -> RRC 224 + flip + jitter + Normalize bf16 NCHW"
     del din, out, wsf, wsp
+    torch.cuda.empty_cache()
+    return res
+
+
+def large_suite(dev, stream, hbm, n=LARGE_N):
+    """The same 15 transforms on images of at least 512 x 512 (H, W ~ U[512, 1024]),
+    the size class the HBM-fraction target refers to."""
+    s = Suite(dev, 0, n=n, lo=512, hi=1024)
+    t = per_op_times(s, stream, reps=5)
+    res = {}
+    for op in s.ops:
+        to = t[op["name"]]
+        gbs = op["alg_bytes"] / to / 1e9
+        res[op["name"]] = dict(images_per_s=round(n / to, 1), ms=round(to * 1e3, 4), gbs=round(gbs, 1),
+                               frac=round(gbs / hbm, 4))
+    res["workload"] = f"{n} u8 RGB images H,W~U[512,1024], each transform alone (one ragged launch)"
+    del s
     torch.cuda.empty_cache()
     return res
 
@@ -496,7 +518,7 @@ def main():
     ap.add_argument("--only", default="", help="comma-separated suite transforms (profiling runs)")
     ap.add_argument("--n", type=int, default=SUITE_N, help="suite images (profiling runs)")
     ap.add_argument("--skip-e2e", action="store_true")
-    ap.add_argument("--extras", default="fused,detection,differentiable",
+    ap.add_argument("--extras", default="fused,detection,differentiable,large",
                     help="sub-workloads to run after the suite (comma-separated)")
     ap.add_argument("--fused-n", type=int, default=FUSED_N, help="images of the fused workload (profiling runs)")
     args = ap.parse_args()
@@ -558,6 +580,8 @@ def main():
             extra["detection"] = detection(dev, stream)
         if "differentiable" in which:
             extra["differentiable"] = differentiable(dev, stream)
+        if "large" in which:
+            extra["per_transform_large"] = large_suite(dev, stream, hbm)
     cpu = None
     if rank == 0 and ws == 1 and args.cpu_images > 0:
         # the oracle on the same resident workload, copied to the host

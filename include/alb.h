@@ -133,8 +133,12 @@ typedef struct alb_chain_cfg {
   int32_t out_h, out_w;  /* output size (224 x 224 for the ImageNet-style chain) */
   double mean[3];        /* Normalize mean per channel (fraction of 255) */
   double std[3];         /* Normalize std per channel (fraction of 255) */
-  int32_t tile_h, tile_w;/* fused-kernel output tile (tile_w a multiple of 8); 0 = autotuned */
-  int32_t ctas_per_sm;   /* fused-kernel residency; 0 = autotuned */
+  int32_t tile_h;        /* fused kernel: output rows per work item (1..32) */
+  int32_t tile_w;        /* must be 0: a work item spans the full output width */
+  int32_t ctas_per_sm;   /* fused kernel: resident CTAs per SM.  tile_h == 0 and
+                            ctas_per_sm == 0: the schedule alb_autotune_batch cached
+                            for this (device, out_h, out_w, batch-size bucket), else
+                            8 rows at the occupancy limit */
   int32_t reserved;
 } alb_chain_cfg;        /* 72 bytes */
 
@@ -233,6 +237,21 @@ ALB_API size_t alb_batch_workspace_size(const alb_chain_cfg* cfg, int32_t n, int
 ALB_API alb_status alb_apply_batch(const alb_chain_cfg* cfg, int32_t n, const alb_params* params_dev,
                            const alb_image* in_dev, void* out_bf16, int32_t mode,
                            void* workspace, size_t workspace_bytes, int32_t* dev_status, void* stream);
+
+/* Autotuner of the fused kernel's schedule (the paper has no counterpart: it is
+ * part of running the chain on a GPU).  Runs alb_apply_batch in fused mode once
+ * as warm-up and `reps` times under CUDA events for every candidate (rows per
+ * item in {2, 4, 8, 16, 32} x CTAs per SM in {occupancy limit, half of it}) on
+ * the caller's own batch, keeps the fastest in a process-wide cache keyed by
+ * (current device, out_h, out_w, ceil(log2 n)), and returns it in *best (a copy
+ * of *cfg with tile_h and ctas_per_sm set).  Arguments as for alb_apply_batch
+ * (workspace for ALB_MODE_FUSED); out_bf16 is overwritten with the chain's
+ * output, identical for every schedule.  Synchronises `stream`: do not call it
+ * while the stream is captured.  Errors: ALB_EINVAL / ALB_ESHAPE /
+ * ALB_EWORKSPACE on bad arguments, ALB_ECUDA when a launch or timing fails. */
+ALB_API alb_status alb_autotune_batch(const alb_chain_cfg* cfg, int32_t n, const alb_params* params_dev,
+                              const alb_image* in_dev, void* out_bf16, void* workspace,
+                              size_t workspace_bytes, int32_t reps, alb_chain_cfg* best, void* stream);
 
 /* ------------------------------------------------------------------ */
 /* Differentiable float32 path.  x: DEVICE float [B][C][H][W] (NCHW, values

@@ -104,6 +104,8 @@ def _declare(L):
     L.alb_batch_workspace_size.restype = C.c_size_t
     L.alb_apply_batch.argtypes = [P(ChainCfg), C.c_int32, vp, vp, vp, C.c_int32, vp, C.c_size_t, vp, vp]
     L.alb_apply_batch.restype = st
+    L.alb_autotune_batch.argtypes = [P(ChainCfg), C.c_int32, vp, vp, vp, vp, C.c_size_t, C.c_int32, P(ChainCfg), vp]
+    L.alb_autotune_batch.restype = st
     L.alb_f32_workspace_size.argtypes = [C.c_int32] * 4
     L.alb_f32_workspace_size.restype = C.c_size_t
     for name in ("alb_warp_affine_f32_fwd", "alb_photometric_f32_fwd"):
@@ -321,6 +323,20 @@ def alb_apply_batch(cfg: ChainCfg, n: int, params_dev, in_dev, out_bf16: torch.T
         ws = workspace(alb_batch_workspace_size(cfg, n, mode), out_bf16.device)
     _check(load().alb_apply_batch(C.byref(cfg), n, _ptr(params_dev), _ptr(in_dev), _ptr(out_bf16), mode, _ptr(ws),
                                   ws.numel(), _ptr(dev_status), _stream(stream)))
+
+
+def alb_autotune_batch(cfg: ChainCfg, n: int, params_dev, in_dev, out_bf16: torch.Tensor, ws=None, reps: int = 3,
+                       stream=None) -> ChainCfg:
+    """Times the fused kernel's candidate schedules on this batch, caches the
+    fastest in the library and returns it (a copy of cfg with tile_h and
+    ctas_per_sm set).  Synchronises the stream."""
+    _cuda(out_bf16, "out")
+    if ws is None:
+        ws = workspace(alb_batch_workspace_size(cfg, n, MODE_FUSED), out_bf16.device)
+    best = ChainCfg()
+    _check(load().alb_autotune_batch(C.byref(cfg), n, _ptr(params_dev), _ptr(in_dev), _ptr(out_bf16), _ptr(ws),
+                                     ws.numel(), reps, C.byref(best), _stream(stream)))
+    return best
 
 
 def alb_f32_workspace_size(B, Cc, H, W) -> int:

@@ -12,6 +12,9 @@
 // Both modes call the same __device__ step functions, so outputs are identical.
 #include <cuda_bf16.h>
 
+#include <mutex>
+#include <vector>
+
 #include "alb_common.cuh"
 #include "alb_kernels.cuh"
 
@@ -274,6 +277,55 @@ static ChainK make_consts(const alb_chain_cfg& cfg) {
   return K;
 }
 
+// ---------------------------------------------------------------- schedule cache
+// A schedule of the fused kernel is (rows per work item, resident CTAs per
+// SM).  alb_autotune_batch times candidates on the caller's batch and keeps
+// the fastest here, per (device, out_h, out_w, batch-size bucket = ceil(log2 n));
+// a cfg with tile_h == 0 and ctas_per_sm == 0 runs with the cached schedule
+// of its key, or the default (8 rows, occupancy limit) when there is none.
+struct TuneEntry {
+  int32_t dev, oh, ow, bucket;
+  int32_t band, per_sm;
+};
+static std::mutex g_tune_mu;
+static std::vector<TuneEntry> g_tune;
+
+static int32_t size_bucket(int32_t n) {
+  int32_t b = 0;
+  while (b < 31 && (int64_t(1) << b) < n) b++;
+  return b;
+}
+
+static bool tune_lookup(int32_t dev, const alb_chain_cfg& cfg, int32_t n, int32_t& band, int32_t& per_sm) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  const int32_t bk = size_bucket(n);
+  for (const TuneEntry& e : g_tune)
+    if (e.dev == dev && e.oh == cfg.out_h && e.ow == cfg.out_w && e.bucket == bk) {
+      band = e.band;
+      per_sm = e.per_sm;
+      return true;
+    }
+  return false;
+}
+
+static void tune_store(int32_t dev, const alb_chain_cfg& cfg, int32_t n, int32_t band, int32_t per_sm) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  const int32_t bk = size_bucket(n);
+  for (TuneEntry& e : g_tune)
+    if (e.dev == dev && e.oh == cfg.out_h && e.ow == cfg.out_w && e.bucket == bk) {
+      e.band = band;
+      e.per_sm = per_sm;
+      return;
+    }
+  g_tune.push_back(TuneEntry{dev, cfg.out_h, cfg.out_w, bk, band, per_sm});
+}
+
+static int fused_max_per_sm() {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chain_fused, 256, 0);
+  return per_sm < 1 ? 1 : per_sm;
+}
+
 alb_status launch_chain(const alb_chain_cfg& cfg, int32_t n, const alb_params* params, const alb_image* in,
                         void* out, int32_t mode, Carve& ws, int32_t* status, cudaStream_t st) {
   const ChainK K = make_consts(cfg);
@@ -285,12 +337,17 @@ alb_status launch_chain(const alb_chain_cfg& cfg, int32_t n, const alb_params* p
   __nv_bfloat16* o = (__nv_bfloat16*)out;
   if (mode == ALB_MODE_FUSED) {
     ALB_REQUIRE(cfg.out_w <= 1024, ALB_ESHAPE, "alb_apply_batch: fused mode supports out_w <= 1024");
-    const int32_t band = cfg.tile_h > 0 ? imin(cfg.tile_h, kBandMax) : 8;
-    int per_sm = cfg.ctas_per_sm;
-    if (per_sm <= 0) {
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chain_fused, 256, 0);
-      if (per_sm < 1) per_sm = 1;
+    int32_t band = 8, per_sm = 0;
+    if (cfg.tile_h <= 0 && cfg.ctas_per_sm <= 0) {
+      int dev = 0;
+      ALB_CUDA(cudaGetDevice(&dev));
+      tune_lookup(dev, cfg, n, band, per_sm);
+    } else {
+      if (cfg.tile_h > 0) band = imin(cfg.tile_h, kBandMax);
+      per_sm = cfg.ctas_per_sm;
     }
+    const int max_per_sm = fused_max_per_sm();
+    if (per_sm <= 0 || per_sm > max_per_sm) per_sm = max_per_sm;
     ALB_CUDA(cudaMemsetAsync(queue, 0, sizeof(int32_t), st));
     k_chain_fused<<<per_sm * sm_count(), 256, 0, st>>>(n, params, in, luts, K, band, queue, o);
     ALB_CUDA(cudaGetLastError());
@@ -333,10 +390,80 @@ extern "C" alb_status alb_apply_batch(const alb_chain_cfg* cfg, int32_t n, const
   ALB_REQUIRE(params_dev && in_dev && out_bf16, ALB_EINVAL, "alb_apply_batch: null device array");
   ALB_REQUIRE(mode == ALB_MODE_FUSED || mode == ALB_MODE_PLAIN, ALB_EINVAL, "alb_apply_batch: bad mode %d", mode);
   ALB_REQUIRE(cfg->out_h > 0 && cfg->out_w > 0, ALB_ESHAPE, "alb_apply_batch: bad output size");
+  ALB_REQUIRE(cfg->tile_w == 0 && cfg->tile_h >= 0 && cfg->tile_h <= kBandMax && cfg->ctas_per_sm >= 0, ALB_EINVAL,
+              "alb_apply_batch: tile_h must be in [0, %d], tile_w 0, ctas_per_sm >= 0", kBandMax);
   for (int c = 0; c < 3; c++) ALB_REQUIRE(cfg->std[c] > 0, ALB_EINVAL, "alb_apply_batch: std must be > 0");
   ALB_REQUIRE(workspace && workspace_bytes >= chain_workspace(*cfg, n, mode), ALB_EWORKSPACE,
               "alb_apply_batch: workspace of %zu bytes is smaller than %zu", workspace_bytes,
               chain_workspace(*cfg, n, mode));
   Carve cv{(char*)workspace, 0, workspace_bytes};
   return launch_chain(*cfg, n, params_dev, in_dev, out_bf16, mode, cv, dev_status, (cudaStream_t)stream);
+}
+
+// Times every candidate schedule of the fused kernel on this batch (each run
+// is a complete alb_apply_batch in fused mode: tables + fused kernel, output
+// written) and caches the fastest.  Synchronises the stream; not for use while
+// the stream is being captured into a graph.
+extern "C" alb_status alb_autotune_batch(const alb_chain_cfg* cfg, int32_t n, const alb_params* params_dev,
+                                         const alb_image* in_dev, void* out_bf16, void* workspace,
+                                         size_t workspace_bytes, int32_t reps, alb_chain_cfg* best, void* stream) {
+  ALB_REQUIRE(cfg && best, ALB_EINVAL, "alb_autotune_batch: null cfg");
+  ALB_REQUIRE(n > 0, ALB_EINVAL, "alb_autotune_batch: n must be > 0");
+  ALB_REQUIRE(params_dev && in_dev && out_bf16, ALB_EINVAL, "alb_autotune_batch: null device array");
+  ALB_REQUIRE(cfg->out_h > 0 && cfg->out_w > 0 && cfg->out_w <= 1024, ALB_ESHAPE,
+              "alb_autotune_batch: bad output size");
+  ALB_REQUIRE(cfg->tile_w == 0, ALB_EINVAL, "alb_autotune_batch: tile_w must be 0");
+  for (int c = 0; c < 3; c++) ALB_REQUIRE(cfg->std[c] > 0, ALB_EINVAL, "alb_autotune_batch: std must be > 0");
+  const size_t need = chain_workspace(*cfg, n, ALB_MODE_FUSED);
+  ALB_REQUIRE(workspace && workspace_bytes >= need, ALB_EWORKSPACE,
+              "alb_autotune_batch: workspace of %zu bytes is smaller than %zu", workspace_bytes, need);
+  if (reps < 1) reps = 1;
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0;
+  ALB_CUDA(cudaGetDevice(&dev));
+  const int max_per_sm = fused_max_per_sm();
+  const int32_t bands[] = {2, 4, 8, 16, 32};
+  const int32_t residency[] = {max_per_sm, max_per_sm / 2};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  ALB_CUDA(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_status(cudaGetLastError(), "cudaEventCreate");
+  }
+  float best_ms = 0.0f;
+  int32_t best_band = 8, best_per_sm = max_per_sm;
+  alb_status rc = ALB_OK;
+  for (int32_t band : bands) {
+    for (int ri = 0; ri < 2 && rc == ALB_OK; ri++) {
+      const int32_t per_sm = residency[ri];
+      if (per_sm < 1 || (ri == 1 && per_sm == residency[0])) continue;
+      alb_chain_cfg c = *cfg;
+      c.tile_h = band;
+      c.ctas_per_sm = per_sm;
+      Carve cv{(char*)workspace, 0, workspace_bytes};
+      rc = launch_chain(c, n, params_dev, in_dev, out_bf16, ALB_MODE_FUSED, cv, nullptr, st);   // warm-up
+      if (rc != ALB_OK) break;
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < reps && rc == ALB_OK; r++) {
+        Carve cr{(char*)workspace, 0, workspace_bytes};
+        rc = launch_chain(c, n, params_dev, in_dev, out_bf16, ALB_MODE_FUSED, cr, nullptr, st);
+      }
+      cudaEventRecord(e1, st);
+      if (rc != ALB_OK) break;
+      float ms = 0.0f;
+      cudaError_t e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) { rc = cuda_status(e, "autotune timing"); break; }
+      if (best_ms == 0.0f || ms < best_ms) { best_ms = ms; best_band = band; best_per_sm = per_sm; }
+    }
+    if (rc != ALB_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != ALB_OK) return rc;
+  tune_store(dev, *cfg, n, best_band, best_per_sm);
+  *best = *cfg;
+  best->tile_h = best_band;
+  best->ctas_per_sm = best_per_sm;
+  return ALB_OK;
 }

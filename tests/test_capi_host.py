@@ -97,6 +97,24 @@ def test_argument_errors_are_reported_without_cuda(L):
                               None) == alb.ALB_OK
 
 
+def test_schedule_fields_are_checked_without_cuda(L):
+    """alb_apply_batch and alb_autotune_batch reject a bad schedule before any
+    device work (the pointers below are never dereferenced)."""
+    fake = C.c_void_p(16)
+    for kw in (dict(tile_w=8), dict(tile_h=33), dict(tile_h=-1), dict(ctas_per_sm=-2)):
+        cfg = alb.chain_cfg(**kw)
+        assert L.alb_apply_batch(C.byref(cfg), 4, fake, fake, fake, 0, fake, 1 << 40, None, None) == alb.ALB_EINVAL, kw
+        assert "tile_h" in alb.alb_last_error()
+    best = alb.ChainCfg()
+    cfg = alb.chain_cfg(tile_w=8)
+    assert L.alb_autotune_batch(C.byref(cfg), 4, fake, fake, fake, fake, 1 << 40, 1, C.byref(best), None) == alb.ALB_EINVAL
+    assert L.alb_autotune_batch(None, 4, fake, fake, fake, fake, 1 << 40, 1, C.byref(best), None) == alb.ALB_EINVAL
+    assert L.alb_autotune_batch(C.byref(alb.chain_cfg()), 0, fake, fake, fake, fake, 1 << 40, 1, C.byref(best),
+                                None) == alb.ALB_EINVAL
+    assert L.alb_autotune_batch(C.byref(alb.chain_cfg()), 4, fake, fake, fake, fake, 0, 1, C.byref(best),
+                                None) == alb.ALB_EWORKSPACE
+
+
 def test_workspace_sizes(L):
     assert alb.alb_workspace_size(alb.EQUALIZE, 2000) > alb.alb_workspace_size(alb.BRIGHTNESS, 2000)
     assert alb.alb_workspace_size(alb.BRIGHTNESS, 2000) > alb.alb_workspace_size(alb.HFLIP, 2000)

@@ -65,6 +65,35 @@ def test_fused_band_heights(dev, tile_h):
         assert np.array_equal(out[i], O.chain_image(ops[i], rb.image(i).numpy()))
 
 
+def test_autotuned_schedule_and_every_candidate_agree(dev):
+    """The autotuner returns one of its candidate schedules, later zero-field
+    calls use it, and every schedule writes the same bits as the oracle."""
+    sizes = [(256 + (i * 131) % 769, 256 + (i * 71) % 769) for i in range(40)]
+    rb = synth.ragged_noise(sizes, seed=11)
+    oc = O.make_cfg(O.CHAIN, **CHAIN_CFG)
+    ops = [O.sample_params(oc, 11, 20, i, h, w) for i, (h, w) in enumerate(sizes)]
+    lps = [to_lib(p, alb) for p in ops]
+    din = DeviceBatch(to_device(rb, dev))
+    n = len(lps)
+    pdev = alb.params_to_device(lps, dev)
+    out = torch.empty((n, 3, 224, 224), dtype=torch.bfloat16, device=dev)
+    best = alb.alb_autotune_batch(alb.chain_cfg(), n, pdev, din.dev, out, reps=2)
+    torch.cuda.synchronize()
+    assert best.tile_h in (2, 4, 8, 16, 32) and best.ctas_per_sm >= 1 and best.tile_w == 0
+    ref = bits(out)
+    for i in range(n):
+        assert np.array_equal(ref[i], O.chain_image(ops[i], rb.image(i).numpy())), i
+    cached = torch.empty_like(out)
+    alb.alb_apply_batch(alb.chain_cfg(), n, pdev, din.dev, cached, alb.MODE_FUSED)
+    for tile_h, per_sm in ((2, 1), (32, best.ctas_per_sm), (best.tile_h, best.ctas_per_sm), (5, 2)):
+        o = torch.empty_like(out)
+        alb.alb_apply_batch(alb.chain_cfg(tile_h=tile_h, ctas_per_sm=per_sm), n, pdev, din.dev, o, alb.MODE_FUSED)
+        torch.cuda.synchronize()
+        assert np.array_equal(bits(o), ref), (tile_h, per_sm)
+    torch.cuda.synchronize()
+    assert np.array_equal(bits(cached), ref)
+
+
 def test_full_size_ragged_batch_sampled(dev):
     """4096 images, H, W ~ U[256, 1024], params from the device sampler; fused ==
     plain over the whole output; 24 sampled images against the oracle."""
