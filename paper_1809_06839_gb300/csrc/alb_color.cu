@@ -49,8 +49,19 @@ __global__ void __launch_bounds__(256) k_build_luts(int32_t n, PrmList prm, uint
       break;
     }
     case ALB_GAMMA: {
-      const double r = x / 255.0;
-      const uint8_t o = sat_rne(255.0 * pow(r, p.gamma));
+      // float32 first: 255 (v/255)^g is then within 2e-4 of the exact value
+      // (powf's documented bound of a few ulp at <= 255, the rounding of v/255
+      // and of g to float), so unless it lies within 4e-3 of a rounding point
+      // (a half-integer) it rounds like the float64 definition; the rare
+      // others are evaluated in float64 (FP64 throughput is low on this GPU)
+      const float y32 = 255.0f * powf((float)v / 255.0f, (float)p.gamma);
+      const float frac = y32 - floorf(y32);
+      uint8_t o;
+      if (fabsf(frac - 0.5f) > 4e-3f) {
+        o = sat_rne((double)rintf(y32));
+      } else {
+        o = sat_rne(255.0 * pow(x / 255.0, p.gamma));
+      }
       L[v] = L[256 + v] = L[512 + v] = o;
       break;
     }
@@ -112,18 +123,18 @@ alb_status launch_photometric(int32_t tid, int32_t n, const Plan& plan, const Im
     case ALB_BRIGHTNESS: case ALB_CONTRAST: case ALB_BRIGHTNESS_CONTRAST: case ALB_GAMMA: case ALB_SHIFT_RGB: {
       k_build_luts<<<n, 256, 0, st>>>(n, prm, luts);
       ALB_CUDA(cudaGetLastError());
-      return launch_stream_lut(plan, in, out, luts, st);
+      return launch_stream_lut(plan, in, out, luts, status, st);
     }
     case ALB_EQUALIZE: {
       ALB_CUDA(cudaMemsetAsync(hist, 0, (size_t)n * 768 * sizeof(uint32_t), st));
-      alb_status rc = launch_stream_hist(plan, in, hist, st);
+      alb_status rc = launch_stream_hist(plan, in, hist, status, st);
       if (rc != ALB_OK) return rc;
       k_equalize_luts<<<n, 256, 0, st>>>(n, prm, hist, luts);
       ALB_CUDA(cudaGetLastError());
-      return launch_stream_lut(plan, in, out, luts, st);
+      return launch_stream_lut(plan, in, out, luts, status, st);
     }
     case ALB_GRAYSCALE: case ALB_SHIFT_HSV:
-      return launch_stream_pixel(tid, plan, in, out, prm, st);
+      return launch_stream_pixel(tid, plan, in, out, prm, status, st);
     default:
       set_error("launch_photometric: transform %d is not photometric", tid);
       return ALB_EINVAL;

@@ -15,10 +15,11 @@ alb_status launch_boxes(int32_t n, const PrmList& prm, const ImgList& in, const 
 alb_status launch_stream_geometric(int32_t tid, const Plan& plan, const ImgList& in, const ImgList& out,
                                    const PrmList& prm, int32_t channels, cudaStream_t st);
 alb_status launch_stream_lut(const Plan& plan, const ImgList& in, const ImgList& out, const uint8_t* luts,
-                             cudaStream_t st);
+                             int32_t* status, cudaStream_t st);
 alb_status launch_stream_pixel(int32_t tid, const Plan& plan, const ImgList& in, const ImgList& out,
-                               const PrmList& prm, cudaStream_t st);
-alb_status launch_stream_hist(const Plan& plan, const ImgList& in, uint32_t* hist, cudaStream_t st);
+                               const PrmList& prm, int32_t* status, cudaStream_t st);
+alb_status launch_stream_hist(const Plan& plan, const ImgList& in, uint32_t* hist, int32_t* status,
+                              cudaStream_t st);
 
 // alb_resample.cu (tiled warps and resizes)
 alb_status launch_tile_geometric(int32_t tid, const Plan& plan, const ImgList& in, const ImgList& out,

@@ -14,6 +14,7 @@
 #include "alb_common.cuh"
 #include "alb_kernels.cuh"
 #include "alb_vec.cuh"
+#include "alb_bulk.cuh"
 
 namespace alb {
 
@@ -47,67 +48,235 @@ ALB_D void lut_px(const uint8_t* tab, int lb, uint32_t& r, uint32_t& g, uint32_t
   b = tab[lb + 16384 + lut_off(b)];
 }
 
-// 16 RGB pixels of one 48-byte unit through the three tables
-ALB_D void lut_unit(const uint8_t* tab, int lb, const U48& u, uint32_t (&o)[12]) {
-  uint32_t w[12];
-  words48(u, w);
-#pragma unroll
-  for (int m = 0; m < 12; m++) {
-    uint32_t acc = 0;
-#pragma unroll
-    for (int t = 0; t < 4; t++) {
-      const int k = 4 * m + t, c = k % 3;
-      acc |= (uint32_t)tab[lb + 8192 * c + lut_off((w[m] >> (8 * t)) & 0xFFu)] << (8 * t);
-    }
-    o[m] = acc;
+// LUT ops through the bulk-copy engine.  Per CTA, thread 0 runs a pipeline
+// of kBulkStages shared-memory stages of kBulkChunk bytes: bulk loads of the
+// run's 16-byte-aligned core (completion counted on one mbarrier per stage),
+// all threads look the bytes up in place (16-byte vectors; the channel of a
+// byte follows its offset mod 3), then one bulk store writes the stage back
+// and the stage is refilled once that store has read it.  The <= 15 bytes at
+// each end of a run and images that are not contiguous and 16-byte aligned take
+// a per-byte / per-pixel path.
+constexpr int kBulkChunk = 12288;   // bytes per stage: 768 vectors, a multiple of 3 and 16
+constexpr int kBulkStages = 4;
+static_assert(kBulkChunk % 48 == 0, "a stage starts on the same channel phase as the previous one");
+
+// Streams bytes [0, total) of src (and, with dst, back to dst) through the
+// CTA's stages.  body(stage, bytes, offset) runs on every thread for each
+// chunk; with dst it may rewrite the stage in place, which is then stored.
+// seq counts the CTA's chunk loads (stage = seq % stages, phase parity =
+// (seq / stages) & 1) and continues across calls.  Returns false when a
+// bounded wait gave up (status set, loads in flight drained): the caller stops.
+// Called by all threads of the CTA; src/dst/total 16-byte aligned.
+template <class F>
+ALB_D bool bulk_pipeline(uint8_t (*stage)[kBulkChunk], uint64_t* full, uint32_t& seq, const uint8_t* src,
+                         uint8_t* dst, int64_t total, int32_t* status, F&& body) {
+  const int tid = threadIdx.x;
+  const int32_t nch = (int32_t)((total + kBulkChunk - 1) / kBulkChunk);
+  if (nch == 0) return true;
+  auto bytes_of = [&](int32_t j) -> uint32_t {
+    const int64_t rest = total - (int64_t)j * kBulkChunk;
+    return (uint32_t)(rest < kBulkChunk ? rest : kBulkChunk);
+  };
+  auto issue = [&](int32_t j) {
+    const uint32_t q = seq + (uint32_t)j, st = q % kBulkStages;
+    mbar_arrive_expect_tx(&full[st], bytes_of(j));
+    bulk_load(stage[st], src + (int64_t)j * kBulkChunk, bytes_of(j), &full[st]);
+  };
+  if (tid == 0) {
+    if (dst) bulk_wait_read<0>();                // every earlier store has read its stage
+    for (int32_t j = 0; j < nch && j < kBulkStages - 1; j++) issue(j);
   }
+  int32_t j = 0;
+  bool dead = false;
+  for (; j < nch; j++) {
+    const uint32_t q = seq + (uint32_t)j, st = q % kBulkStages;
+    const bool ok = mbar_wait(&full[st], (q / kBulkStages) & 1u);
+    if (__syncthreads_or(!ok)) { dead = true; break; }
+    body(stage[st], (int)bytes_of(j), (int64_t)j * kBulkChunk);
+    if (dst) fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) {
+      if (dst) {
+        bulk_store(dst + (int64_t)j * kBulkChunk, stage[st], bytes_of(j));
+        bulk_commit();
+      }
+      const int32_t jn = j + kBulkStages - 1;    // refills the stage of chunk j - 1
+      if (jn < nch) {
+        if (dst) bulk_wait_read<1>();
+        issue(jn);
+      }
+    }
+  }
+  if (dead) {
+    if (tid == 0) {
+      const int32_t last = imin(nch, j + kBulkStages - 1);
+      for (int32_t k = j; k < last; k++) {
+        const uint32_t q = seq + (uint32_t)k;
+        mbar_wait(&full[q % kBulkStages], (q / kBulkStages) & 1u);
+      }
+      dev_fail(status, ALB_ETIMEOUT);
+    }
+    return false;
+  }
+  seq += (uint32_t)nch;
+  return true;
 }
 
-__global__ void __launch_bounds__(256) k_lut_stream(Plan plan, ImgList in, ImgList out,
-                                                    const uint8_t* __restrict__ luts) {
-  __shared__ __align__(16) uint32_t tab32[kLutBytes / 4];
-  __shared__ uint8_t sh768[768];
-  const uint8_t* tab = reinterpret_cast<const uint8_t*>(tab32);
+// the run's bytes [S0, E0) split into head [S0, A), 16-byte-aligned core [A, E), tail [E, E0)
+ALB_D void aligned_core(int64_t S0, int64_t E0, int64_t& A, int64_t& E) {
+  A = (S0 + 15) & ~int64_t(15);
+  E = E0 & ~int64_t(15);
+  if (A > E0) A = E0;
+  if (E < A) E = A;
+}
+
+struct LutBulkSmem {
+  uint8_t stage[kBulkStages][kBulkChunk];
+  uint32_t tab32[kLutBytes / 4];
+  uint64_t full[kBulkStages];
+  uint8_t sh768[768];
+};
+
+__global__ void __launch_bounds__(256) k_lut_bulk(Plan plan, ImgList in, ImgList out, const uint8_t* __restrict__ luts,
+                                                  int32_t* status) {
+  extern __shared__ __align__(128) uint8_t lut_dyn[];
+  LutBulkSmem& sm = *reinterpret_cast<LutBulkSmem*>(lut_dyn);
   const int lb = 4 * (threadIdx.x & 31);
+  const uint8_t* tab0 = reinterpret_cast<const uint8_t*>(sm.tab32);
+  const uint8_t* tab = tab0 + lb;
+  const int tid = threadIdx.x, bs = blockDim.x;
+  if (tid == 0) {
+    for (int i = 0; i < kBulkStages; i++) mbar_init(&sm.full[i], 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  uint32_t seq = 0;
+  bool dead = false;
   for_each_run(plan, [&](int32_t b, int32_t r0, int32_t r1) {
+    if (dead) return;
     __syncthreads();
-    build_lut_copies(luts + (int64_t)b * 768, sh768, tab32);
+    build_lut_copies(luts + (int64_t)b * 768, sm.sh768, sm.tab32);
     const alb_image si = in.get(b), so = out.get(b);
     r1 = imin(r1, so.h);
     const uint8_t* __restrict__ ip = (const uint8_t*)si.data;
     uint8_t* __restrict__ op = (uint8_t*)so.data;
-    if (flat_aligned(si) && flat_aligned(so)) {
-      const int64_t a = (int64_t)r0 * so.w, e = (int64_t)r1 * so.w;   // pixel range
-      const int64_t u0 = (a + 15) >> 4, u1 = e >> 4;                    // whole 16-pixel units
-      // the next unit's three vectors are in flight while this one is looked up
-      int64_t u = u0 + threadIdx.x;
-      U48 nx;
-      if (u < u1) ld48(ip + 48 * u, nx);
-      for (; u < u1; u += blockDim.x) {
-        const U48 cur = nx;
-        if (u + blockDim.x < u1) ld48(ip + 48 * (u + blockDim.x), nx);
-        uint32_t o[12];
-        lut_unit(tab, lb, cur, o);
-        st48(op + 48 * u, o);
-      }
-      const int64_t h1 = u0 * 16 < e ? u0 * 16 : e;
-      for (int64_t q = a + threadIdx.x; q < e; q += blockDim.x) {
-        if (q >= h1 && q < u1 * 16) continue;
-        uint32_t R = ip[3 * q], G = ip[3 * q + 1], B = ip[3 * q + 2];
-        lut_px(tab, lb, R, G, B);
-        op[3 * q] = (uint8_t)R; op[3 * q + 1] = (uint8_t)G; op[3 * q + 2] = (uint8_t)B;
-      }
-    } else {
+    if (!(flat_aligned(si) && flat_aligned(so))) {
       const int64_t npx = (int64_t)(r1 - r0) * so.w;
-      for (int64_t i = threadIdx.x; i < npx; i += blockDim.x) {
+      for (int64_t i = tid; i < npx; i += bs) {
         const int32_t y = r0 + (int32_t)(i / so.w), x = (int32_t)(i % so.w);
         const uint8_t* s0 = ip + (int64_t)y * si.row_stride + 3 * (int64_t)x;
         uint8_t* d = op + (int64_t)y * so.row_stride + 3 * (int64_t)x;
         uint32_t R = s0[0], G = s0[1], B = s0[2];
-        lut_px(tab, lb, R, G, B);
+        lut_px(tab0, lb, R, G, B);
         d[0] = (uint8_t)R; d[1] = (uint8_t)G; d[2] = (uint8_t)B;
       }
+      return;
     }
+    int64_t A, E;
+    const int64_t S0 = 3 * (int64_t)r0 * so.w, E0 = 3 * (int64_t)r1 * so.w;
+    aligned_core(S0, E0, A, E);
+    for (int64_t q = S0 + tid; q < A; q += bs) op[q] = tab[8192 * (int)(q % 3) + lut_off(ip[q])];
+    for (int64_t q = E + tid; q < E0; q += bs) op[q] = tab[8192 * (int)(q % 3) + lut_off(ip[q])];
+    const int phi = (int)(A % 3);   // channel of the core's first byte; chunks keep it (kBulkChunk % 3 == 0)
+    dead = !bulk_pipeline(sm.stage, sm.full, seq, ip + A, op + A, E - A, status,
+                          [&](uint8_t* sb, int nbytes, int64_t) {
+      const int nv = nbytes >> 4;
+      for (int v = tid; v < nv; v += bs) {
+        const uint4 x = *reinterpret_cast<const uint4*>(sb + 16 * v);
+        const int rho = (phi + v) % 3;             // 16 = 1 mod 3: channel of the vector's first byte
+        const uint8_t* t0 = tab + 8192 * rho;
+        const uint8_t* t1 = tab + 8192 * (rho == 2 ? 0 : rho + 1);
+        const uint8_t* t2 = tab + 8192 * (rho == 0 ? 2 : rho - 1);
+        const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+        uint32_t o[4];
+#pragma unroll
+        for (int m = 0; m < 4; m++) {
+          uint32_t acc = 0;
+#pragma unroll
+          for (int t = 0; t < 4; t++) {
+            const int k = 4 * m + t;
+            const uint8_t* tb = k % 3 == 0 ? t0 : (k % 3 == 1 ? t1 : t2);
+            acc |= (uint32_t)tb[lut_off((w[m] >> (8 * t)) & 0xFFu)] << (8 * t);
+          }
+          o[m] = acc;
+        }
+        *reinterpret_cast<uint4*>(sb + 16 * v) = make_uint4(o[0], o[1], o[2], o[3]);
+      }
+    });
+  });
+  if (tid == 0) bulk_wait_all();
+}
+
+// Per-channel histograms through the bulk-copy stages (read only): per-warp
+// shared copies, merged into the image's global histogram at the end of each
+// run (one image per run).
+struct HistBulkSmem {
+  uint8_t stage[kBulkStages][kBulkChunk];
+  uint32_t sh[8][768];
+  uint64_t full[kBulkStages];
+};
+
+__global__ void __launch_bounds__(256) k_hist_bulk(Plan plan, ImgList in, uint32_t* __restrict__ hist,
+                                                   int32_t* status) {
+  extern __shared__ __align__(128) uint8_t hist_dyn[];
+  HistBulkSmem& sm = *reinterpret_cast<HistBulkSmem*>(hist_dyn);
+  const int tid = threadIdx.x, bs = blockDim.x;
+  uint32_t* my = sm.sh[tid >> 5];
+  for (int i = tid; i < 8 * 768; i += bs) (&sm.sh[0][0])[i] = 0;
+  if (tid == 0) {
+    for (int i = 0; i < kBulkStages; i++) mbar_init(&sm.full[i], 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  uint32_t seq = 0;
+  bool dead = false;
+  for_each_run(plan, [&](int32_t b, int32_t r0, int32_t r1) {
+    if (dead) return;
+    const alb_image si = in.get(b);
+    r1 = imin(r1, si.h);
+    const uint8_t* __restrict__ ip = (const uint8_t*)si.data;
+    if (flat_aligned(si)) {
+      int64_t A, E;
+      const int64_t S0 = 3 * (int64_t)r0 * si.w, E0 = 3 * (int64_t)r1 * si.w;
+      aligned_core(S0, E0, A, E);
+      for (int64_t q = S0 + tid; q < A; q += bs) atomicAdd(&my[256 * (int)(q % 3) + ip[q]], 1u);
+      for (int64_t q = E + tid; q < E0; q += bs) atomicAdd(&my[256 * (int)(q % 3) + ip[q]], 1u);
+      const int phi = (int)(A % 3);
+      dead = !bulk_pipeline(sm.stage, sm.full, seq, ip + A, nullptr, E - A, status,
+                            [&](uint8_t* sb, int nbytes, int64_t) {
+        const int nv = nbytes >> 4;
+        for (int v = tid; v < nv; v += bs) {
+          const uint4 x = *reinterpret_cast<const uint4*>(sb + 16 * v);
+          const int rho = (phi + v) % 3;
+          uint32_t* h0 = my + 256 * rho;
+          uint32_t* h1 = my + 256 * (rho == 2 ? 0 : rho + 1);
+          uint32_t* h2 = my + 256 * (rho == 0 ? 2 : rho - 1);
+          const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+          for (int k = 0; k < 16; k++) {
+            uint32_t* hb = k % 3 == 0 ? h0 : (k % 3 == 1 ? h1 : h2);
+            atomicAdd(&hb[(w[k >> 2] >> (8 * (k & 3))) & 0xFFu], 1u);
+          }
+        }
+      });
+      if (dead) return;
+    } else {
+      const int64_t npx = (int64_t)(r1 - r0) * si.w;
+      for (int64_t i = tid; i < npx; i += bs) {
+        const int32_t y = r0 + (int32_t)(i / si.w), x = (int32_t)(i % si.w);
+        const uint8_t* s = ip + (int64_t)y * si.row_stride + 3 * (int64_t)x;
+#pragma unroll
+        for (int c = 0; c < 3; c++) atomicAdd(&my[256 * c + s[c]], 1u);
+      }
+    }
+    __syncthreads();
+    for (int i = tid; i < 768; i += bs) {
+      uint32_t sum = 0;
+#pragma unroll
+      for (int w = 0; w < 8; w++) { sum += sm.sh[w][i]; sm.sh[w][i] = 0; }
+      if (sum) atomicAdd(&hist[(int64_t)b * 768 + i], sum);
+    }
+    __syncthreads();
   });
 }
 
@@ -464,62 +633,6 @@ __global__ void __launch_bounds__(256) k_rowcopy(Plan plan, ImgList in, ImgList 
   }
 }
 
-// ================================================================== histogram
-// Per-CTA shared-memory histograms (one copy per warp to spread contention on
-// the smooth images' repeated values), merged into the image's global
-// histogram with one atomic per bin when the CTA leaves the image.
-__global__ void __launch_bounds__(256) k_hist_stream(Plan plan, ImgList in, uint32_t* __restrict__ hist) {
-  constexpr int NWARP = 8;
-  __shared__ uint32_t sh[NWARP][768];
-  uint32_t* my = sh[threadIdx.x >> 5];
-  for (int i = threadIdx.x; i < NWARP * 768; i += blockDim.x) (&sh[0][0])[i] = 0;
-  __syncthreads();
-  for_each_run(plan, [&](int32_t b, int32_t r0, int32_t r1) {
-    const alb_image si = in.get(b);
-    r1 = imin(r1, si.h);
-    const uint8_t* __restrict__ ip = (const uint8_t*)si.data;
-    if (flat_aligned(si)) {
-      // 48-byte units start on a pixel: byte k of a unit is channel k % 3
-      const int64_t a = (int64_t)r0 * si.w, e = (int64_t)r1 * si.w;
-      const int64_t u0 = (a + 15) >> 4, u1 = e >> 4;
-      int64_t u = u0 + threadIdx.x;
-      U48 nx;
-      if (u < u1) ld48(ip + 48 * u, nx);
-      for (; u < u1; u += blockDim.x) {
-        const U48 cur = nx;
-        if (u + blockDim.x < u1) ld48(ip + 48 * (u + blockDim.x), nx);
-        uint32_t w[12];
-        words48(cur, w);
-#pragma unroll
-        for (int k = 0; k < 48; k++) atomicAdd(&my[256 * (k % 3) + byte_of(w, k)], 1u);
-      }
-      const int64_t h1 = u0 * 16 < e ? u0 * 16 : e;
-      for (int64_t q = a + threadIdx.x; q < e; q += blockDim.x) {
-        if (q >= h1 && q < u1 * 16) continue;
-#pragma unroll
-        for (int c = 0; c < 3; c++) atomicAdd(&my[256 * c + ip[3 * q + c]], 1u);
-      }
-    } else {
-      const int64_t npx = (int64_t)(r1 - r0) * si.w;
-      for (int64_t i = threadIdx.x; i < npx; i += blockDim.x) {
-        const int32_t y = r0 + (int32_t)(i / si.w), x = (int32_t)(i % si.w);
-        const uint8_t* s = ip + (int64_t)y * si.row_stride + 3 * (int64_t)x;
-#pragma unroll
-        for (int c = 0; c < 3; c++) atomicAdd(&my[256 * c + s[c]], 1u);
-      }
-    }
-    // one image per run: merge the warps' copies into its global histogram
-    __syncthreads();
-    for (int i = threadIdx.x; i < 768; i += blockDim.x) {
-      uint32_t sum = 0;
-#pragma unroll
-      for (int w = 0; w < NWARP; w++) { sum += sh[w][i]; sh[w][i] = 0; }
-      if (sum) atomicAdd(&hist[(int64_t)b * 768 + i], sum);
-    }
-    __syncthreads();
-  });
-}
-
 // ================================================================== launchers
 static int grid_for(const void* fn, int threads) {
   int per_sm = 0;
@@ -564,18 +677,32 @@ alb_status launch_stream_geometric(int32_t tid, const Plan& plan, const ImgList&
 }
 
 alb_status launch_stream_lut(const Plan& plan, const ImgList& in, const ImgList& out, const uint8_t* luts,
-                             cudaStream_t st) {
-  return launch_k(k_lut_stream, st, plan, in, out, luts);
+                             int32_t* status, cudaStream_t st) {
+  const int smem = (int)sizeof(LutBulkSmem);
+  ALB_CUDA(cudaFuncSetAttribute(k_lut_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lut_bulk, 256, smem);
+  k_lut_bulk<<<(per_sm < 1 ? 1 : per_sm) * sm_count(), 256, smem, st>>>(plan, in, out, luts, status);
+  ALB_CUDA(cudaGetLastError());
+  return ALB_OK;
 }
 
 alb_status launch_stream_pixel(int32_t tid, const Plan& plan, const ImgList& in, const ImgList& out,
-                               const PrmList& prm, cudaStream_t st) {
+                               const PrmList& prm, int32_t* status, cudaStream_t st) {
+  (void)status;   // the register-pipelined kernels have no bounded waits
   if (tid == ALB_GRAYSCALE) return launch_k(k_pixel_stream<0>, st, plan, in, out, prm);
   return launch_k(k_pixel_stream<1>, st, plan, in, out, prm);
 }
 
-alb_status launch_stream_hist(const Plan& plan, const ImgList& in, uint32_t* hist, cudaStream_t st) {
-  return launch_k(k_hist_stream, st, plan, in, hist);
+alb_status launch_stream_hist(const Plan& plan, const ImgList& in, uint32_t* hist, int32_t* status,
+                              cudaStream_t st) {
+  const int smem = (int)sizeof(HistBulkSmem);
+  ALB_CUDA(cudaFuncSetAttribute(k_hist_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hist_bulk, 256, smem);
+  k_hist_bulk<<<(per_sm < 1 ? 1 : per_sm) * sm_count(), 256, smem, st>>>(plan, in, hist, status);
+  ALB_CUDA(cudaGetLastError());
+  return ALB_OK;
 }
 
 }  // namespace alb

@@ -282,3 +282,29 @@ def test_ragged_masks_with_mixed_channel_counts(dev, name):
     assert int(status.item()) == 0
     for i in range(3):
         assert np.array_equal(dmo.rb.image(i).cpu().numpy(), O.apply_mask(ops[i], masks.image(i).numpy())), i
+
+
+def test_gamma_tables_exact_over_a_dense_gamma_grid(dev):
+    """Every entry of 3000 gamma tables (gamma on a dense grid over [0.5, 2.0])
+    equals the oracle's float64 definition: the device builds the tables in
+    float32 and falls back to float64 near rounding points, so the grid
+    exercises both branches."""
+    from paper_1809_06839_gb300.synth import Ragged
+    n = 3000
+    gammas = np.linspace(0.5, 2.0, n)
+    row = np.repeat(np.arange(256, dtype=np.uint8), 3)
+    flat = torch.from_numpy(np.tile(row, n))
+    rb = Ragged(flat.to(dev), [768 * i for i in range(n)], [(1, 256, 3)] * n)
+    din = DeviceBatch(rb)
+    ops = [O.sample_params(O.make_cfg(O.GAMMA, lo=(g,), hi=(g,)), 1, 2, i, 1, 256) for i, g in enumerate(gammas)]
+    prm = alb.params_to_device([to_lib(o, alb) for o in ops], dev)
+    dout = output_batch([to_lib(o, alb) for o in ops], rb.shapes, dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    alb.alb_apply_ragged(O.GAMMA, n, prm, din.dev, dout.dev, ws=alb.workspace(alb.alb_workspace_size(O.GAMMA, n), dev),
+                         dev_status=status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    got = dout.rb.flat.cpu().numpy().reshape(n, 256, 3)
+    for i in range(n):
+        ref = O.apply_image(ops[i], row.reshape(1, 256, 3))[0]
+        assert np.array_equal(got[i], ref), (i, gammas[i])
