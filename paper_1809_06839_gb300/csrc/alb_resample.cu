@@ -468,8 +468,9 @@ ALB_D void r_tile_geo(const RImg& k, int32_t item, int lane, RTile& g, int32_t& 
   g.big = g.bw > RB_X || g.bh > RB_Y;
 }
 
-// Lane r (and r + 32) stages box row r: raw aligned 16-byte chunks, phase kept.
-ALB_D void r_tile_stage(const RImg& k, const RTile& g, int lane, uint8_t* box, int16_t* phase) {
+// Lane r (and r + 32) stages box row r: raw aligned 16-byte chunks;
+// rowoff[r] = r * pitch + the row's byte phase.
+ALB_D void r_tile_stage(const RImg& k, const RTile& g, int lane, uint8_t* box, int32_t* rowoff) {
   if (g.big) return;
   const int span = 3 * g.bw;
   for (int r = lane; r < g.bh; r += 32) {
@@ -478,7 +479,7 @@ ALB_D void r_tile_stage(const RImg& k, const RTile& g, int lane, uint8_t* box, i
                             (uintptr_t)(3 * (k.wx0 + g.bx0));
     const uintptr_t c0 = first & ~uintptr_t(15);
     const int ph = (int)(first - c0);
-    phase[r] = (int16_t)ph;
+    rowoff[r] = r * RPITCH + ph;
     const int nch = (ph + span + 15) >> 4;
     uint8_t* d = box + r * RPITCH;
     for (int j = 0; j < nch; j++) cp_async16(d + 16 * j, reinterpret_cast<const void*>(c0 + 16 * j));
@@ -492,17 +493,18 @@ ALB_D void r_hrow(uint32_t lo, uint32_t hi, uint32_t wx, uint32_t (&h)[3]) {
   h[2] = __dp4a(__byte_perm(lo, hi, 0x0052), wx, 0u);
 }
 
-ALB_D uint32_t r_vert(const uint32_t (&ha)[3], const uint32_t (&hb)[3], uint32_t wy) {
+// the output pixel from the two tap rows' h, stored channel by channel
+ALB_D void r_vert_store(const uint32_t (&ha)[3], const uint32_t (&hb)[3], uint32_t wy, bool store, uint8_t* od) {
   const uint32_t r = __dp2a_lo(__byte_perm(ha[0], hb[0], 0x5410), wy, 512u) >> 10;
   const uint32_t g = __dp2a_lo(__byte_perm(ha[1], hb[1], 0x5410), wy, 512u) >> 10;
   const uint32_t b = __dp2a_lo(__byte_perm(ha[2], hb[2], 0x5410), wy, 512u) >> 10;
-  return r | (g << 8) | (b << 16);
+  if (store) { od[0] = (uint8_t)r; od[1] = (uint8_t)g; od[2] = (uint8_t)b; }
 }
 
 ALB_D void r_tile_compute(const RImg& k, const RTile& g, int lane, int32_t vcol, int32_t vrow,
-                          const uint8_t* __restrict__ box, const int16_t* __restrict__ ph) {
+                          const uint8_t* __restrict__ box, const int32_t* __restrict__ rowoff) {
   const int32_t fx = vcol & 31;
-  const uint32_t wx = (uint32_t)(32 - fx) | ((uint32_t)fx << 8);
+  const uint32_t wx = (uint32_t)(32 + 255 * fx);       // (32 - fx) | fx << 8
   const bool store = lane < g.tw;
   uint8_t* od = k.dst + (int64_t)g.oy0 * k.dstride + 3 * (int64_t)(g.ox0 + lane);
   uint32_t ha[3] = {0u, 0u, 0u}, hb[3] = {0u, 0u, 0u};
@@ -511,7 +513,7 @@ ALB_D void r_tile_compute(const RImg& k, const RTile& g, int lane, int32_t vcol,
     const int32_t ocol = 3 * ((vcol >> 5) - g.bx0);
     auto hrow = [&](int32_t i, uint32_t (&h)[3]) {
       uint32_t lo, hi;
-      taps_row(box, i * RPITCH + ph[i] + ocol, lo, hi);
+      taps_row(box, rowoff[i] + ocol, lo, hi);
       r_hrow(lo, hi, wx, h);
     };
     // at a clamped bottom edge the row below the last tap row is not staged
@@ -536,8 +538,7 @@ ALB_D void r_tile_compute(const RImg& k, const RTile& g, int lane, int32_t vcol,
         ha[0] = adv ? hb[0] : ha[0]; ha[1] = adv ? hb[1] : ha[1]; ha[2] = adv ? hb[2] : ha[2];
         hb[0] = hn[0]; hb[1] = hn[1]; hb[2] = hn[2];
         ia = iy;
-        const uint32_t v = r_vert(ha, hb, (uint32_t)(32 - fy) | ((uint32_t)fy << 8));
-        if (store) { od[0] = (uint8_t)v; od[1] = (uint8_t)(v >> 8); od[2] = (uint8_t)(v >> 16); }
+        r_vert_store(ha, hb, (uint32_t)(32 + 255 * fy), store, od);
       }
     } else {
       for (int r = 0; r < g.th; r++, od += k.dstride) {
@@ -552,8 +553,7 @@ ALB_D void r_tile_compute(const RImg& k, const RTile& g, int lane, int32_t vcol,
           hrow(imin(iy + 1, last), hb);
           ia = iy;
         }
-        const uint32_t v = r_vert(ha, hb, (uint32_t)(32 - fy) | ((uint32_t)fy << 8));
-        if (store) { od[0] = (uint8_t)v; od[1] = (uint8_t)(v >> 8); od[2] = (uint8_t)(v >> 16); }
+        r_vert_store(ha, hb, (uint32_t)(32 + 255 * fy), store, od);
       }
     }
   } else {
@@ -574,15 +574,14 @@ ALB_D void r_tile_compute(const RImg& k, const RTile& g, int lane, int32_t vcol,
         hrow(k.wy0 + imin(iy + 1, k.ch - 1), hb);
         ia = iy;
       }
-      const uint32_t v = r_vert(ha, hb, (uint32_t)(32 - fy) | ((uint32_t)fy << 8));
-      if (store) { od[0] = (uint8_t)v; od[1] = (uint8_t)(v >> 8); od[2] = (uint8_t)(v >> 16); }
+      r_vert_store(ha, hb, (uint32_t)(32 + 255 * fy), store, od);
     }
   }
 }
 
 struct RShared {       // dynamic shared memory of k_resize_rows (above the 48 KB static limit)
   uint8_t box[RWARP][2][RB_Y * RPITCH + 16];   // +16: the last row's tap read past the staged bytes
-  int16_t phase[RWARP][2][RB_Y];
+  int32_t rowoff[RWARP][2][RB_Y];
   RImg simg[RWARP][2];
   RTile stile[RWARP][2];
 };
@@ -591,7 +590,7 @@ __global__ void __launch_bounds__(32 * RWARP) k_resize_rows(Plan plan, ImgList i
   extern __shared__ __align__(16) uint8_t rs_dyn[];
   RShared& sm = *reinterpret_cast<RShared*>(rs_dyn);
   auto& box = sm.box;
-  auto& phase = sm.phase;
+  auto& rowoff = sm.rowoff;
   auto& simg = sm.simg;
   auto& stile = sm.stile;
   int32_t it0, it1;
@@ -606,7 +605,7 @@ __global__ void __launch_bounds__(32 * RWARP) k_resize_rows(Plan plan, ImgList i
     r_load_img(plan, in, out, prm, item_image(plan, item), k);
     r_tile_geo(k, item, lane, g, ccol, crow);
     if (lane == 0) { simg[w][0] = k; stile[w][0] = g; }
-    r_tile_stage(k, g, lane, box[w][0], phase[w][0]);
+    r_tile_stage(k, g, lane, box[w][0], rowoff[w][0]);
   }
   cp_async_commit();
   int buf = 0;
@@ -625,14 +624,230 @@ __global__ void __launch_bounds__(32 * RWARP) k_resize_rows(Plan plan, ImgList i
       r_tile_geo(k, nitem, lane, g, ncol, nrow);
       __syncwarp();
       if (lane == 0) { simg[w][buf ^ 1] = k; stile[w][buf ^ 1] = g; }
-      r_tile_stage(k, g, lane, box[w][buf ^ 1], phase[w][buf ^ 1]);
+      r_tile_stage(k, g, lane, box[w][buf ^ 1], rowoff[w][buf ^ 1]);
     }
     cp_async_commit();
     cp_async_wait<1>();
     __syncwarp();
-    r_tile_compute(simg[w][buf], stile[w][buf], lane, ccol, crow, box[w][buf], phase[w][buf]);
+    r_tile_compute(simg[w][buf], stile[w][buf], lane, ccol, crow, box[w][buf], rowoff[w][buf]);
     __syncwarp();      // every lane is done with box[buf] before it is refilled
     ccol = ncol; crow = nrow;
+  }
+  cp_async_wait<0>();
+}
+
+// --------------------------------------------------------------- affine warp (RGB, bilinear)
+// Rotate / ShiftScaleRotate on RGB images.  A warp owns a 32 x 12 output tile,
+// lane j = output column j, and walks the tile's rows: the Q16 source
+// coordinates of a lane advance by (q1, q4) per row, already offset to the
+// tile's staged box and biased by the Q16 -> Q5 rounding constant.  The box
+// (up to AB - 1 pixels each way: the whole tile at any angle for scales >= 0.9;
+// the box is kept at 40 so that 16 warps fit on an SM: the kernel is
+// latency-sensitive)
+// is staged per warp by cp.async, rows reflected at copy time, double-
+// buffered; a per-row table holds row * pitch + byte phase, so a tap row's
+// offset is one shared load.  Tiles whose box crosses the left/right image
+// border map each tap column through reflect-101; tiles whose footprint does
+// not fit read their taps from global memory.
+constexpr int AT_W = 32, AT_H = 12;   // output tile (columns x rows)
+constexpr int AB = 40;                // staged box side (pixels)
+constexpr int APITCH = 144;           // staged row pitch in bytes
+constexpr int AWARP = 4;              // warps per CTA
+static_assert(APITCH % 16 == 0, "cp.async destinations must be 16-byte aligned");
+static_assert(APITCH >= 15 + 3 * (AB - 1) + 12, "a tap read (3 words from the pair's word) stays in its row");
+
+struct AImg {          // per-image values of a warp's current image (warp-uniform)
+  int32_t b, prefix, ntiles, tiles_x;
+  int32_t H, W, OH, OW;
+  int64_t q[6];
+  const uint8_t* src;
+  uint8_t* dst;
+  int64_t sstride, dstride;
+};
+struct ATile {         // geometry of one tile
+  int32_t ox0, oy0, tw, th;
+  int32_t bx0, by0, bw, bh, ra, rb, mode;   // mode 0 inside, 1 crosses a left/right border, 2 too large
+  int64_t X00, Y00;                          // Q16 source coordinates of the tile's pixel (0, 0)
+};
+
+ALB_D void a_load_img(const Plan& plan, const ImgList& in, const ImgList& out, const PrmList& prm, int32_t b,
+                      AImg& k) {
+  const alb_image si = in.get(b), so = out.get(b);
+  const alb_params& p = prm.get(b);
+  k.b = b; k.prefix = plan.prefix[b]; k.ntiles = plan.prefix[b + 1] - k.prefix; k.tiles_x = plan.rows_per_item[b];
+  k.H = si.h; k.W = si.w; k.OH = so.h; k.OW = so.w;
+  const bool app = p.apply != 0;
+  k.q[0] = app ? p.q[0] : 65536; k.q[1] = app ? p.q[1] : 0; k.q[2] = app ? p.q[2] : 0;
+  k.q[3] = app ? p.q[3] : 0; k.q[4] = app ? p.q[4] : 65536; k.q[5] = app ? p.q[5] : 0;
+  k.src = (const uint8_t*)si.data; k.dst = (uint8_t*)so.data;
+  k.sstride = si.row_stride; k.dstride = so.row_stride;
+}
+
+ALB_D void a_tile_geo(const AImg& k, int32_t item, ATile& g) {
+  const int32_t t = item - k.prefix, ty = t / k.tiles_x, tx = t - ty * k.tiles_x;
+  g.ox0 = tx * AT_W; g.oy0 = ty * AT_H;
+  g.tw = imin(AT_W, k.OW - g.ox0); g.th = imin(AT_H, k.OH - g.oy0);
+  g.X00 = k.q[0] * g.ox0 + k.q[1] * g.oy0 + k.q[2];
+  g.Y00 = k.q[3] * g.ox0 + k.q[4] * g.oy0 + k.q[5];
+  const int64_t dXx = k.q[0] * (g.tw - 1), dXy = k.q[1] * (g.th - 1), dYx = k.q[3] * (g.tw - 1), dYy = k.q[4] * (g.th - 1);
+  const int64_t xmin = g.X00 + (dXx < 0 ? dXx : 0) + (dXy < 0 ? dXy : 0);
+  const int64_t xmax = g.X00 + (dXx > 0 ? dXx : 0) + (dXy > 0 ? dXy : 0);
+  const int64_t ymin = g.Y00 + (dYx < 0 ? dYx : 0) + (dYy < 0 ? dYy : 0);
+  const int64_t ymax = g.Y00 + (dYx > 0 ? dYx : 0) + (dYy > 0 ? dYy : 0);
+  // Q5 cells of the extreme coordinates, +1 for the second tap
+  const int32_t bx0 = (int32_t)((xmin + 1024) >> 16), bx1 = (int32_t)((xmax + 1024) >> 16) + 1;
+  const int32_t by0 = (int32_t)((ymin + 1024) >> 16), by1 = (int32_t)((ymax + 1024) >> 16) + 1;
+  g.bx0 = bx0; g.by0 = by0; g.bw = bx1 - bx0 + 1; g.bh = by1 - by0 + 1;
+  g.ra = bx0; g.rb = bx1; g.mode = 0;
+  const int32_t W = k.W;
+  if (g.bw > AB - 1 || g.bh > AB - 1) {
+    g.mode = 2;
+  } else if (bx0 < 0 || bx1 >= W) {
+    // stage the real columns the box's columns reflect onto (one fold at most)
+    int32_t lo, hi;
+    const bool ok = W > 1 && bx0 > -W && bx1 < 2 * W - 1;
+    if (bx0 < 0 && bx1 >= W) { lo = 0; hi = W - 1; }
+    else if (bx0 < 0) { lo = bx1 < 0 ? -bx1 : 0; hi = imax(-bx0, bx1); }
+    else { lo = bx0 > W - 1 ? 2 * (W - 1) - bx1 : imin(bx0, 2 * (W - 1) - bx1); hi = bx0 > W - 1 ? 2 * (W - 1) - bx0 : W - 1; }
+    g.ra = lo; g.rb = hi;
+    g.mode = ok && hi - lo + 1 <= AB - 1 ? 1 : 2;
+  }
+}
+
+// Lane r (and r + 32) stages box row r (reflected source row): raw aligned
+// chunks; rowoff[r] = r * pitch + the row's byte phase.
+ALB_D void a_tile_stage(const AImg& k, const ATile& g, int lane, uint8_t* box, int32_t* rowoff) {
+  if (g.mode == 2) return;
+  const int span = 3 * (g.rb - g.ra + 1);
+  for (int r = lane; r < g.bh; r += 32) {
+    const int ry = reflect101(g.by0 + r, k.H);
+    const uintptr_t first = reinterpret_cast<uintptr_t>(k.src) + (uintptr_t)((int64_t)ry * k.sstride) +
+                            (uintptr_t)(3 * g.ra);
+    const uintptr_t c0 = first & ~uintptr_t(15);
+    const int ph = (int)(first - c0);
+    rowoff[r] = r * APITCH + ph;
+    const int nch = (ph + span + 15) >> 4;
+    uint8_t* d = box + r * APITCH;
+    for (int j = 0; j < nch; j++) cp_async16(d + 16 * j, reinterpret_cast<const void*>(c0 + 16 * j));
+  }
+}
+
+ALB_D void a_store3(uint8_t* od, uint32_t r, uint32_t g, uint32_t b) {
+  od[0] = (uint8_t)r; od[1] = (uint8_t)g; od[2] = (uint8_t)b;
+}
+
+ALB_D void a_tile_compute(const AImg& k, const ATile& g, int lane, const uint8_t* __restrict__ box,
+                          const int32_t* __restrict__ rowoff) {
+  const int32_t col = imin(lane, g.tw - 1);             // lanes past the tile edge follow its last column
+  const bool store = lane < g.tw;
+  uint8_t* od = k.dst + (int64_t)g.oy0 * k.dstride + 3 * (int64_t)(g.ox0 + lane);
+  const int32_t q1 = (int32_t)k.q[1], q4 = (int32_t)k.q[4];
+  if (g.mode != 2) {
+    // box-relative Q16 coordinates plus the Q16 -> Q5 rounding bias
+    int32_t X = (int32_t)(g.X00 - 65536 * (int64_t)g.bx0) + (int32_t)k.q[0] * col + 1024;
+    int32_t Y = (int32_t)(g.Y00 - 65536 * (int64_t)g.by0) + (int32_t)k.q[3] * col + 1024;
+    if (g.mode == 0) {
+#pragma unroll 2
+      for (int r = 0; r < g.th; r++, X += q1, Y += q4, od += k.dstride) {
+        const int32_t ix = X >> 16, fx = (X >> 11) & 31, iy = Y >> 16, fy = (Y >> 11) & 31;
+        const int o = 3 * ix;
+        uint32_t tl, th2, bl, bh2;
+        taps_row(box, rowoff[iy] + o, tl, th2);
+        taps_row(box, rowoff[iy + 1] + o, bl, bh2);
+        const uint32_t wx = (uint32_t)(32 + 255 * fx), wy = (uint32_t)(32 + 255 * fy);   // (32 - f) | f << 8
+        const uint32_t hr = __dp4a(__byte_perm(tl, th2, 0x0030), wx, 0u), br = __dp4a(__byte_perm(bl, bh2, 0x0030), wx, 0u);
+        const uint32_t hg = __dp4a(__byte_perm(tl, th2, 0x0041), wx, 0u), bg = __dp4a(__byte_perm(bl, bh2, 0x0041), wx, 0u);
+        const uint32_t hb = __dp4a(__byte_perm(tl, th2, 0x0052), wx, 0u), bb = __dp4a(__byte_perm(bl, bh2, 0x0052), wx, 0u);
+        const uint32_t vr = __dp2a_lo(__byte_perm(hr, br, 0x5410), wy, 512u) >> 10;
+        const uint32_t vg = __dp2a_lo(__byte_perm(hg, bg, 0x5410), wy, 512u) >> 10;
+        const uint32_t vb = __dp2a_lo(__byte_perm(hb, bb, 0x5410), wy, 512u) >> 10;
+        if (store) a_store3(od, vr, vg, vb);
+      }
+    } else {
+      const int32_t W = k.W;
+      for (int r = 0; r < g.th; r++, X += q1, Y += q4, od += k.dstride) {
+        const int32_t ix = X >> 16, fx = (X >> 11) & 31, iy = Y >> 16, fy = (Y >> 11) & 31;
+        const int o0 = rowoff[iy], o1 = rowoff[iy + 1];
+        const int xa = 3 * (reflect101(g.bx0 + ix, W) - g.ra), xb = 3 * (reflect101(g.bx0 + ix + 1, W) - g.ra);
+        const int w11 = fx * fy, w01 = 32 * fx - w11, w10 = 32 * fy - w11, w00 = 1024 - 32 * fx - 32 * fy + w11;
+        uint32_t v[3];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          const int acc = w00 * box[o0 + xa + c] + w01 * box[o0 + xb + c] + w10 * box[o1 + xa + c] + w11 * box[o1 + xb + c];
+          v[c] = (uint32_t)((acc + 512) >> 10);
+        }
+        if (store) a_store3(od, v[0], v[1], v[2]);
+      }
+    }
+  } else {
+    // footprint too large for the box: taps straight from global memory
+    const int32_t W = k.W, H = k.H;
+    int64_t X = g.X00 + k.q[0] * col + 1024, Y = g.Y00 + k.q[3] * col + 1024;
+    for (int r = 0; r < g.th; r++, X += k.q[1], Y += k.q[4], od += k.dstride) {
+      const int64_t xq = X >> 11, yq = Y >> 11;
+      const int fx = (int)(xq & 31), fy = (int)(yq & 31);
+      const int sx0 = reflect101(xq >> 5, W), sx1 = reflect101((xq >> 5) + 1, W);
+      const int sy0 = reflect101(yq >> 5, H), sy1 = reflect101((yq >> 5) + 1, H);
+      const int w11 = fx * fy, w01 = 32 * fx - w11, w10 = 32 * fy - w11, w00 = 1024 - 32 * fx - 32 * fy + w11;
+      const uint8_t* ra = k.src + (int64_t)sy0 * k.sstride;
+      const uint8_t* rbp = k.src + (int64_t)sy1 * k.sstride;
+      uint32_t v[3];
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        const int acc = w00 * ra[3 * sx0 + c] + w01 * ra[3 * sx1 + c] + w10 * rbp[3 * sx0 + c] + w11 * rbp[3 * sx1 + c];
+        v[c] = (uint32_t)((acc + 512) >> 10);
+      }
+      if (store) a_store3(od, v[0], v[1], v[2]);
+    }
+  }
+}
+
+struct AShared {       // dynamic shared memory of k_warp_affine3
+  uint8_t box[AWARP][2][AB * APITCH + 16];   // +16: the last row's tap read past the staged bytes
+  int32_t rowoff[AWARP][2][AB];
+  AImg simg[AWARP][2];
+  ATile stile[AWARP][2];
+};
+
+__global__ void __launch_bounds__(32 * AWARP) k_warp_affine3(Plan plan, ImgList in, ImgList out, PrmList prm) {
+  extern __shared__ __align__(16) uint8_t aw_dyn[];
+  AShared& sm = *reinterpret_cast<AShared*>(aw_dyn);
+  int32_t it0, it1;
+  item_range(plan, it0, it1);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int32_t item = it0 + w;
+  if (item >= it1) return;
+  {
+    AImg k;
+    ATile g;
+    a_load_img(plan, in, out, prm, item_image(plan, item), k);
+    a_tile_geo(k, item, g);
+    if (lane == 0) { sm.simg[w][0] = k; sm.stile[w][0] = g; }
+    a_tile_stage(k, g, lane, sm.box[w][0], sm.rowoff[w][0]);
+  }
+  cp_async_commit();
+  int buf = 0;
+  for (; item < it1; item += AWARP, buf ^= 1) {
+    const int32_t nitem = item + AWARP;
+    if (nitem < it1) {
+      __syncwarp();
+      AImg k = sm.simg[w][buf];
+      if (nitem >= k.prefix + k.ntiles) {
+        int32_t b = k.b;
+        while (nitem >= plan.prefix[b + 1]) b++;
+        a_load_img(plan, in, out, prm, b, k);
+      }
+      ATile g;
+      a_tile_geo(k, nitem, g);
+      __syncwarp();
+      if (lane == 0) { sm.simg[w][buf ^ 1] = k; sm.stile[w][buf ^ 1] = g; }
+      a_tile_stage(k, g, lane, sm.box[w][buf ^ 1], sm.rowoff[w][buf ^ 1]);
+    }
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncwarp();
+    a_tile_compute(sm.simg[w][buf], sm.stile[w][buf], lane, sm.box[w][buf], sm.rowoff[w][buf]);
+    __syncwarp();      // every lane is done with box[buf] before it is refilled
   }
   cp_async_wait<0>();
 }
@@ -666,6 +881,17 @@ alb_status launch_tile_geometric(int32_t tid, const Plan& plan, const ImgList& i
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_resize_rows, 32 * RWARP, smem);
     k_resize_rows<<<(per_sm < 1 ? 1 : per_sm) * sm_count(), 32 * RWARP, smem, st>>>(plan, in, out, prm);
+    ALB_CUDA(cudaGetLastError());
+    return ALB_OK;
+  }
+  if (affine && !mask) {
+    k_plan_tiles<<<1, 1024, 0, st>>>(out, plan.n, AT_W, AT_H, prefix, tiles_x, chk);
+    ALB_CUDA(cudaGetLastError());
+    const int smem = (int)sizeof(AShared);
+    ALB_CUDA(cudaFuncSetAttribute(k_warp_affine3, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_warp_affine3, 32 * AWARP, smem);
+    k_warp_affine3<<<(per_sm < 1 ? 1 : per_sm) * sm_count(), 32 * AWARP, smem, st>>>(plan, in, out, prm);
     ALB_CUDA(cudaGetLastError());
     return ALB_OK;
   }
