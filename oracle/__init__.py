@@ -110,6 +110,14 @@ def _declare(L):
     L.orc_chain_image.argtypes = [P(Params), P(C.c_double), P(C.c_double), u8p, C.c_int, C.c_int,
                                   C.c_int64, P(C.c_uint16)]
     L.orc_chain_image.restype = C.c_int
+    L.orc_chain_image_jitter.argtypes = L.orc_chain_image.argtypes
+    L.orc_chain_image_jitter.restype = C.c_int
+    L.orc_jitter_mode1.argtypes = [P(Params), u8p, C.c_size_t]
+    L.orc_jitter_mode1.restype = None
+    L.orc_contrast_pivot.argtypes = [u8p, C.c_size_t]
+    L.orc_contrast_pivot.restype = C.c_int
+    L.orc_jitter_op.argtypes = [C.c_int, C.c_int]
+    L.orc_jitter_op.restype = C.c_int
     dp = P(C.c_double)
     L.orc_warp_photo_fwd.argtypes = [C.c_int] * 4 + [dp] * 10
     L.orc_warp_photo_bwd.argtypes = [C.c_int] * 4 + [dp] * 11
@@ -248,18 +256,37 @@ def normalize_consts(mean=IMAGENET_MEAN, std=IMAGENET_STD):
     return k, mm
 
 
-def chain_image(p: Params, img: np.ndarray, mean=IMAGENET_MEAN, std=IMAGENET_STD) -> np.ndarray:
-    """bf16 bit patterns, shape (3, out_h, out_w)."""
+def chain_image(p: Params, img: np.ndarray, mean=IMAGENET_MEAN, std=IMAGENET_STD, jitter: int = 0) -> np.ndarray:
+    """bf16 bit patterns, shape (3, out_h, out_w).  jitter 0: fixed order,
+    constant contrast pivot, float saturation; 1: the record's random order,
+    image-mean contrast pivot, uint8 after each jitter op."""
     img = np.ascontiguousarray(img, dtype=np.uint8)
     h, w, _ = img.shape
     m = np.ascontiguousarray(mean, dtype=np.float64)
     s = np.ascontiguousarray(std, dtype=np.float64)
     out = np.zeros((3, p.out_h, p.out_w), dtype=np.uint16)
-    rc = lib().orc_chain_image(C.byref(p), _ptr(m, C.c_double), _ptr(s, C.c_double),
-                               _ptr(img, C.c_uint8), h, w, w * 3, _ptr(out, C.c_uint16))
+    fn = lib().orc_chain_image_jitter if jitter else lib().orc_chain_image
+    rc = fn(C.byref(p), _ptr(m, C.c_double), _ptr(s, C.c_double), _ptr(img, C.c_uint8), h, w, w * 3,
+            _ptr(out, C.c_uint16))
     if rc != 0:
         raise ValueError("chain failed")
     return out
+
+
+def jitter_mode1(p: Params, img: np.ndarray) -> np.ndarray:
+    """The three jitter ops of mode 1 in the record's order on a uint8 RGB image."""
+    out = np.ascontiguousarray(img, dtype=np.uint8).copy()
+    lib().orc_jitter_mode1(C.byref(p), _ptr(out, C.c_uint8), out.size // 3)
+    return out
+
+
+def contrast_pivot(img: np.ndarray) -> int:
+    a = np.ascontiguousarray(img, dtype=np.uint8)
+    return int(lib().orc_contrast_pivot(_ptr(a, C.c_uint8), a.size // 3))
+
+
+def jitter_op(k: int, i: int) -> int:
+    return int(lib().orc_jitter_op(k, i))
 
 
 # ---------------------------------------------------------------- float path

@@ -20,8 +20,10 @@
  * brightness transforms, horizontal flip + random sized crop on images,
  * boxes and masks, crops / rotations / reflections / scaling with masks
  * transformed the same way) but defines none of them mathematically.  The
- * definitions below are the readings written down in DESIGN.md ("Readings of
- * the paper"); each function states the one it follows.
+ * definitions below are this project's readings of the paper (pixel-centre
+ * coordinates, round-half-even saturation, reflect-101 borders, 5-bit
+ * fixed-point bilinear weights, Q16 affine coefficients); each function
+ * states the reading it follows.
  *
  * Parity status: every function is pinned by tests/test_oracle_*.py against
  * closed forms, library routines (numpy, Python fractions, colorsys, torch
@@ -201,7 +203,8 @@ static int64_t rne_div(int64_t num, int64_t den) {
 }
 
 /* ======================================================================
- * Parameter geometry (readings C6 / C-R in the design doc)
+ * Parameter geometry: affine maps about the pixel-centre image centre, and
+ * the half-pixel resize map
  * ====================================================================== */
 
 /* Rotation about the image centre c = ((W-1)/2, (H-1)/2) by angle degrees
@@ -248,7 +251,7 @@ EXPORT int orc_output_shape(const orc_params* p, int h, int w, int* oh, int* ow)
 }
 
 /* ======================================================================
- * Parameter sampling (reading S in the design doc): one Philox word stream per
+ * Parameter sampling: one Philox word stream per
  * (seed, stream id, image index); the probability draw comes first and all
  * parameter draws follow whether or not the transform is applied.
  * Size-changing transforms are always applied.
@@ -374,6 +377,7 @@ EXPORT int orc_sample_params(const orc_cfg* cfg, uint64_t seed, uint64_t stream_
       p->beta = stream_uniform(&s, cfg->lo[2], cfg->hi[2]);   /* brightness factor b */
       p->alpha = stream_uniform(&s, cfg->lo[2], cfg->hi[2]);  /* contrast factor c */
       p->sat = stream_uniform(&s, cfg->lo[2], cfg->hi[2]);    /* saturation factor s */
+      p->k = stream_randint(&s, 5);   /* order of the three jitter ops, 0..5 (used by jitter mode 1) */
       break;
     default:
       return ORC_EINVAL;
@@ -382,7 +386,8 @@ EXPORT int orc_sample_params(const orc_cfg* cfg, uint64_t seed, uint64_t stream_
 }
 
 /* ======================================================================
- * Per-channel 256-entry look-up tables (readings L-* in the design doc)
+ * Per-channel 256-entry look-up tables, each entry computed in float64 and
+ * saturated with round-half-even
  * ====================================================================== */
 EXPORT int orc_build_lut(const orc_params* p, uint8_t lut[3][256]) {
   for (int c = 0; c < 3; c++)
@@ -429,7 +434,7 @@ EXPORT void orc_equalize_lut(const uint64_t hist[256], uint8_t lut[256]) {
 }
 
 /* ======================================================================
- * Colour space (reading HSV in the design doc): Smith's hexcone, float64.
+ * Colour space: Smith's hexcone HSV, float64.
  * ====================================================================== */
 static void shift_hsv_pixel(const double shift[3], const uint8_t in[3], uint8_t out[3]) {
   double r = in[0], g = in[1], b = in[2];
@@ -726,7 +731,7 @@ EXPORT int orc_apply_boxes(const orc_params* p, int h, int w, const float* in, i
 }
 
 /* ======================================================================
- * Fused chain (reading F in the design doc): RandomResizedCrop window resized
+ * Fused chain: RandomResizedCrop window resized
  * to out_h x out_w (Q5 bilinear), optional h-flip, brightness/contrast LUT,
  * saturation in float32, Normalize to bfloat16 NCHW.  Written as the plain
  * sequence of its steps with every intermediate materialised.
@@ -748,6 +753,82 @@ EXPORT void orc_normalize_consts(const double mean[3], const double stdv[3], flo
     k[c] = (float)(1.0 / (255.0 * stdv[c]));
     m[c] = (float)(-mean[c] / stdv[c]);
   }
+}
+
+static uint8_t sat_rne_f32(float v) {
+  float r = rintf(v);
+  if (r < 0.0f) r = 0.0f;
+  if (r > 255.0f) r = 255.0f;
+  return (uint8_t)r;
+}
+
+/* The three jitter ops of mode 1 in the order of permutation index k
+ * (0 BCS, 1 BSC, 2 CBS, 3 CSB, 4 SBC, 5 SCB; B = 0, C = 1, S = 2). */
+EXPORT int orc_jitter_op(int k, int i) {
+  static const int perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  if (k < 0 || k > 5 || i < 0 || i > 2) return -1;
+  return perm[k][i];
+}
+
+/* Contrast pivot of a uint8 RGB image: the round-half-even mean of the
+ * integer BT.601 grey values rne((299 R + 587 G + 114 B) / 1000). */
+EXPORT int orc_contrast_pivot(const uint8_t* img, size_t npx) {
+  int64_t sum = 0;
+  for (size_t i = 0; i < npx; i++) {
+    sum += rne_div(299 * (int64_t)img[3 * i] + 587 * (int64_t)img[3 * i + 1] + 114 * (int64_t)img[3 * i + 2], 1000);
+  }
+  return (int)rne_div(sum, (int64_t)npx);
+}
+
+/* Colour jitter, mode 1 (the torchvision / PIL reading: a random order of
+ * the three ops, each producing a uint8 image):
+ *   B: v -> sat_rne(b v)                                  (float64)
+ *   C: v -> sat_rne(m + c (v - m)), m = contrast pivot of the image as it
+ *      is when C runs                                     (float64)
+ *   S: per pixel, grey = 0.299 R + 0.587 G + 0.114 B in float32 fmas,
+ *      v -> sat_rne(fmaf(s, v - grey, grey))              (float32)
+ * applied in place to npx RGB pixels. */
+EXPORT void orc_jitter_mode1(const orc_params* p, uint8_t* img, size_t npx) {
+  for (int i = 0; i < 3; i++) {
+    int op = orc_jitter_op(p->k, i);
+    if (op == 0) {
+      for (size_t j = 0; j < 3 * npx; j++) img[j] = sat_rne(p->beta * (double)img[j]);
+    } else if (op == 1) {
+      double m = (double)orc_contrast_pivot(img, npx);
+      for (size_t j = 0; j < 3 * npx; j++) img[j] = sat_rne(m + p->alpha * ((double)img[j] - m));
+    } else {
+      float sf = (float)p->sat;
+      for (size_t j = 0; j < npx; j++) {
+        float r = img[3 * j], g = img[3 * j + 1], b = img[3 * j + 2];
+        float grey = fmaf(0.114f, b, fmaf(0.587f, g, 0.299f * r));
+        for (int c = 0; c < 3; c++) img[3 * j + c] = sat_rne_f32(fmaf(sf, (float)img[3 * j + c] - grey, grey));
+      }
+    }
+  }
+}
+
+/* The chain with jitter mode 1: crop + resize, h-flip, the three jitter
+ * ops in the record's order (uint8 after each), Normalize -> bf16 NCHW. */
+EXPORT int orc_chain_image_jitter(const orc_params* p, const double mean[3], const double stdv[3],
+                                  const uint8_t* in, int h, int w, int64_t is, uint16_t* out) {
+  int oh = p->out_h, ow = p->out_w;
+  size_t npx = (size_t)oh * ow;
+  uint8_t* resized = (uint8_t*)malloc(npx * 3);
+  uint8_t* cur = (uint8_t*)malloc(npx * 3);
+  if (!resized || !cur) { free(resized); free(cur); return ORC_EINVAL; }
+  orc_params rp = *p;
+  rp.tid = T_RANDOM_RESIZED_CROP; rp.apply = 1;
+  apply_geometric(&rp, in, h, w, 3, is, resized, (int64_t)ow * 3, 0);
+  orc_params fp = *p;
+  fp.tid = T_HFLIP; fp.apply = p->flip;
+  apply_geometric(&fp, resized, oh, ow, 3, (int64_t)ow * 3, cur, (int64_t)ow * 3, 0);
+  orc_jitter_mode1(p, cur, npx);
+  float kc[3], mc[3];
+  orc_normalize_consts(mean, stdv, kc, mc);
+  for (int c = 0; c < 3; c++)
+    for (size_t i = 0; i < npx; i++) out[(size_t)c * npx + i] = f32_to_bf16_rne(fmaf((float)cur[3 * i + c], kc[c], mc[c]));
+  free(resized); free(cur);
+  return ORC_OK;
 }
 
 EXPORT int orc_chain_image(const orc_params* p, const double mean[3], const double stdv[3],
@@ -796,7 +877,7 @@ EXPORT int orc_chain_image(const orc_params* p, const double mean[3], const doub
 }
 
 /* ======================================================================
- * Differentiable float path (reading D in the design doc), float64 throughout.
+ * Differentiable float path, float64 throughout.
  * x: [B][C][H][W]; per image angle (deg), scale, tx, ty (fractions of W, H),
  * alpha, beta, gamma.  w = bilinear warp of x with zero border;
  * z = alpha w + beta; y = clamp(z, 0, 1)^gamma.

@@ -226,6 +226,7 @@ ALB_HD int sample_one(const alb_sample_cfg& cfg, uint64_t seed, uint64_t sid, ui
       p.beta = ph_uniform(s, cfg.lo[2], cfg.hi[2]);   // brightness factor
       p.alpha = ph_uniform(s, cfg.lo[2], cfg.hi[2]);  // contrast factor
       p.sat = ph_uniform(s, cfg.lo[2], cfg.hi[2]);    // saturation factor
+      p.k = ph_randint(s, 5);                          // order of the jitter ops, 0..5 (jitter mode 1)
       break;
     default:
       return ALB_EINVAL;
