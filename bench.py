@@ -314,8 +314,23 @@ def fused_pipeline(dev, stream, steps=3, warmup=2, n=FUSED_N):
     tf = res["fused"]["ms"] / 1e3
     res["fused_gbs"] = (rd + wr) / tf / 1e9
     res["speedup_vs_plain"] = res["plain"]["ms"] / res["fused"]["ms"]
+    # jitter mode 1: per-image random order and image-mean contrast pivot (a
+    # per-image reduction before the write pass), fused vs plain
+    jcfg = A.chain_cfg(jitter=1)
+    wsj = A.workspace(A.alb_batch_workspace_size(jcfg, FUSED_N, A.MODE_PLAIN), dev)
+    jb = A.alb_autotune_batch(jcfg, FUSED_N, pdev, din.dev, out, wsj, reps=2, stream=stream)
+    jres = {"schedule": {"rows_per_item": jb.tile_h, "ctas_per_sm": jb.ctas_per_sm}}
+    for name, mode in (("fused", A.MODE_FUSED), ("plain", A.MODE_PLAIN)):
+        def runj(mode=mode):
+            A.alb_sample_params_batch(cfg, SEED, 20, 0, FUSED_N, din.dev, pdev, stream=stream)
+            A.alb_apply_batch(jcfg, FUSED_N, pdev, din.dev, out, mode, wsj, stream=stream)
+        runj()
+        t = ev_time(runj, stream, steps)
+        jres[name] = dict(images_per_s=FUSED_N / t, ms=t * 1e3)
+    jres["speedup_vs_plain"] = jres["plain"]["ms"] / jres["fused"]["ms"]
+    res["jitter_random_order_mean_pivot"] = jres
     res["workload"] = "4096 ragged u8 RGB images H,W~U[256,1024] -> RRC 224 + flip + jitter + Normalize bf16 NCHW"
-    del din, out, wsf, wsp
+    del din, out, wsf, wsp, wsj
     torch.cuda.empty_cache()
     return res
 

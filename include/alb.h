@@ -139,7 +139,12 @@ typedef struct alb_chain_cfg {
                             ctas_per_sm == 0: the schedule alb_autotune_batch cached
                             for this (device, out_h, out_w, batch-size bucket), else
                             8 rows at the occupancy limit */
-  int32_t reserved;
+  int32_t jitter;        /* colour jitter: 0 = brightness b then contrast c about 128 as one
+                            table, then saturation s in float32 (not rounded); 1 = the three
+                            ops in the record's random order k (0..5: BCS BSC CBS CSB SBC SCB),
+                            each producing uint8: B v -> rne(b v); C v -> rne(m + c (v - m)),
+                            m = rounded mean of the integer BT.601 grey of the image at that
+                            point (a per-image reduction); S the float32 blend, rounded */
 } alb_chain_cfg;        /* 72 bytes */
 
 enum { ALB_MODE_FUSED = 0, ALB_MODE_PLAIN = 1 };

@@ -60,7 +60,7 @@ class SampleCfg(C.Structure):
 
 class ChainCfg(C.Structure):
     _fields_ = [("out_h", C.c_int32), ("out_w", C.c_int32), ("mean", C.c_double * 3), ("std", C.c_double * 3),
-                ("tile_h", C.c_int32), ("tile_w", C.c_int32), ("ctas_per_sm", C.c_int32), ("reserved", C.c_int32)]
+                ("tile_h", C.c_int32), ("tile_w", C.c_int32), ("ctas_per_sm", C.c_int32), ("jitter", C.c_int32)]
 
 
 assert C.sizeof(Image) == 32 and C.sizeof(Params) == 232 and C.sizeof(SampleCfg) == 88 and C.sizeof(ChainCfg) == 72
@@ -213,12 +213,13 @@ IMAGENET_MEAN = (0.485, 0.456, 0.406)
 IMAGENET_STD = (0.229, 0.224, 0.225)
 
 
-def chain_cfg(out_h=224, out_w=224, mean=IMAGENET_MEAN, std=IMAGENET_STD, tile_h=0, tile_w=0, ctas_per_sm=0):
+def chain_cfg(out_h=224, out_w=224, mean=IMAGENET_MEAN, std=IMAGENET_STD, tile_h=0, tile_w=0, ctas_per_sm=0,
+              jitter=0):
     c = ChainCfg()
     c.out_h, c.out_w = out_h, out_w
     for i in range(3):
         c.mean[i], c.std[i] = mean[i], std[i]
-    c.tile_h, c.tile_w, c.ctas_per_sm = tile_h, tile_w, ctas_per_sm
+    c.tile_h, c.tile_w, c.ctas_per_sm, c.jitter = tile_h, tile_w, ctas_per_sm, jitter
     return c
 
 

@@ -20,6 +20,9 @@
 
 namespace alb {
 
+constexpr int kBandMax = 32;   // output rows per work item, at most
+constexpr int kBandMaxP = 32;  // rows per pivot item
+
 struct ChainK {
   float k[3], m[3];  // Normalize: y = fma(x, k_c, m_c)
   int32_t oh, ow;
@@ -108,6 +111,129 @@ ALB_D void chain_saturate(const uint32_t rgb[3], float s, float out[3]) {
 
 ALB_D __nv_bfloat16 chain_normalize(float v, float k, float m) { return __float2bfloat16_rn(__fmaf_rn(v, k, m)); }
 
+// ---------------------------------------------------------------- jitter mode 1
+// Brightness (B = 0), contrast (C = 1) and saturation (S = 2) in a per-image
+// order, permutation index k in 0..5 (lexicographic: BCS BSC CBS CSB SBC SCB),
+// each op producing uint8: B and C through per-image tables (B: sat_rne(b v);
+// C: sat_rne(m + c (v - m)) with m the image's contrast pivot, both float64),
+// S per pixel in float32 fmas rounded half-even to uint8.
+ALB_D int jitter_op(int k, int i) {
+  // two bits per position, six bits per permutation
+  constexpr uint64_t code = (uint64_t)(0 | 1 << 2 | 2 << 4) | (uint64_t)(0 | 2 << 2 | 1 << 4) << 6 |
+                            (uint64_t)(1 | 0 << 2 | 2 << 4) << 12 | (uint64_t)(1 | 2 << 2 | 0 << 4) << 18 |
+                            (uint64_t)(2 | 0 << 2 | 1 << 4) << 24 | (uint64_t)(2 | 1 << 2 | 0 << 4) << 30;
+  return (int)((code >> (6 * k + 2 * i)) & 3u);
+}
+
+ALB_D uint32_t sat_rne_f(float v) {
+  const float r = fminf(fmaxf(rintf(v), 0.0f), 255.0f);
+  return (uint32_t)r;
+}
+
+// saturation of jitter mode 1: the float32 blend of chain_saturate, rounded to uint8
+ALB_D void jitter_saturate(uint32_t rgb[3], float s) {
+  const float r = (float)rgb[0], g = (float)rgb[1], b = (float)rgb[2];
+  const float grey = __fmaf_rn(0.114f, b, __fmaf_rn(0.587f, g, __fmul_rn(0.299f, r)));
+  uint32_t o[3];
+#pragma unroll
+  for (int c = 0; c < 3; c++) o[c] = sat_rne_f(__fmaf_rn(s, __fsub_rn((float)rgb[c], grey), grey));
+  rgb[0] = o[0]; rgb[1] = o[1]; rgb[2] = o[2];
+}
+
+// integer BT.601 grey, round half to even: rne((299 R + 587 G + 114 B) / 1000)
+ALB_D uint32_t grey_bt601(const uint32_t rgb[3]) {
+  const uint32_t num = 299u * rgb[0] + 587u * rgb[1] + 114u * rgb[2];
+  uint32_t q = num / 1000u;
+  const uint32_t r = num - 1000u * q;
+  if (r > 500u || (r == 500u && (q & 1u))) q++;
+  return q;
+}
+
+// ops [from, to) of the image's order; tb / tc: its B and C tables
+ALB_D void jitter_ops(uint32_t rgb[3], int k, int from, int to, const uint8_t* tb, const uint8_t* tc, float s) {
+  for (int i = from; i < to; i++) {
+    const int op = jitter_op(k, i);
+    if (op == 2) {
+      jitter_saturate(rgb, s);
+    } else {
+      const uint8_t* t = op == 0 ? tb : tc;
+      rgb[0] = t[rgb[0]]; rgb[1] = t[rgb[1]]; rgb[2] = t[rgb[2]];
+    }
+  }
+}
+
+ALB_D int jitter_pos_c(int k) { return jitter_op(k, 0) == 1 ? 0 : (jitter_op(k, 1) == 1 ? 1 : 2); }
+
+// Per image: B table (which == 0), or the C table from the image's grey sum (which == 1).
+__global__ void k_jitter_luts(int32_t n, const alb_params* __restrict__ prm, const unsigned long long* __restrict__ sums,
+                              int64_t npx, int32_t which, uint8_t* __restrict__ luts) {
+  const int b = blockIdx.x, v = threadIdx.x;
+  if (b >= n) return;
+  const alb_params& p = prm[b];
+  uint8_t* L = luts + (int64_t)b * 512;
+  if (which == 0) {
+    L[v] = sat_rne_d(p.beta * (double)v);
+  } else {
+    const uint64_t sum = sums[b];
+    uint64_t q = sum / (uint64_t)npx;
+    const uint64_t r = sum - q * (uint64_t)npx;
+    if (2 * r > (uint64_t)npx || (2 * r == (uint64_t)npx && (q & 1))) q++;
+    const double m = (double)q;
+    L[256 + v] = sat_rne_d(m + p.alpha * ((double)v - m));
+  }
+}
+
+// Contrast pivot sums of the fused path: per output pixel the resized value
+// with the ops ordered before C applied, its integer grey, summed per image.
+// Item = (image, band of rows), grid-stride; flip does not change the sum.
+__global__ void __launch_bounds__(256) k_chain_pivot(int32_t n, const alb_params* __restrict__ prm,
+                                                     const alb_image* __restrict__ imgs,
+                                                     const uint8_t* __restrict__ luts, ChainK K, int32_t band,
+                                                     unsigned long long* __restrict__ sums) {
+  __shared__ uint8_t s_tb[256];
+  __shared__ int32_t s_col[1024];
+  __shared__ int32_t s_row[kBandMaxP];
+  __shared__ unsigned long long s_part[8];
+  const int32_t bands = (K.oh + band - 1) / band;
+  const int64_t total = (int64_t)n * bands;
+  int32_t cached = -1;
+  for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
+    const int32_t b = (int32_t)(item / bands), r0 = (int32_t)(item - (int64_t)b * bands) * band;
+    const int32_t r1 = imin(r0 + band, K.oh);
+    const alb_params& p = prm[b];
+    __syncthreads();
+    if (b != cached) {
+      for (int i = threadIdx.x; i < 256; i += blockDim.x) s_tb[i] = luts[(int64_t)b * 512 + i];
+      for (int x = threadIdx.x; x < K.ow; x += blockDim.x) s_col[x] = chain_q5(x, p.cw, K.ow);
+      cached = b;
+    }
+    if (threadIdx.x < r1 - r0) s_row[threadIdx.x] = chain_q5(r0 + threadIdx.x, p.ch, K.oh);
+    __syncthreads();
+    const alb_image im = imgs[b];
+    const uint8_t* win = (const uint8_t*)im.data + (int64_t)p.y0 * im.row_stride + 3 * (int64_t)p.x0;
+    const int pos_c = jitter_pos_c(p.k);
+    const float s = (float)p.sat;
+    uint64_t acc = 0;
+    const int32_t npx = (r1 - r0) * K.ow;
+    for (int32_t i = threadIdx.x; i < npx; i += blockDim.x) {
+      const int32_t yy = i / K.ow, x = i - yy * K.ow;
+      uint32_t rgb[3];
+      chain_bilinear(win, im.row_stride, p.ch, p.cw, s_col[x], s_row[yy], rgb);
+      jitter_ops(rgb, p.k, 0, pos_c, s_tb, s_tb, s);
+      acc += grey_bt601(rgb);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long t = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += s_part[w];
+      atomicAdd(&sums[b], t);
+    }
+  }
+}
+
 // per-image brightness-then-contrast table c (b v - 128) + 128 (float64, half even)
 __global__ void k_chain_luts(int32_t n, const alb_params* __restrict__ prm, uint8_t* __restrict__ luts) {
   const int b = blockIdx.x, v = threadIdx.x;
@@ -124,14 +250,17 @@ __global__ void k_chain_luts(int32_t n, const alb_params* __restrict__ prm, uint
 // Per image the column coordinates (flip folded in) and the colour table live
 // in shared memory; per band the row coordinates are computed once.  A thread
 // produces two horizontally adjacent pixels, stored as one bf16x2 per channel.
-constexpr int kBandMax = 32;
 
+// MODE 0: brightness/contrast table (fixed order, pivot 128), float saturation.
+// MODE 1: jitter mode 1 (per-image order; B and C tables [n][512]; uint8 after each op).
+template <int MODE>
 __global__ void __launch_bounds__(256) k_chain_fused(int32_t n, const alb_params* __restrict__ prm,
                                                      const alb_image* __restrict__ imgs,
                                                      const uint8_t* __restrict__ luts, ChainK K, int32_t band,
                                                      int32_t* __restrict__ queue, __nv_bfloat16* __restrict__ out) {
+  constexpr int TAB = MODE == 0 ? 256 : 512;
   __shared__ int32_t s_item;
-  __shared__ uint8_t s_lut[256];
+  __shared__ uint8_t s_lut[TAB];
   __shared__ int32_t s_col[1024];
   __shared__ int32_t s_row[kBandMax];
   const int32_t bands = (K.oh + band - 1) / band;
@@ -147,7 +276,7 @@ __global__ void __launch_bounds__(256) k_chain_fused(int32_t n, const alb_params
     const int32_t b = item / bands, r0 = (item - b * bands) * band, r1 = imin(r0 + band, K.oh);
     const alb_params& p = prm[b];
     if (b != cached) {
-      for (int i = threadIdx.x; i < 256; i += blockDim.x) s_lut[i] = luts[(int64_t)b * 256 + i];
+      for (int i = threadIdx.x; i < TAB; i += blockDim.x) s_lut[i] = luts[(int64_t)b * TAB + i];
       for (int x = threadIdx.x; x < K.ow; x += blockDim.x) {
         const int32_t xr = p.flip ? K.ow - 1 - x : x;  // output column x shows resized column xr
         s_col[x] = chain_q5(xr, p.cw, K.ow);
@@ -169,11 +298,18 @@ __global__ void __launch_bounds__(256) k_chain_fused(int32_t n, const alb_params
         uint32_t a[3], c[3];
         chain_bilinear(win, im.row_stride, p.ch, p.cw, s_col[x], yq, a);
         chain_bilinear(win, im.row_stride, p.ch, p.cw, s_col[x + 1], yq, c);
-#pragma unroll
-        for (int q = 0; q < 3; q++) { a[q] = s_lut[a[q]]; c[q] = s_lut[c[q]]; }
         float va[3], vc[3];
-        chain_saturate(a, s, va);
-        chain_saturate(c, s, vc);
+        if (MODE == 0) {
+#pragma unroll
+          for (int q = 0; q < 3; q++) { a[q] = s_lut[a[q]]; c[q] = s_lut[c[q]]; }
+          chain_saturate(a, s, va);
+          chain_saturate(c, s, vc);
+        } else {
+          jitter_ops(a, p.k, 0, 3, s_lut, s_lut + 256, s);
+          jitter_ops(c, p.k, 0, 3, s_lut, s_lut + 256, s);
+#pragma unroll
+          for (int q = 0; q < 3; q++) { va[q] = (float)a[q]; vc[q] = (float)c[q]; }
+        }
         const int64_t o = (int64_t)y * K.ow + x;
 #pragma unroll
         for (int q = 0; q < 3; q++) {
@@ -189,10 +325,16 @@ __global__ void __launch_bounds__(256) k_chain_fused(int32_t n, const alb_params
         const int32_t yy = i / K.ow, x = i - yy * K.ow, y = r0 + yy;
         uint32_t rgb[3];
         chain_bilinear(win, im.row_stride, p.ch, p.cw, s_col[x], s_row[yy], rgb);
-#pragma unroll
-        for (int q = 0; q < 3; q++) rgb[q] = s_lut[rgb[q]];
         float v[3];
-        chain_saturate(rgb, s, v);
+        if (MODE == 0) {
+#pragma unroll
+          for (int q = 0; q < 3; q++) rgb[q] = s_lut[rgb[q]];
+          chain_saturate(rgb, s, v);
+        } else {
+          jitter_ops(rgb, p.k, 0, 3, s_lut, s_lut + 256, s);
+#pragma unroll
+          for (int q = 0; q < 3; q++) v[q] = (float)rgb[q];
+        }
 #pragma unroll
         for (int q = 0; q < 3; q++) ob[q * plane + (int64_t)y * K.ow + x] = chain_normalize(v[q], K.k[q], K.m[q]);
       }
@@ -258,10 +400,49 @@ __global__ void k_plain_normalize(int32_t n, ChainK K, const float* __restrict__
   }
 }
 
+// plain path, jitter mode 1: contrast pivot sums of the images whose op at
+// position `step` is C, from the materialised uint8 image
+__global__ void k_plain_pivot(int32_t n, const alb_params* __restrict__ prm, ChainK K, int32_t step,
+                              const uint8_t* __restrict__ in, unsigned long long* __restrict__ sums) {
+  const int64_t plane = (int64_t)K.oh * K.ow;
+  const int64_t total = (int64_t)n * plane;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t b = (int32_t)(i / plane);
+    if (jitter_op(prm[b].k, step) != 1) continue;
+    const uint32_t rgb[3] = {in[3 * i], in[3 * i + 1], in[3 * i + 2]};
+    atomicAdd(&sums[b], (unsigned long long)grey_bt601(rgb));
+  }
+}
+
+// plain path, jitter mode 1: each image's op at position `step`
+__global__ void k_plain_jitter_step(int32_t n, const alb_params* __restrict__ prm, ChainK K, int32_t step,
+                                    const uint8_t* __restrict__ luts, const uint8_t* __restrict__ in,
+                                    uint8_t* __restrict__ out) {
+  const int64_t plane = (int64_t)K.oh * K.ow;
+  const int64_t total = (int64_t)n * plane;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t b = (int32_t)(i / plane);
+    const alb_params& p = prm[b];
+    uint32_t rgb[3] = {in[3 * i], in[3 * i + 1], in[3 * i + 2]};
+    const uint8_t* L = luts + (int64_t)b * 512;
+    jitter_ops(rgb, p.k, step, step + 1, L, L + 256, (float)p.sat);
+    for (int c = 0; c < 3; c++) out[3 * i + c] = (uint8_t)rgb[c];
+  }
+}
+
+__global__ void k_plain_normalize_u8(int32_t n, ChainK K, const uint8_t* __restrict__ in, __nv_bfloat16* __restrict__ out) {
+  const int64_t plane = (int64_t)K.oh * K.ow;
+  const int64_t total = (int64_t)n * plane;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = i / plane, r = i - b * plane;
+    for (int c = 0; c < 3; c++) out[(b * 3 + c) * plane + r] = chain_normalize((float)in[3 * i + c], K.k[c], K.m[c]);
+  }
+}
+
 // ---------------------------------------------------------------- launcher
 size_t chain_workspace(const alb_chain_cfg& cfg, int32_t n, int32_t mode) {
   size_t px = (size_t)n * cfg.out_h * cfg.out_w;
-  size_t b = 4096 + (size_t)n * 256;
+  size_t b = 4096 + (size_t)n * 512 + (size_t)n * 8 + 512;   // queue, tables, pivot sums
   if (mode == ALB_MODE_PLAIN) b += 2 * px * 3 + px * 3 * 4 + 1024;
   return b;
 }
@@ -280,11 +461,12 @@ static ChainK make_consts(const alb_chain_cfg& cfg) {
 // ---------------------------------------------------------------- schedule cache
 // A schedule of the fused kernel is (rows per work item, resident CTAs per
 // SM).  alb_autotune_batch times candidates on the caller's batch and keeps
-// the fastest here, per (device, out_h, out_w, batch-size bucket = ceil(log2 n));
+// the fastest here, per (device, out_h, out_w, jitter mode, batch-size bucket
+// = ceil(log2 n));
 // a cfg with tile_h == 0 and ctas_per_sm == 0 runs with the cached schedule
 // of its key, or the default (8 rows, occupancy limit) when there is none.
 struct TuneEntry {
-  int32_t dev, oh, ow, bucket;
+  int32_t dev, oh, ow, jitter, bucket;
   int32_t band, per_sm;
 };
 static std::mutex g_tune_mu;
@@ -300,7 +482,7 @@ static bool tune_lookup(int32_t dev, const alb_chain_cfg& cfg, int32_t n, int32_
   std::lock_guard<std::mutex> lock(g_tune_mu);
   const int32_t bk = size_bucket(n);
   for (const TuneEntry& e : g_tune)
-    if (e.dev == dev && e.oh == cfg.out_h && e.ow == cfg.out_w && e.bucket == bk) {
+    if (e.dev == dev && e.oh == cfg.out_h && e.ow == cfg.out_w && e.jitter == cfg.jitter && e.bucket == bk) {
       band = e.band;
       per_sm = e.per_sm;
       return true;
@@ -312,27 +494,36 @@ static void tune_store(int32_t dev, const alb_chain_cfg& cfg, int32_t n, int32_t
   std::lock_guard<std::mutex> lock(g_tune_mu);
   const int32_t bk = size_bucket(n);
   for (TuneEntry& e : g_tune)
-    if (e.dev == dev && e.oh == cfg.out_h && e.ow == cfg.out_w && e.bucket == bk) {
+    if (e.dev == dev && e.oh == cfg.out_h && e.ow == cfg.out_w && e.jitter == cfg.jitter && e.bucket == bk) {
       e.band = band;
       e.per_sm = per_sm;
       return;
     }
-  g_tune.push_back(TuneEntry{dev, cfg.out_h, cfg.out_w, bk, band, per_sm});
+  g_tune.push_back(TuneEntry{dev, cfg.out_h, cfg.out_w, cfg.jitter, bk, band, per_sm});
 }
 
-static int fused_max_per_sm() {
+static int fused_max_per_sm(int jitter) {
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chain_fused, 256, 0);
+  if (jitter) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chain_fused<1>, 256, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chain_fused<0>, 256, 0);
   return per_sm < 1 ? 1 : per_sm;
 }
 
 alb_status launch_chain(const alb_chain_cfg& cfg, int32_t n, const alb_params* params, const alb_image* in,
                         void* out, int32_t mode, Carve& ws, int32_t* status, cudaStream_t st) {
   const ChainK K = make_consts(cfg);
+  const int jit = cfg.jitter;
+  const int64_t npx = (int64_t)cfg.out_h * cfg.out_w;
   int32_t* queue = ws.take<int32_t>(64);
-  uint8_t* luts = ws.take<uint8_t>((size_t)n * 256);
-  ALB_REQUIRE(queue && luts, ALB_EWORKSPACE, "alb_apply_batch: workspace too small");
-  k_chain_luts<<<n, 256, 0, st>>>(n, params, luts);
+  uint8_t* luts = ws.take<uint8_t>((size_t)n * (jit ? 512 : 256));
+  unsigned long long* sums = jit ? ws.take<unsigned long long>((size_t)n) : nullptr;
+  ALB_REQUIRE(queue && luts && (!jit || sums), ALB_EWORKSPACE, "alb_apply_batch: workspace too small");
+  if (jit) {
+    k_jitter_luts<<<n, 256, 0, st>>>(n, params, nullptr, npx, 0, luts);   // B tables
+    ALB_CUDA(cudaMemsetAsync(sums, 0, (size_t)n * sizeof(unsigned long long), st));
+  } else {
+    k_chain_luts<<<n, 256, 0, st>>>(n, params, luts);
+  }
   ALB_CUDA(cudaGetLastError());
   __nv_bfloat16* o = (__nv_bfloat16*)out;
   if (mode == ALB_MODE_FUSED) {
@@ -346,23 +537,49 @@ alb_status launch_chain(const alb_chain_cfg& cfg, int32_t n, const alb_params* p
       if (cfg.tile_h > 0) band = imin(cfg.tile_h, kBandMax);
       per_sm = cfg.ctas_per_sm;
     }
-    const int max_per_sm = fused_max_per_sm();
+    const int max_per_sm = fused_max_per_sm(jit);
     if (per_sm <= 0 || per_sm > max_per_sm) per_sm = max_per_sm;
+    if (jit) {
+      // the contrast pivots first (a reduction over each image), then the C tables
+      k_chain_pivot<<<4 * sm_count(), 256, 0, st>>>(n, params, in, luts, K, 16, sums);
+      ALB_CUDA(cudaGetLastError());
+      k_jitter_luts<<<n, 256, 0, st>>>(n, params, sums, npx, 1, luts);
+      ALB_CUDA(cudaGetLastError());
+    }
     ALB_CUDA(cudaMemsetAsync(queue, 0, sizeof(int32_t), st));
-    k_chain_fused<<<per_sm * sm_count(), 256, 0, st>>>(n, params, in, luts, K, band, queue, o);
+    if (jit) k_chain_fused<1><<<per_sm * sm_count(), 256, 0, st>>>(n, params, in, luts, K, band, queue, o);
+    else k_chain_fused<0><<<per_sm * sm_count(), 256, 0, st>>>(n, params, in, luts, K, band, queue, o);
     ALB_CUDA(cudaGetLastError());
     return ALB_OK;
   }
   const size_t px = (size_t)n * cfg.out_h * cfg.out_w;
   uint8_t* a = ws.take<uint8_t>(px * 3);
   uint8_t* b = ws.take<uint8_t>(px * 3);
-  float* f = ws.take<float>(px * 3);
-  ALB_REQUIRE(a && b && f, ALB_EWORKSPACE, "alb_apply_batch: workspace too small for plain mode");
+  float* f = jit ? nullptr : ws.take<float>(px * 3);
+  ALB_REQUIRE(a && b && (jit || f), ALB_EWORKSPACE, "alb_apply_batch: workspace too small for plain mode");
   const int grid = 8 * sm_count();
   k_plain_resize<<<grid, 256, 0, st>>>(n, params, in, K, a);
   ALB_CUDA(cudaGetLastError());
   k_plain_flip<<<grid, 256, 0, st>>>(n, params, K, a, b);
   ALB_CUDA(cudaGetLastError());
+  if (jit) {
+    // one launch per position of the order; before each, the pivots of the
+    // images whose contrast runs at that position, and their C tables
+    uint8_t* cur = b;
+    uint8_t* nxt = a;
+    for (int step = 0; step < 3; step++) {
+      k_plain_pivot<<<grid, 256, 0, st>>>(n, params, K, step, cur, sums);
+      ALB_CUDA(cudaGetLastError());
+      k_jitter_luts<<<n, 256, 0, st>>>(n, params, sums, npx, 1, luts);
+      ALB_CUDA(cudaGetLastError());
+      k_plain_jitter_step<<<grid, 256, 0, st>>>(n, params, K, step, luts, cur, nxt);
+      ALB_CUDA(cudaGetLastError());
+      uint8_t* t = cur; cur = nxt; nxt = t;
+    }
+    k_plain_normalize_u8<<<grid, 256, 0, st>>>(n, K, cur, o);
+    ALB_CUDA(cudaGetLastError());
+    return ALB_OK;
+  }
   k_plain_lut<<<grid, 256, 0, st>>>(n, K, luts, b, a);
   ALB_CUDA(cudaGetLastError());
   k_plain_saturate<<<grid, 256, 0, st>>>(n, params, K, a, f);
@@ -392,6 +609,7 @@ extern "C" alb_status alb_apply_batch(const alb_chain_cfg* cfg, int32_t n, const
   ALB_REQUIRE(cfg->out_h > 0 && cfg->out_w > 0, ALB_ESHAPE, "alb_apply_batch: bad output size");
   ALB_REQUIRE(cfg->tile_w == 0 && cfg->tile_h >= 0 && cfg->tile_h <= kBandMax && cfg->ctas_per_sm >= 0, ALB_EINVAL,
               "alb_apply_batch: tile_h must be in [0, %d], tile_w 0, ctas_per_sm >= 0", kBandMax);
+  ALB_REQUIRE(cfg->jitter == 0 || cfg->jitter == 1, ALB_EINVAL, "alb_apply_batch: jitter must be 0 or 1");
   for (int c = 0; c < 3; c++) ALB_REQUIRE(cfg->std[c] > 0, ALB_EINVAL, "alb_apply_batch: std must be > 0");
   ALB_REQUIRE(workspace && workspace_bytes >= chain_workspace(*cfg, n, mode), ALB_EWORKSPACE,
               "alb_apply_batch: workspace of %zu bytes is smaller than %zu", workspace_bytes,
@@ -413,6 +631,7 @@ extern "C" alb_status alb_autotune_batch(const alb_chain_cfg* cfg, int32_t n, co
   ALB_REQUIRE(cfg->out_h > 0 && cfg->out_w > 0 && cfg->out_w <= 1024, ALB_ESHAPE,
               "alb_autotune_batch: bad output size");
   ALB_REQUIRE(cfg->tile_w == 0, ALB_EINVAL, "alb_autotune_batch: tile_w must be 0");
+  ALB_REQUIRE(cfg->jitter == 0 || cfg->jitter == 1, ALB_EINVAL, "alb_autotune_batch: jitter must be 0 or 1");
   for (int c = 0; c < 3; c++) ALB_REQUIRE(cfg->std[c] > 0, ALB_EINVAL, "alb_autotune_batch: std must be > 0");
   const size_t need = chain_workspace(*cfg, n, ALB_MODE_FUSED);
   ALB_REQUIRE(workspace && workspace_bytes >= need, ALB_EWORKSPACE,
@@ -421,7 +640,7 @@ extern "C" alb_status alb_autotune_batch(const alb_chain_cfg* cfg, int32_t n, co
   cudaStream_t st = (cudaStream_t)stream;
   int dev = 0;
   ALB_CUDA(cudaGetDevice(&dev));
-  const int max_per_sm = fused_max_per_sm();
+  const int max_per_sm = fused_max_per_sm(cfg->jitter);
   const int32_t bands[] = {2, 4, 8, 16, 32};
   const int32_t residency[] = {max_per_sm, max_per_sm / 2};
   cudaEvent_t e0 = nullptr, e1 = nullptr;

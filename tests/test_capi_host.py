@@ -105,6 +105,9 @@ def test_schedule_fields_are_checked_without_cuda(L):
         cfg = alb.chain_cfg(**kw)
         assert L.alb_apply_batch(C.byref(cfg), 4, fake, fake, fake, 0, fake, 1 << 40, None, None) == alb.ALB_EINVAL, kw
         assert "tile_h" in alb.alb_last_error()
+    cfg = alb.chain_cfg(jitter=2)
+    assert L.alb_apply_batch(C.byref(cfg), 4, fake, fake, fake, 0, fake, 1 << 40, None, None) == alb.ALB_EINVAL
+    assert "jitter" in alb.alb_last_error()
     best = alb.ChainCfg()
     cfg = alb.chain_cfg(tile_w=8)
     assert L.alb_autotune_batch(C.byref(cfg), 4, fake, fake, fake, fake, 1 << 40, 1, C.byref(best), None) == alb.ALB_EINVAL

@@ -26,9 +26,9 @@ def bits(t):
     return t.view(torch.int16).cpu().numpy().view(np.uint16)
 
 
-def run_chain(din, lps, dev, mode, oh=224, ow=224, tile_h=0):
+def run_chain(din, lps, dev, mode, oh=224, ow=224, tile_h=0, jitter=0):
     n = len(lps)
-    cfg = alb.chain_cfg(oh, ow, tile_h=tile_h)
+    cfg = alb.chain_cfg(oh, ow, tile_h=tile_h, jitter=jitter)
     out = torch.empty((n, 3, oh, ow), dtype=torch.bfloat16, device=dev)
     alb.alb_apply_batch(cfg, n, alb.params_to_device(lps, dev), din.dev, out, mode)
     torch.cuda.synchronize()
@@ -116,4 +116,52 @@ def test_full_size_ragged_batch_sampled(dev):
         h, w = sizes[i]
         op = O.sample_params(oc, 1809, 20, i, h, w)     # the oracle samples its own parameters
         ref = O.chain_image(op, rb.image(i).cpu().numpy())
+        assert np.array_equal(fb[k], ref), i
+
+
+@pytest.mark.parametrize("oh,ow", [(224, 224), (37, 61)])
+def test_jitter_mode1_fused_plain_oracle_agree(dev, oh, ow):
+    """Random op order and image-mean contrast pivot: fused == plain == oracle
+    for every one of the six orders."""
+    sizes = [(256 + (i * 97) % 769, 256 + (i * 193) % 769) for i in range(12)] + [(3, 900), (1024, 1024)]
+    rb = synth.ragged_noise(sizes, seed=9)
+    oc = O.make_cfg(O.CHAIN, **{**CHAIN_CFG, "out_h": oh, "out_w": ow})
+    ops = [O.sample_params(oc, 9, 20, i, h, w) for i, (h, w) in enumerate(sizes)]
+    for i, op in enumerate(ops):
+        op.k = i % 6
+    lps = [to_lib(p, alb) for p in ops]
+    din = DeviceBatch(to_device(rb, dev))
+    fused = run_chain(din, lps, dev, alb.MODE_FUSED, oh, ow, jitter=1)
+    plain = run_chain(din, lps, dev, alb.MODE_PLAIN, oh, ow, jitter=1)
+    assert torch.equal(fused.view(torch.int16), plain.view(torch.int16))
+    fb = bits(fused)
+    for i in range(len(sizes)):
+        ref = O.chain_image(ops[i], rb.image(i).numpy(), jitter=1)
+        assert np.array_equal(fb[i], ref), (i, ops[i].k)
+
+
+def test_jitter_mode1_full_size_batch_sampled(dev):
+    """4096 images, device-sampled records (order drawn per image), every
+    schedule of the autotuner's pick; fused == plain; 24 images vs the oracle."""
+    n = 4096
+    sizes = synth.uniform_sizes(n, 256, 1024, seed=1810)
+    rb = synth.ragged_noise(sizes, seed=1810, device=dev)
+    din = DeviceBatch(rb)
+    oc = O.make_cfg(O.CHAIN, **CHAIN_CFG)
+    pdev = torch.zeros(n * 232, dtype=torch.uint8, device=dev)
+    alb.alb_sample_params_batch(cfg_to_lib(oc, alb), 1810, 20, 0, n, din.dev, pdev)
+    cfg = alb.chain_cfg(jitter=1)
+    fused = torch.empty((n, 3, 224, 224), dtype=torch.bfloat16, device=dev)
+    best = alb.alb_autotune_batch(cfg, n, pdev, din.dev, fused, reps=1)
+    assert best.jitter == 1 and best.tile_h in (2, 4, 8, 16, 32)
+    plain = torch.empty_like(fused)
+    alb.alb_apply_batch(cfg, n, pdev, din.dev, fused, alb.MODE_FUSED)
+    alb.alb_apply_batch(cfg, n, pdev, din.dev, plain, alb.MODE_PLAIN)
+    torch.cuda.synchronize()
+    assert torch.equal(fused.view(torch.int16), plain.view(torch.int16))
+    fb = bits(fused[::171])
+    for k, i in enumerate(range(0, n, 171)):
+        h, w = sizes[i]
+        op = O.sample_params(oc, 1810, 20, i, h, w)
+        ref = O.chain_image(op, rb.image(i).cpu().numpy(), jitter=1)
         assert np.array_equal(fb[k], ref), i
