@@ -30,6 +30,7 @@ BRIGHTNESS, CONTRAST, BRIGHTNESS_CONTRAST, GAMMA = 5, 6, 7, 8
 SHIFT_RGB, SHIFT_HSV, GRAYSCALE, EQUALIZE = 9, 10, 11, 12
 ROTATE, SHIFT_SCALE_ROTATE, RESIZE, RANDOM_SIZED_CROP = 13, 14, 15, 16
 RANDOM_RESIZED_CROP, TRANSPOSE, ROT90, CHAIN = 17, 18, 19, 20
+GRID_DISTORTION, ELASTIC = 21, 22
 
 
 class Params(C.Structure):
@@ -104,6 +105,18 @@ def _declare(L):
         f.restype = C.c_int
     L.orc_apply_boxes.argtypes = [P(Params), C.c_int, C.c_int, P(C.c_float), C.c_int, P(C.c_float)]
     L.orc_apply_boxes.restype = C.c_int
+    L.orc_grid_q5.argtypes = [P(Params), C.c_int, C.c_int64, C.c_int64]
+    L.orc_grid_q5.restype = C.c_int64
+    L.orc_grid_edge_inverse.argtypes = [P(Params), C.c_int, C.c_double, C.c_int64]
+    L.orc_grid_edge_inverse.restype = C.c_double
+    L.orc_grid_factor.argtypes = [P(Params), C.c_int]
+    L.orc_grid_factor.restype = C.c_int32
+    L.orc_grid_set_factor.argtypes = [P(Params), C.c_int, C.c_int32]
+    L.orc_grid_set_factor.restype = None
+    L.orc_elastic_point.argtypes = [P(Params), C.c_int64, P(C.c_int32), P(C.c_int32)]
+    L.orc_elastic_point.restype = None
+    L.orc_elastic_disp.argtypes = [P(Params), C.c_int64, C.c_int64, C.c_int, P(C.c_int32), P(C.c_int32)]
+    L.orc_elastic_disp.restype = None
     L.orc_f32_to_bf16.argtypes = [C.c_float]
     L.orc_f32_to_bf16.restype = C.c_uint16
     L.orc_normalize_consts.argtypes = [P(C.c_double), P(C.c_double), P(C.c_float), P(C.c_float)]
@@ -233,7 +246,38 @@ def apply_boxes(p: Params, h: int, w: int, boxes: np.ndarray) -> np.ndarray:
     b = np.ascontiguousarray(boxes, dtype=np.float32).reshape(-1, 4)
     out = np.zeros_like(b)
     n = lib().orc_apply_boxes(C.byref(p), h, w, _ptr(b, C.c_float), b.shape[0], _ptr(out, C.c_float))
+    if n < 0:
+        raise ValueError("boxes are not defined for this transform")
     return out[:n]
+
+
+# ---------------------------------------------------------------- grid / elastic helpers
+def grid_q5(p: Params, axis: int, x: int, n: int) -> int:
+    return int(lib().orc_grid_q5(C.byref(p), axis, x, n))
+
+
+def grid_edge_inverse(p: Params, axis: int, e: float, n: int) -> float:
+    return float(lib().orc_grid_edge_inverse(C.byref(p), axis, e, n))
+
+
+def grid_factor(p: Params, slot: int) -> int:
+    return int(lib().orc_grid_factor(C.byref(p), slot))
+
+
+def grid_set_factor(p: Params, slot: int, d: int) -> None:
+    lib().orc_grid_set_factor(C.byref(p), slot, d)
+
+
+def elastic_point(p: Params, t: int):
+    dx, dy = C.c_int32(), C.c_int32()
+    lib().orc_elastic_point(C.byref(p), t, C.byref(dx), C.byref(dy))
+    return dx.value, dy.value
+
+
+def elastic_disp(p: Params, x: int, y: int, w: int):
+    dx, dy = C.c_int32(), C.c_int32()
+    lib().orc_elastic_disp(C.byref(p), x, y, w, C.byref(dx), C.byref(dy))
+    return dx.value, dy.value
 
 
 def f32_to_bf16_bits(x: np.ndarray) -> np.ndarray:

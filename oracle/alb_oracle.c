@@ -43,7 +43,7 @@ enum {
   T_SHIFT_RGB = 9, T_SHIFT_HSV = 10, T_GRAYSCALE = 11, T_EQUALIZE = 12,
   T_ROTATE = 13, T_SHIFT_SCALE_ROTATE = 14, T_RESIZE = 15,
   T_RANDOM_SIZED_CROP = 16, T_RANDOM_RESIZED_CROP = 17, T_TRANSPOSE = 18,
-  T_ROT90 = 19, T_CHAIN = 20
+  T_ROT90 = 19, T_CHAIN = 20, T_GRID_DISTORTION = 21, T_ELASTIC = 22
 };
 
 /* Sampled parameter record of one transform for one image (oracle layout). */
@@ -283,6 +283,109 @@ static int sample_rrc(orc_stream* s, int h, int w, double slo, double shi,
   return 1;
 }
 
+/* ======================================================================
+ * Grid distortion and elastic transform (Sec. II-C: non-rigid distortions
+ * for medical images).  The paper names them only; the readings here:
+ *
+ * Grid distortion.  Each axis of length n is cut into G cells of equal
+ * width in the output; cell i keeps a positive factor d_i (Q14 integers).
+ * The source cells have widths proportional to d_i and together span the
+ * same [0, n-1] (pixel centres), so the source coordinate of output sample
+ * x in cell i = min(G-1, floor(G x / (n-1))) is the exact rational
+ *   src(x) = ((n-1) P_i + (G x - i (n-1)) d_i) / D,  P_i = sum_{j<i} d_j,
+ *   D = sum_j d_j,
+ * quantised to Q5 with round half up.  Images: Q5 bilinear (taps inside the
+ * image; the +1 tap clamped); masks: nearest floor((Xq + 16) / 32).
+ *
+ * Elastic transform.  A lattice of control points every S = 2^s px (from
+ * (0, 0), ceil(W/S) + 1 by ceil(H/S) + 1 points) carries integer Q5
+ * displacements in [-A, A]; point t = i * nx + j takes the Philox4x32-10
+ * block with counter (t, image index, stream id lo, stream id hi ^ 2^31) and
+ * key = seed: dx = floor(w0 (2A + 1) / 2^32) - A, dy the same from w1.  A
+ * pixel's displacement is the bilinear blend of its cell's four points with
+ * integer weights (S - fx)(S - fy), ..., rounded half up: floor((sum +
+ * S^2/2) / S^2).  The source coordinate is (32 x + dx, 32 y + dy) in Q5;
+ * images: Q5 bilinear with reflect-101 taps; masks: nearest, reflected.
+ * ====================================================================== */
+EXPORT void orc_grid_set_factor(orc_params* p, int slot, int32_t d) {
+  uint64_t w = (uint64_t)p->q[slot >> 2];
+  int sh = 16 * (slot & 3);
+  w = (w & ~((uint64_t)0xFFFF << sh)) | ((uint64_t)(uint16_t)d << sh);
+  p->q[slot >> 2] = (int64_t)w;
+}
+
+EXPORT int32_t orc_grid_factor(const orc_params* p, int slot) {
+  return (int32_t)(((uint64_t)p->q[slot >> 2] >> (16 * (slot & 3))) & 0xFFFFu);
+}
+
+/* Q5 source coordinate of output sample x on an axis of n samples
+ * (axis 0 = x: factor slots 0..G-1, axis 1 = y: slots 12..12+G-1). */
+EXPORT int64_t orc_grid_q5(const orc_params* p, int axis, int64_t x, int64_t n) {
+  int g = p->k;
+  if (n <= 1) return 0;
+  int64_t d[12], D = 0;
+  for (int j = 0; j < g; j++) { d[j] = orc_grid_factor(p, 12 * axis + j); D += d[j]; }
+  int64_t i = (g * x) / (n - 1);
+  if (i > g - 1) i = g - 1;
+  int64_t P = 0;
+  for (int j = 0; j < i; j++) P += d[j];
+  int64_t N = (n - 1) * P + (g * x - i * (n - 1)) * d[i];
+  int64_t xq = floor_div(64 * N + D, 2 * D);
+  if (xq < 0) xq = 0;
+  if (xq > 32 * (n - 1)) xq = 32 * (n - 1);
+  return xq;
+}
+
+/* Output edge coordinate of source edge coordinate e on a grid-distorted
+ * axis of n samples: the inverse of the (unquantised) piecewise-linear
+ * src(x) in centre coordinates between the first and last pixel centres
+ * (both fixed points of the map); the outer half pixels map to themselves,
+ * so the image edges stay the image edges. */
+EXPORT double orc_grid_edge_inverse(const orc_params* p, int axis, double e, int64_t n) {
+  int g = p->k;
+  if (n <= 1) return e;
+  double d[12], D = 0.0, c[13];
+  for (int j = 0; j < g; j++) { d[j] = (double)orc_grid_factor(p, 12 * axis + j); D += d[j]; }
+  double P = 0.0;
+  for (int j = 0; j <= g; j++) { c[j] = (double)(n - 1) * P / D; if (j < g) P += d[j]; }
+  double t = e - 0.5;
+  if (t <= 0.0 || t >= (double)(n - 1)) return e;
+  int i = 0;
+  while (i < g - 1 && t >= c[i + 1]) i++;
+  double Pi = 0.0;
+  for (int j = 0; j < i; j++) Pi += d[j];
+  double x = (D * t - (double)(n - 1) * Pi) / ((double)g * d[i]) + (double)i * (double)(n - 1) / (double)g;
+  return x + 0.5;
+}
+
+/* Lattice displacements of an elastic record (Q5): dx, dy of point t. */
+EXPORT void orc_elastic_point(const orc_params* p, int64_t t, int32_t* dx, int32_t* dy) {
+  uint64_t seed = (uint64_t)p->q[0], sid = (uint64_t)p->q[1];
+  uint32_t ctr[4] = {(uint32_t)t, (uint32_t)p->q[2], (uint32_t)sid, (uint32_t)(sid >> 32) ^ 0x80000000u};
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t o[4];
+  orc_philox4x32_10(ctr, key, o);
+  uint64_t span = 2 * (uint64_t)p->k + 1;
+  *dx = (int32_t)((o[0] * span) >> 32) - p->k;
+  *dy = (int32_t)((o[1] * span) >> 32) - p->k;
+}
+
+/* Q5 displacement of pixel (x, y) of an image w pixels wide. */
+EXPORT void orc_elastic_disp(const orc_params* p, int64_t x, int64_t y, int w, int32_t* dx, int32_t* dy) {
+  int sh = p->cw;
+  int64_t S = (int64_t)1 << sh;
+  int64_t nx = ((w + S - 1) >> sh) + 1;
+  int64_t ci = y >> sh, cj = x >> sh, fy = y & (S - 1), fx = x & (S - 1);
+  int32_t ax[4], ay[4];
+  orc_elastic_point(p, ci * nx + cj, &ax[0], &ay[0]);
+  orc_elastic_point(p, ci * nx + cj + 1, &ax[1], &ay[1]);
+  orc_elastic_point(p, (ci + 1) * nx + cj, &ax[2], &ay[2]);
+  orc_elastic_point(p, (ci + 1) * nx + cj + 1, &ax[3], &ay[3]);
+  int64_t w00 = (S - fx) * (S - fy), w01 = fx * (S - fy), w10 = (S - fx) * fy, w11 = fx * fy;
+  *dx = (int32_t)floor_div(w00 * ax[0] + w01 * ax[1] + w10 * ax[2] + w11 * ax[3] + S * S / 2, S * S);
+  *dy = (int32_t)floor_div(w00 * ay[0] + w01 * ay[1] + w10 * ay[2] + w11 * ay[3] + S * S / 2, S * S);
+}
+
 EXPORT int orc_sample_params(const orc_cfg* cfg, uint64_t seed, uint64_t stream_id,
                              uint32_t index, int h, int w, orc_params* p) {
   memset(p, 0, sizeof(*p));
@@ -366,6 +469,33 @@ EXPORT int orc_sample_params(const orc_cfg* cfg, uint64_t seed, uint64_t stream_
       p->out_h = cfg->out_h; p->out_w = cfg->out_w;
       sample_rrc(&s, h, w, cfg->lo[0], cfg->hi[0], cfg->lo[1], cfg->hi[1], &p->y0, &p->x0, &p->ch, &p->cw);
       break;
+    case T_GRID_DISTORTION: {
+      /* G cells per axis (lo[1], default 5, at most 12); a factor per cell,
+       * 1 + U[lo[0], hi[0]], kept as Q14 integers (x cells, then y cells) */
+      int g = cfg->lo[1] > 0 ? (int)cfg->lo[1] : 5;
+      if (g < 1 || g > 12) return ORC_EINVAL;
+      p->k = g;
+      for (int j = 0; j < 2 * g; j++) {
+        double d = 1.0 + stream_uniform(&s, cfg->lo[0], cfg->hi[0]);
+        int64_t dq = (int64_t)rint(d * 16384.0);
+        if (dq < 1) dq = 1;
+        if (dq > 32767) dq = 32767;
+        orc_grid_set_factor(p, j < g ? j : 12 + (j - g), (int32_t)dq);
+      }
+      break;
+    }
+    case T_ELASTIC: {
+      /* amplitude alpha = lo[0] px (Q5: k = rne(32 alpha)), lattice spacing
+       * 2^cw px with cw = lo[1] (default 5); the lattice itself is drawn from
+       * the image's own Philox block stream (orc_elastic_lattice) */
+      double a = cfg->lo[0];
+      int sh = cfg->lo[1] > 0 ? (int)cfg->lo[1] : 5;
+      if (a < 0.0 || a > 4096.0 || sh < 2 || sh > 8) return ORC_EINVAL;
+      p->k = (int32_t)rint(a * 32.0);
+      p->cw = sh;
+      p->q[0] = (int64_t)seed; p->q[1] = (int64_t)stream_id; p->q[2] = (int64_t)index;
+      break;
+    }
     case T_CHAIN:
       /* RandomResizedCrop, then h-flip with probability 1/2, then brightness,
        * contrast and saturation factors, each uniform in [lo[2], hi[2]]. */
@@ -597,6 +727,20 @@ static int apply_geometric(const orc_params* p, const uint8_t* in, int h, int w,
             }
             break;
           }
+          case T_GRID_DISTORTION: {
+            int64_t xq = orc_grid_q5(p, 0, x, w), yq = orc_grid_q5(p, 1, y, h);
+            if (nearest) *o = PX(in, is, c, floor_div(yq + 16, 32), floor_div(xq + 16, 32))[k];
+            else *o = q5_bilinear(in, h, w, c, is, k, xq, yq, 0);
+            break;
+          }
+          case T_ELASTIC: {
+            int32_t dx, dy;
+            orc_elastic_disp(p, x, y, w, &dx, &dy);
+            int64_t xq = 32 * (int64_t)x + dx, yq = 32 * (int64_t)y + dy;
+            if (nearest) *o = PX(in, is, c, reflect101(floor_div(yq + 16, 32), h), reflect101(floor_div(xq + 16, 32), w))[k];
+            else *o = q5_bilinear(in, h, w, c, is, k, xq, yq, 1);
+            break;
+          }
           default: return ORC_EINVAL;
         }
       }
@@ -716,6 +860,12 @@ EXPORT int orc_apply_boxes(const orc_params* p, int h, int w, const float* in, i
         }
         break;
       }
+      case T_GRID_DISTORTION:
+        a1 = orc_grid_edge_inverse(p, 0, x1, w); a2 = orc_grid_edge_inverse(p, 0, x2, w);
+        b1 = orc_grid_edge_inverse(p, 1, y1, h); b2 = orc_grid_edge_inverse(p, 1, y2, h);
+        break;
+      case T_ELASTIC:
+        return -1;      /* boxes are not defined for a non-parametric distortion */
       default: break;   /* photometric: boxes unchanged */
     }
     if (a1 < 0) a1 = 0;
