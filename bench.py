@@ -335,6 +335,38 @@ def fused_pipeline(dev, stream, steps=3, warmup=2, n=FUSED_N):
     return res
 
 
+def distortions(dev, stream, hbm, n=SUITE_N):
+    """Grid distortion (5 cells per axis, factors 1 +- 0.3) and the elastic
+    transform (amplitude 8 px, lattice every 16 px) on the suite's images,
+    each one ragged launch, with masks off (images only)."""
+    from paper_1809_06839_gb300 import alb as A, synth
+    from paper_1809_06839_gb300.ragged import DeviceBatch, output_batch
+    sizes = synth.uniform_sizes(n, SUITE_LO, SUITE_HI, seed=SEED)
+    inp = DeviceBatch(synth.ragged_noise(sizes, seed=SEED, device=dev))
+    res = {}
+    for name, tid, lo, hi in (("GridDistortion", A.GRID_DISTORTION, (-0.3, 5), (0.3, 5)),
+                              ("ElasticTransform", A.ELASTIC, (8.0, 4), (8.0, 4))):
+        cfg = A.sample_cfg(tid, lo=lo, hi=hi)
+        pdev = torch.zeros(n * 232, dtype=torch.uint8, device=dev)
+        A.alb_sample_params_batch(cfg, SEED, tid, 0, n, inp.dev, pdev)
+        params = A.params_from_device(pdev)
+        out = output_batch(params, inp.rb.shapes, dev)
+        ws = A.workspace(A.alb_workspace_size(tid, n), dev)
+
+        def run():
+            A.alb_apply_ragged(tid, n, pdev, inp.dev, out.dev, ws=ws, stream=stream)
+        run()
+        t = ev_time(run, stream, 5)
+        alg = sum(2 * h * w * 3 for h, w in sizes)
+        res[name] = dict(images_per_s=round(n / t, 1), ms=round(t * 1e3, 4), gbs=round(alg / t / 1e9, 1),
+                         frac=round(alg / t / 1e9 / hbm, 4))
+        del out, ws
+    res["workload"] = f"{n} u8 RGB images H,W~U[{SUITE_LO},{SUITE_HI}], each distortion alone (one ragged launch)"
+    del inp
+    torch.cuda.empty_cache()
+    return res
+
+
 def large_suite(dev, stream, hbm, n=LARGE_N):
     """The same 15 transforms on images of at least 512 x 512 (H, W ~ U[512, 1024]),
     the size class the HBM-fraction target refers to."""
@@ -533,7 +565,7 @@ def main():
     ap.add_argument("--only", default="", help="comma-separated suite transforms (profiling runs)")
     ap.add_argument("--n", type=int, default=SUITE_N, help="suite images (profiling runs)")
     ap.add_argument("--skip-e2e", action="store_true")
-    ap.add_argument("--extras", default="fused,detection,differentiable,large",
+    ap.add_argument("--extras", default="fused,detection,differentiable,large,distort",
                     help="sub-workloads to run after the suite (comma-separated)")
     ap.add_argument("--fused-n", type=int, default=FUSED_N, help="images of the fused workload (profiling runs)")
     args = ap.parse_args()
@@ -597,6 +629,8 @@ def main():
             extra["differentiable"] = differentiable(dev, stream)
         if "large" in which:
             extra["per_transform_large"] = large_suite(dev, stream, hbm)
+        if "distort" in which:
+            extra["distortions"] = distortions(dev, stream, hbm)
     cpu = None
     if rank == 0 and ws == 1 and args.cpu_images > 0:
         # the oracle on the same resident workload, copied to the host

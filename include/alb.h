@@ -77,7 +77,9 @@ typedef enum alb_tid {
   ALB_RANDOM_RESIZED_CROP = 17,  /* crop of sampled area and aspect, resized */
   ALB_TRANSPOSE = 18,            /* Sec. II-B, Dih4 element */
   ALB_ROT90 = 19,                /* Sec. II-B, Dih4 rotations */
-  ALB_CHAIN = 20                 /* the fused ragged-batch chain (alb_apply_batch) */
+  ALB_CHAIN = 20,                /* the fused ragged-batch chain (alb_apply_batch) */
+  ALB_GRID_DISTORTION = 21,      /* Sec. II-C: grid distortion (separable piecewise-linear map) */
+  ALB_ELASTIC = 22               /* Sec. II-C: elastic transform (smooth random displacement field) */
 } alb_tid;
 
 /* One image (or mask) in device memory.  32 bytes. */
@@ -98,9 +100,12 @@ typedef struct alb_params {
   int32_t in_h, in_w;    /* input size the record was sampled for */
   int32_t out_h, out_w;  /* output size */
   int32_t y0, x0;        /* crop window origin; PadToSize: top/left padding */
-  int32_t ch, cw;        /* crop window size (RandomCrop, Resize, RSC, RRC, chain) */
+  int32_t ch, cw;        /* crop window size (RandomCrop, Resize, RSC, RRC, chain);
+                            ELASTIC: cw = log2 of the lattice spacing (2..8) */
   int32_t flip;          /* chain: 1 = horizontal flip */
-  int32_t k;             /* ROT90: quarter turns counter-clockwise */
+  int32_t k;             /* ROT90: quarter turns counter-clockwise; CHAIN: order of the
+                            jitter ops 0..5; GRID_DISTORTION: cells per axis G (1..12);
+                            ELASTIC: displacement amplitude A in 1/32 px */
   double alpha;          /* contrast gain; chain: contrast factor */
   double beta;           /* brightness shift (pixel units); chain: brightness factor */
   double gamma;          /* gamma exponent */
@@ -110,7 +115,11 @@ typedef struct alb_params {
   double scale;          /* warp scale */
   double dx, dy;         /* warp shift, fractions of w and h */
   double m[6];           /* forward map src -> dst, pixel-centre coordinates, row-major 2x3 */
-  int64_t q[6];          /* inverse map dst -> src, Q16 fixed point (round half even) */
+  int64_t q[6];          /* Rotate/SSR: inverse map dst -> src, Q16 fixed point (round half
+                            even).  GRID_DISTORTION: per-cell factors, Q14, 16 bits each
+                            (slot j in bits 16 (j % 4) of q[j / 4]; x cells in slots 0..11,
+                            y cells in 12..23).  ELASTIC: the lattice's Philox seed, stream
+                            id and image index in q[0..2] */
 } alb_params;
 
 /* Sampling configuration of one transform.  Meaning of the ranges:
@@ -121,6 +130,9 @@ typedef struct alb_params {
  *  RANDOM_SIZED_CROP [0] side as a fraction of min(h, w);
  *  RANDOM_RESIZED_CROP / CHAIN [0] area fraction, [1] aspect w/h,
  *  CHAIN [2] brightness, contrast and saturation factors.
+ *  GRID_DISTORTION [0] cell factor offset (factor 1 + U[lo, hi]); lo[1] cells
+ *  per axis (1..12, 0 = 5).  ELASTIC lo[0] amplitude in px (0..4096), lo[1]
+ *  log2 of the lattice spacing (2..8, 0 = 5); no random range.
  *  out_h/out_w: crop / pad / resize target size. */
 typedef struct alb_sample_cfg {
   int32_t tid, out_h, out_w, reserved;

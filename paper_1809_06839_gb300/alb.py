@@ -22,16 +22,18 @@ BRIGHTNESS, CONTRAST, BRIGHTNESS_CONTRAST, GAMMA = 5, 6, 7, 8
 SHIFT_RGB, SHIFT_HSV, GRAYSCALE, EQUALIZE = 9, 10, 11, 12
 ROTATE, SHIFT_SCALE_ROTATE, RESIZE, RANDOM_SIZED_CROP = 13, 14, 15, 16
 RANDOM_RESIZED_CROP, TRANSPOSE, ROT90, CHAIN = 17, 18, 19, 20
+GRID_DISTORTION, ELASTIC = 21, 22
 MODE_FUSED, MODE_PLAIN = 0, 1
 
 GEOMETRIC = {HFLIP, VFLIP, RANDOM_CROP, PAD_TO_SIZE, ROTATE, SHIFT_SCALE_ROTATE, RESIZE, RANDOM_SIZED_CROP,
-             RANDOM_RESIZED_CROP, TRANSPOSE, ROT90}
+             RANDOM_RESIZED_CROP, TRANSPOSE, ROT90, GRID_DISTORTION, ELASTIC}
 NAMES = {HFLIP: "HorizontalFlip", VFLIP: "VerticalFlip", RANDOM_CROP: "RandomCrop", PAD_TO_SIZE: "PadToSize",
          BRIGHTNESS: "Brightness", CONTRAST: "Contrast", BRIGHTNESS_CONTRAST: "BrightnessContrast",
          GAMMA: "Gamma", SHIFT_RGB: "ShiftRGB", SHIFT_HSV: "ShiftHSV", GRAYSCALE: "Grayscale",
          EQUALIZE: "Equalize", ROTATE: "Rotate", SHIFT_SCALE_ROTATE: "ShiftScaleRotate", RESIZE: "Resize",
          RANDOM_SIZED_CROP: "RandomSizedCrop", RANDOM_RESIZED_CROP: "RandomResizedCrop",
-         TRANSPOSE: "Transpose", ROT90: "RandomRotate90", CHAIN: "Chain"}
+         TRANSPOSE: "Transpose", ROT90: "RandomRotate90", CHAIN: "Chain", GRID_DISTORTION: "GridDistortion",
+         ELASTIC: "ElasticTransform"}
 
 
 class Image(C.Structure):

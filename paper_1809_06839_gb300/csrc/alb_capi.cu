@@ -133,7 +133,7 @@ extern "C" const char* alb_version(void) { return "alb 1.0 sm_103a"; }
 
 extern "C" alb_status alb_output_shape(const alb_params* p, int32_t h, int32_t w, int32_t* out_h, int32_t* out_w) {
   ALB_REQUIRE(p && out_h && out_w, ALB_EINVAL, "alb_output_shape: null argument");
-  ALB_REQUIRE(p->tid >= ALB_HFLIP && p->tid <= ALB_CHAIN, ALB_EINVAL, "alb_output_shape: unknown id %d", p->tid);
+  ALB_REQUIRE(p->tid >= ALB_HFLIP && p->tid <= ALB_ELASTIC, ALB_EINVAL, "alb_output_shape: unknown id %d", p->tid);
   out_shape(*p, h, w, *out_h, *out_w);
   return ALB_OK;
 }
@@ -146,7 +146,8 @@ extern "C" alb_status alb_apply(const alb_params* params, const alb_image* in, c
                                 size_t workspace_bytes, void* stream) {
   ALB_REQUIRE(params && in, ALB_EINVAL, "alb_apply: params and in are required");
   const alb_params& p = *params;
-  ALB_REQUIRE(p.tid >= ALB_HFLIP && p.tid < ALB_CHAIN, ALB_EINVAL, "alb_apply: unknown transform id %d", p.tid);
+  ALB_REQUIRE(p.tid >= ALB_HFLIP && p.tid <= ALB_ELASTIC && p.tid != ALB_CHAIN, ALB_EINVAL,
+              "alb_apply: unknown transform id %d", p.tid);
   alb_status rc = check_image(in, "alb_apply(in)");
   if (rc != ALB_OK) return rc;
   int32_t oh, ow;
@@ -184,6 +185,13 @@ extern "C" alb_status alb_apply(const alb_params* params, const alb_image* in, c
   if (boxes_in || boxes_out || n_boxes_out)
     ALB_REQUIRE(boxes_in && boxes_out && n_boxes_out && n_boxes >= 0, ALB_EINVAL,
                 "alb_apply: boxes_in, boxes_out and n_boxes_out go together");
+  ALB_REQUIRE(!(boxes_in && p.tid == ALB_ELASTIC), ALB_EINVAL,
+              "alb_apply: boxes are not defined for the elastic transform");
+  if (p.tid == ALB_GRID_DISTORTION && p.apply)
+    ALB_REQUIRE(p.k >= 1 && p.k <= 12, ALB_EINVAL, "alb_apply: grid distortion needs 1..12 cells, got %d", p.k);
+  if (p.tid == ALB_ELASTIC && p.apply)
+    ALB_REQUIRE(p.k >= 0 && p.k <= 131072 && p.cw >= 2 && p.cw <= 8, ALB_EINVAL,
+                "alb_apply: elastic amplitude %d or lattice exponent %d out of range", p.k, p.cw);
   ALB_REQUIRE(workspace && workspace_bytes >= ragged_ws(p.tid, 1), ALB_EWORKSPACE,
               "alb_apply: workspace of %zu bytes is smaller than %zu", workspace_bytes, ragged_ws(p.tid, 1));
   PrmList prm{nullptr, p};
@@ -202,7 +210,8 @@ extern "C" alb_status alb_apply_ragged(int32_t tid, int32_t n, const alb_params*
                                        const int32_t* n_boxes_dev, int32_t box_cap, float* boxes_out_dev,
                                        int32_t* n_boxes_out_dev, void* workspace, size_t workspace_bytes,
                                        int32_t* dev_status, void* stream) {
-  ALB_REQUIRE(tid >= ALB_HFLIP && tid < ALB_CHAIN, ALB_EINVAL, "alb_apply_ragged: unknown transform id %d", tid);
+  ALB_REQUIRE(tid >= ALB_HFLIP && tid <= ALB_ELASTIC && tid != ALB_CHAIN, ALB_EINVAL,
+              "alb_apply_ragged: unknown transform id %d", tid);
   ALB_REQUIRE(n >= 0, ALB_EINVAL, "alb_apply_ragged: negative n");
   if (n == 0) return ALB_OK;
   ALB_REQUIRE(params_dev && in_dev, ALB_EINVAL, "alb_apply_ragged: params and in are required");
@@ -210,6 +219,8 @@ extern "C" alb_status alb_apply_ragged(int32_t tid, int32_t n, const alb_params*
   if (boxes_dev || boxes_out_dev || n_boxes_out_dev)
     ALB_REQUIRE(boxes_dev && n_boxes_dev && boxes_out_dev && n_boxes_out_dev && box_cap > 0, ALB_EINVAL,
                 "alb_apply_ragged: box arrays go together and need box_cap > 0");
+  ALB_REQUIRE(!(boxes_dev && tid == ALB_ELASTIC), ALB_EINVAL,
+              "alb_apply_ragged: boxes are not defined for the elastic transform");
   ALB_REQUIRE(workspace && workspace_bytes >= ragged_ws(tid, n), ALB_EWORKSPACE,
               "alb_apply_ragged: workspace of %zu bytes is smaller than %zu", workspace_bytes, ragged_ws(tid, n));
   PrmList prm{params_dev, {}};

@@ -167,6 +167,15 @@ ALB_D int check_image_pair(int32_t tid, const alb_params& p, const alb_image& si
   }
   if (geometric && tid == ALB_PAD_TO_SIZE && (p.y0 < 0 || p.x0 < 0 || p.y0 + si.h > so.h || p.x0 + si.w > so.w))
     return ALB_ESHAPE;
+  if (geometric && tid == ALB_GRID_DISTORTION && p.apply) {
+    if (p.k < 1 || p.k > 12) return ALB_EINVAL;
+    for (int j = 0; j < p.k; j++)
+      if (((uint64_t)p.q[j >> 2] >> (16 * (j & 3)) & 0xFFFFu) == 0 ||
+          ((uint64_t)p.q[(12 + j) >> 2] >> (16 * ((12 + j) & 3)) & 0xFFFFu) == 0)
+        return ALB_EINVAL;
+  }
+  if (geometric && tid == ALB_ELASTIC && p.apply && (p.k < 0 || p.k > 131072 || p.cw < 2 || p.cw > 8))
+    return ALB_EINVAL;
   return 0;
 }
 

@@ -11,6 +11,7 @@
 // byte position touches at most a few consecutive source lines.
 #include "alb_common.cuh"
 #include "alb_kernels.cuh"
+#include "alb_distort.cuh"
 
 namespace alb {
 
@@ -356,6 +357,10 @@ __global__ void k_boxes(int32_t n, PrmList prm, ImgList in, const float* __restr
           }
           break;
         }
+        case ALB_GRID_DISTORTION:
+          a1 = grid_edge_inverse(p.q, p.k, 0, x1, w); a2 = grid_edge_inverse(p.q, p.k, 0, x2, w);
+          b1 = grid_edge_inverse(p.q, p.k, 1, y1, h); b2 = grid_edge_inverse(p.q, p.k, 1, y2, h);
+          break;
         default: break;
       }
       if (a1 < 0) a1 = 0;
@@ -381,6 +386,136 @@ static int grid_for(const void* fn, int threads, size_t smem) {
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
   if (per_sm < 1) per_sm = 1;
   return per_sm * sm_count();
+}
+
+// ------------------------------------------------------------------ distortions
+// Grid distortion and elastic transform (any channel count): one thread per
+// output pixel over the plan's row items.  Images: Q5 bilinear (grid: taps
+// inside the image, the +1 tap clamped; elastic: reflect-101 taps); masks:
+// nearest floor((Xq + 16) / 32) (elastic: reflected).
+template <int CT>
+ALB_D void q5_taps_store(const uint8_t* __restrict__ src, int64_t ss, int32_t C, int32_t xa, int32_t xb, int32_t ya,
+                         int32_t yb, int32_t fx, int32_t fy, uint8_t* op) {
+  const uint8_t* ra = src + (int64_t)ya * ss;
+  const uint8_t* rbp = src + (int64_t)yb * ss;
+  const int32_t w00 = (32 - fx) * (32 - fy), w01 = fx * (32 - fy), w10 = (32 - fx) * fy, w11 = fx * fy;
+  for (int c = 0; c < C; c++) {
+    const int32_t acc = w00 * __ldg(ra + (int64_t)xa * C + c) + w01 * __ldg(ra + (int64_t)xb * C + c) +
+                        w10 * __ldg(rbp + (int64_t)xa * C + c) + w11 * __ldg(rbp + (int64_t)xb * C + c);
+    op[c] = (uint8_t)((acc + 512) >> 10);
+  }
+}
+
+template <int CT, bool NEAREST>
+__global__ void __launch_bounds__(256) k_grid_u8(Plan plan, ImgList in, ImgList out, PrmList prm, int32_t* status) {
+  __shared__ int32_t colq[kResizeColCap];
+  int32_t it0, it1;
+  item_range(plan, it0, it1);
+  if (it0 >= it1) return;
+  int32_t b = item_image(plan, it0);
+  int32_t cached_b = -1;
+  for (int32_t item = it0; item < it1; item++) {
+    while (item >= plan.prefix[b + 1]) b++;
+    const alb_image si = in.get(b), so = out.get(b);
+    const alb_params& p = prm.get(b);
+    const int32_t C = CT ? CT : so.c;
+    const int32_t rb = plan.rows_per_item[b];
+    const int32_t r0 = (item - plan.prefix[b]) * rb, r1 = imin(r0 + rb, so.h);
+    const int32_t W = si.w, H = si.h;
+    const bool act = p.apply != 0;
+    const bool table = W <= kResizeColCap;
+    if (table && cached_b != b) {
+      __syncthreads();
+      for (int x = threadIdx.x; x < W; x += blockDim.x) colq[x] = act ? grid_q5(p.q, p.k, 0, x, W) : 32 * x;
+      __syncthreads();
+      cached_b = b;
+    }
+    const uint8_t* __restrict__ src = (const uint8_t*)si.data;
+    uint8_t* __restrict__ dst = (uint8_t*)so.data;
+    const int64_t npx = (int64_t)(r1 - r0) * W;
+    for (int64_t i = threadIdx.x; i < npx; i += blockDim.x) {
+      const int32_t y = r0 + (int32_t)(i / W), x = (int32_t)(i % W);
+      uint8_t* op = dst + (int64_t)y * so.row_stride + (int64_t)x * C;
+      const int32_t xq = table ? colq[x] : (act ? grid_q5(p.q, p.k, 0, x, W) : 32 * x);
+      const int32_t yq = act ? grid_q5(p.q, p.k, 1, y, H) : 32 * y;
+      if (NEAREST) {
+        const uint8_t* sp = src + (int64_t)((yq + 16) >> 5) * si.row_stride + (int64_t)((xq + 16) >> 5) * C;
+        for (int c = 0; c < C; c++) op[c] = __ldg(sp + c);
+      } else {
+        const int32_t ix = xq >> 5, iy = yq >> 5;
+        q5_taps_store<CT>(src, si.row_stride, C, ix, imin(ix + 1, W - 1), iy, imin(iy + 1, H - 1), xq & 31, yq & 31,
+                          op);
+      }
+    }
+  }
+}
+
+constexpr int kLatticeCap = 4096;   // lattice points cached per CTA and item
+
+template <int CT, bool NEAREST>
+__global__ void __launch_bounds__(256) k_elastic_u8(Plan plan, ImgList in, ImgList out, PrmList prm, int32_t* status) {
+  __shared__ int2 lat[kLatticeCap];
+  int32_t it0, it1;
+  item_range(plan, it0, it1);
+  if (it0 >= it1) return;
+  int32_t b = item_image(plan, it0);
+  for (int32_t item = it0; item < it1; item++) {
+    while (item >= plan.prefix[b + 1]) b++;
+    const alb_image si = in.get(b), so = out.get(b);
+    const alb_params& p = prm.get(b);
+    const int32_t C = CT ? CT : so.c;
+    const int32_t rb = plan.rows_per_item[b];
+    const int32_t r0 = (item - plan.prefix[b]) * rb, r1 = imin(r0 + rb, so.h);
+    if (r1 <= r0) continue;
+    const int32_t W = si.w, H = si.h;
+    const bool act = p.apply != 0;
+    const int sh = act ? p.cw : 2;
+    const int32_t S = 1 << sh;
+    const int32_t nx = ((W + S - 1) >> sh) + 1;
+    const int32_t ci0 = r0 >> sh, ci1 = ((r1 - 1) >> sh) + 1;     // lattice rows the item blends
+    const int64_t npts = (int64_t)(ci1 - ci0 + 1) * nx;
+    const bool cached = act && npts <= kLatticeCap;
+    __syncthreads();
+    if (cached)
+      for (int32_t t = threadIdx.x; t < npts; t += blockDim.x) {
+        int32_t dx, dy;
+        elastic_point(p.q, p.k, (int64_t)ci0 * nx + t, dx, dy);
+        lat[t] = make_int2(dx, dy);
+      }
+    __syncthreads();
+    auto point = [&](int32_t ci, int32_t cj) -> int2 {
+      if (cached) return lat[(ci - ci0) * nx + cj];
+      int32_t dx, dy;
+      elastic_point(p.q, p.k, (int64_t)ci * nx + cj, dx, dy);
+      return make_int2(dx, dy);
+    };
+    const uint8_t* __restrict__ src = (const uint8_t*)si.data;
+    uint8_t* __restrict__ dst = (uint8_t*)so.data;
+    const int64_t npx = (int64_t)(r1 - r0) * W;
+    for (int64_t i = threadIdx.x; i < npx; i += blockDim.x) {
+      const int32_t y = r0 + (int32_t)(i / W), x = (int32_t)(i % W);
+      uint8_t* op = dst + (int64_t)y * so.row_stride + (int64_t)x * C;
+      int64_t xq = 32 * (int64_t)x, yq = 32 * (int64_t)y;
+      if (act) {
+        const int32_t ci = y >> sh, cj = x >> sh, fy = y & (S - 1), fx = x & (S - 1);
+        const int2 a = point(ci, cj), bq = point(ci, cj + 1), c = point(ci + 1, cj), d = point(ci + 1, cj + 1);
+        const int64_t w00 = (int64_t)(S - fx) * (S - fy), w01 = (int64_t)fx * (S - fy), w10 = (int64_t)(S - fx) * fy,
+                      w11 = (int64_t)fx * fy;
+        const int64_t SS = (int64_t)S * S;
+        xq += floor_div(w00 * a.x + w01 * bq.x + w10 * c.x + w11 * d.x + SS / 2, SS);
+        yq += floor_div(w00 * a.y + w01 * bq.y + w10 * c.y + w11 * d.y + SS / 2, SS);
+      }
+      if (NEAREST) {
+        const int32_t sx = reflect101(floor_div(xq + 16, 32), W), sy = reflect101(floor_div(yq + 16, 32), H);
+        const uint8_t* sp = src + (int64_t)sy * si.row_stride + (int64_t)sx * C;
+        for (int c = 0; c < C; c++) op[c] = __ldg(sp + c);
+      } else {
+        const int64_t ix = floor_div(xq, 32), iy = floor_div(yq, 32);
+        q5_taps_store<CT>(src, si.row_stride, C, reflect101(ix, W), reflect101(ix + 1, W), reflect101(iy, H),
+                          reflect101(iy + 1, H), (int32_t)(xq - 32 * ix), (int32_t)(yq - 32 * iy), op);
+      }
+    }
+  }
 }
 
 template <class K>
@@ -411,6 +546,20 @@ alb_status launch_geometric(int32_t tid, const Plan& plan, const ImgList& in, co
       }
       if (c3) return launch_items(k_warp_affine_u8<3, false>, plan, in, out, prm, status, st);
       return launch_items(k_warp_affine_u8<0, false>, plan, in, out, prm, status, st);
+    case ALB_GRID_DISTORTION:
+      if (mask) {
+        if (c1) return launch_items(k_grid_u8<1, true>, plan, in, out, prm, status, st);
+        return launch_items(k_grid_u8<0, true>, plan, in, out, prm, status, st);
+      }
+      if (c3) return launch_items(k_grid_u8<3, false>, plan, in, out, prm, status, st);
+      return launch_items(k_grid_u8<0, false>, plan, in, out, prm, status, st);
+    case ALB_ELASTIC:
+      if (mask) {
+        if (c1) return launch_items(k_elastic_u8<1, true>, plan, in, out, prm, status, st);
+        return launch_items(k_elastic_u8<0, true>, plan, in, out, prm, status, st);
+      }
+      if (c3) return launch_items(k_elastic_u8<3, false>, plan, in, out, prm, status, st);
+      return launch_items(k_elastic_u8<0, false>, plan, in, out, prm, status, st);
     case ALB_RESIZE: case ALB_RANDOM_SIZED_CROP: case ALB_RANDOM_RESIZED_CROP:
       if (mask) {
         if (c1) return launch_items(k_resize_u8<1, true>, plan, in, out, prm, status, st);

@@ -40,7 +40,7 @@ inline bool is_geometric(int32_t tid) {
   switch (tid) {
     case ALB_HFLIP: case ALB_VFLIP: case ALB_RANDOM_CROP: case ALB_PAD_TO_SIZE: case ALB_ROTATE:
     case ALB_SHIFT_SCALE_ROTATE: case ALB_RESIZE: case ALB_RANDOM_SIZED_CROP: case ALB_RANDOM_RESIZED_CROP:
-    case ALB_TRANSPOSE: case ALB_ROT90:
+    case ALB_TRANSPOSE: case ALB_ROT90: case ALB_GRID_DISTORTION: case ALB_ELASTIC:
       return true;
     default:
       return false;

@@ -11,6 +11,7 @@
 #include <cstring>
 
 #include "alb_common.cuh"
+#include "alb_distort.cuh"
 
 namespace alb {
 
@@ -19,23 +20,6 @@ struct Philox {
   uint32_t buf[4];
   int pos;
 };
-
-ALB_HD void philox_block(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1,
-                         uint32_t out[4]) {
-#pragma unroll
-  for (int r = 0; r < 10; r++) {
-    if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
-    uint64_t a = (uint64_t)0xD2511F53u * c0;
-    uint64_t b = (uint64_t)0xCD9E8D57u * c2;
-    uint32_t n0 = (uint32_t)(b >> 32) ^ c1 ^ k0;
-    uint32_t n2 = (uint32_t)(a >> 32) ^ c3 ^ k1;
-    c1 = (uint32_t)b;
-    c3 = (uint32_t)a;
-    c0 = n0;
-    c2 = n2;
-  }
-  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
-}
 
 ALB_HD void ph_init(Philox& s, uint64_t seed, uint64_t sid, uint32_t index) {
   s.key0 = (uint32_t)seed; s.key1 = (uint32_t)(seed >> 32);
@@ -217,6 +201,36 @@ ALB_HD int sample_one(const alb_sample_cfg& cfg, uint64_t seed, uint64_t sid, ui
       p.out_h = cfg.out_h; p.out_w = cfg.out_w;
       sample_rrc(s, h, w, cfg.lo[0], cfg.hi[0], cfg.lo[1], cfg.hi[1], p);
       break;
+    case ALB_GRID_DISTORTION: {
+      // G cells per axis (lo[1], default 5, at most 12); per cell 1 + U[lo[0], hi[0]]
+      // kept as Q14 integers, x cells then y cells
+      const int g = cfg.lo[1] > 0 ? (int)cfg.lo[1] : 5;
+      if (g < 1 || g > kGridMaxCells) return ALB_EINVAL;
+      p.k = g;
+      for (int j = 0; j < 2 * g; j++) {
+        const double d = 1.0 + ph_uniform(s, cfg.lo[0], cfg.hi[0]);
+        int64_t dq = (int64_t)rint(d * 16384.0);
+        if (dq < 1) dq = 1;
+        if (dq > 32767) dq = 32767;
+        const int slot = j < g ? j : 12 + (j - g);
+        uint64_t w = (uint64_t)p.q[slot >> 2];
+        const int sh = 16 * (slot & 3);
+        w = (w & ~((uint64_t)0xFFFF << sh)) | ((uint64_t)(uint16_t)dq << sh);
+        p.q[slot >> 2] = (int64_t)w;
+      }
+      break;
+    }
+    case ALB_ELASTIC: {
+      // amplitude lo[0] px (Q5: k = rne(32 a)), lattice spacing 2^cw px (lo[1], default 5);
+      // the lattice comes from the image's own Philox blocks (alb_distort.cuh)
+      const double a = cfg.lo[0];
+      const int sh = cfg.lo[1] > 0 ? (int)cfg.lo[1] : 5;
+      if (!(a >= 0.0 && a <= 4096.0) || sh < 2 || sh > 8) return ALB_EINVAL;
+      p.k = (int32_t)rint(a * 32.0);
+      p.cw = sh;
+      p.q[0] = (int64_t)seed; p.q[1] = (int64_t)sid; p.q[2] = (int64_t)index;
+      break;
+    }
     case ALB_CHAIN:
       p.apply = 1;
       if (cfg.out_h <= 0 || cfg.out_w <= 0) return ALB_ESHAPE;
@@ -268,7 +282,7 @@ extern "C" alb_status alb_sample_params_batch(const alb_sample_cfg* cfg, uint64_
   ALB_REQUIRE(n >= 0, ALB_EINVAL, "alb_sample_params_batch: negative n");
   if (n == 0) return ALB_OK;
   ALB_REQUIRE(images_dev && params_dev, ALB_EINVAL, "alb_sample_params_batch: null device array");
-  ALB_REQUIRE(cfg->tid >= ALB_HFLIP && cfg->tid <= ALB_CHAIN, ALB_EINVAL,
+  ALB_REQUIRE(cfg->tid >= ALB_HFLIP && cfg->tid <= ALB_ELASTIC, ALB_EINVAL,
               "alb_sample_params_batch: unknown transform id %d", cfg->tid);
   cudaStream_t st = (cudaStream_t)stream;
   k_sample<<<(n + 127) / 128, 128, 0, st>>>(*cfg, seed, stream_id, first_index, n, images_dev, params_dev,

@@ -58,8 +58,8 @@ using namespace alb;
 extern "C" alb_status alb_apply_ragged_static(int32_t tid, int32_t n, const alb_params* params_dev,
                                               const alb_image* in_dev, const alb_image* out_dev,
                                               int32_t* dev_status, void* stream) {
-  ALB_REQUIRE(tid >= ALB_HFLIP && tid < ALB_CHAIN, ALB_EINVAL, "alb_apply_ragged_static: unknown transform id %d",
-              tid);
+  ALB_REQUIRE(tid >= ALB_HFLIP && tid <= ALB_ELASTIC && tid != ALB_CHAIN, ALB_EINVAL,
+              "alb_apply_ragged_static: unknown transform id %d", tid);
   ALB_REQUIRE(n >= 0, ALB_EINVAL, "alb_apply_ragged_static: negative n");
   ALB_REQUIRE(n <= kStaticMaxImages, ALB_ECAPACITY,
               "alb_apply_ragged_static: %d images exceed the static scratch limit of %d images", n,

@@ -63,6 +63,8 @@ EXTRA_CFGS = {
     "RandomResizedCrop224": O.make_cfg(O.RANDOM_RESIZED_CROP, out_h=224, out_w=224, lo=(0.08, 3 / 4),
                                        hi=(1.0, 4 / 3)),
     "HFlipHalf": O.make_cfg(O.HFLIP, p=0.5),
+    "GridDistortion": O.make_cfg(O.GRID_DISTORTION, lo=(-0.3, 5), hi=(0.3, 5)),
+    "ElasticTransform": O.make_cfg(O.ELASTIC, lo=(8.0, 4)),
 }
 
 

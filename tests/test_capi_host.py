@@ -118,6 +118,31 @@ def test_schedule_fields_are_checked_without_cuda(L):
                                 None) == alb.ALB_EWORKSPACE
 
 
+def test_distortion_records_are_checked_without_cuda(L):
+    """alb_apply rejects boxes with the elastic transform and out-of-range
+    distortion records before any device work."""
+    fake = C.c_void_p(16)
+    img = alb.Image()
+    img.data, img.h, img.w, img.c, img.row_stride = 16, 4, 4, 3, 12
+    out = alb.Image()
+    out.data, out.h, out.w, out.c, out.row_stride = 4096, 4, 4, 3, 12
+    p = alb.Params()
+    p.tid, p.apply, p.k, p.cw = alb.ELASTIC, 1, 32, 4
+    box = (C.c_float * 4)(0, 0, 1, 1)
+    nout = C.c_int32()
+    assert L.alb_apply(C.byref(p), C.byref(img), C.byref(out), None, None, box, 1, box, C.byref(nout), fake,
+                       1 << 30, None) == alb.ALB_EINVAL
+    assert "elastic" in alb.alb_last_error()
+    p.cw = 9
+    assert L.alb_apply(C.byref(p), C.byref(img), None, None, None, None, 0, None, None, fake, 1 << 30,
+                       None) == alb.ALB_EINVAL
+    p.tid, p.k = alb.GRID_DISTORTION, 13
+    assert L.alb_apply(C.byref(p), C.byref(img), None, None, None, None, 0, None, None, fake, 1 << 30,
+                       None) == alb.ALB_EINVAL
+    assert L.alb_apply_ragged(alb.ELASTIC, 2, fake, fake, fake, None, None, fake, fake, 4, fake, fake, fake,
+                              1 << 30, None, None) == alb.ALB_EINVAL
+
+
 def test_workspace_sizes(L):
     assert alb.alb_workspace_size(alb.EQUALIZE, 2000) > alb.alb_workspace_size(alb.BRIGHTNESS, 2000)
     assert alb.alb_workspace_size(alb.BRIGHTNESS, 2000) > alb.alb_workspace_size(alb.HFLIP, 2000)

@@ -75,7 +75,8 @@ def run_ragged(name, sizes, seed, dev, with_mask=True, with_boxes=True):
 @pytest.mark.parametrize("name", sorted(ALL))
 def test_ragged_transform_matches_oracle(dev, name):
     sizes = sizes_for(name)
-    rb, masks, ops, dout, dmo, boxes, nb, bo, nbo = run_ragged(name, sizes, 1809, dev)
+    with_boxes = ALL[name].tid != O.ELASTIC           # boxes are not defined for the elastic field
+    rb, masks, ops, dout, dmo, boxes, nb, bo, nbo = run_ragged(name, sizes, 1809, dev, with_boxes=with_boxes)
     for i, (h, w) in enumerate(sizes):
         img = rb.image(i).numpy()
         ref = O.apply_image(ops[i], img)
@@ -87,6 +88,8 @@ def test_ragged_transform_matches_oracle(dev, name):
             assert np.array_equal(got, ref), (name, i, (got != ref).sum())
         mref = O.apply_mask(ops[i], masks.image(i).numpy())
         assert np.array_equal(dmo.rb.image(i).cpu().numpy(), mref), (name, "mask", i)
+        if not with_boxes:
+            continue
         bref = O.apply_boxes(ops[i], h, w, boxes[i, :nb[i]])
         assert nbo[i] == len(bref), (name, "boxes", i)
         assert np.abs(bo[i, :nbo[i]] - bref).max(initial=0) <= 1e-4
@@ -308,3 +311,32 @@ def test_gamma_tables_exact_over_a_dense_gamma_grid(dev):
     for i in range(n):
         ref = O.apply_image(ops[i], row.reshape(1, 256, 3))[0]
         assert np.array_equal(got[i], ref), (i, gammas[i])
+
+
+@pytest.mark.parametrize("name,cfg", [
+    ("grid G=1", O.make_cfg(O.GRID_DISTORTION, lo=(-0.5, 1), hi=(0.5, 1))),
+    ("grid G=12 strong", O.make_cfg(O.GRID_DISTORTION, lo=(-0.9, 12), hi=(0.9, 12))),
+    ("elastic S=4 large", O.make_cfg(O.ELASTIC, lo=(40.0, 2))),
+    ("elastic S=256", O.make_cfg(O.ELASTIC, lo=(3.0, 8))),
+    ("elastic p=0.5", O.make_cfg(O.ELASTIC, p=0.5, lo=(5.0, 5))),
+])
+def test_distortion_extremes(dev, name, cfg):
+    """Few and many grid cells with strong factors, dense and sparse elastic
+    lattices with large displacements (taps reflected far outside), half the
+    records not applied; images and masks bit-exact."""
+    sizes = [(333, 500), (1, 97), (88, 1), (1, 1), (257, 65), (700, 40), (31, 900)]
+    rb = synth.ragged_noise(sizes, seed=4)
+    masks = synth.ragged_masks(sizes, seed=4)
+    ops = [O.sample_params(cfg, 4, cfg.tid, i, h, w) for i, (h, w) in enumerate(sizes)]
+    lps = [to_lib(p, alb) for p in ops]
+    din, dmi = DeviceBatch(to_device(rb, dev)), DeviceBatch(to_device(masks, dev))
+    dout, dmo = output_batch(lps, rb.shapes, dev), mask_output_batch(lps, masks.shapes, dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    n = len(sizes)
+    alb.alb_apply_ragged(cfg.tid, n, alb.params_to_device(lps, dev), din.dev, dout.dev, dmi.dev, dmo.dev,
+                         ws=alb.workspace(alb.alb_workspace_size(cfg.tid, n), dev), dev_status=status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    for i in range(n):
+        assert np.array_equal(dout.rb.image(i).cpu().numpy(), O.apply_image(ops[i], rb.image(i).numpy())), (name, i)
+        assert np.array_equal(dmo.rb.image(i).cpu().numpy(), O.apply_mask(ops[i], masks.image(i).numpy())), (name, i)
