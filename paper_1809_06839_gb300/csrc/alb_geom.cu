@@ -502,15 +502,16 @@ __global__ void __launch_bounds__(256) k_elastic_u8(Plan plan, ImgList in, ImgLi
         const int64_t w00 = (int64_t)(S - fx) * (S - fy), w01 = (int64_t)fx * (S - fy), w10 = (int64_t)(S - fx) * fy,
                       w11 = (int64_t)fx * fy;
         const int64_t SS = (int64_t)S * S;
-        xq += floor_div(w00 * a.x + w01 * bq.x + w10 * c.x + w11 * d.x + SS / 2, SS);
-        yq += floor_div(w00 * a.y + w01 * bq.y + w10 * c.y + w11 * d.y + SS / 2, SS);
+        // floor((sum + S^2 / 2) / S^2): S^2 is a power of two, an arithmetic shift floors
+        xq += (w00 * a.x + w01 * bq.x + w10 * c.x + w11 * d.x + SS / 2) >> (2 * sh);
+        yq += (w00 * a.y + w01 * bq.y + w10 * c.y + w11 * d.y + SS / 2) >> (2 * sh);
       }
       if (NEAREST) {
-        const int32_t sx = reflect101(floor_div(xq + 16, 32), W), sy = reflect101(floor_div(yq + 16, 32), H);
+        const int32_t sx = reflect101((xq + 16) >> 5, W), sy = reflect101((yq + 16) >> 5, H);   // floor
         const uint8_t* sp = src + (int64_t)sy * si.row_stride + (int64_t)sx * C;
         for (int c = 0; c < C; c++) op[c] = __ldg(sp + c);
       } else {
-        const int64_t ix = floor_div(xq, 32), iy = floor_div(yq, 32);
+        const int64_t ix = xq >> 5, iy = yq >> 5;   // arithmetic shifts floor
         q5_taps_store<CT>(src, si.row_stride, C, reflect101(ix, W), reflect101(ix + 1, W), reflect101(iy, H),
                           reflect101(iy + 1, H), (int32_t)(xq - 32 * ix), (int32_t)(yq - 32 * iy), op);
       }

@@ -17,6 +17,7 @@
 #include "alb_common.cuh"
 #include "alb_kernels.cuh"
 #include "alb_vec.cuh"
+#include "alb_distort.cuh"
 
 namespace alb {
 
@@ -100,7 +101,7 @@ ALB_D int32_t rs_nn(int32_t d, int32_t n_in, int32_t n_out) {
   return (int32_t)(i < n_in - 1 ? i : n_in - 1);
 }
 
-enum { MAP_AFFINE = 0, MAP_RESIZE = 1 };
+enum { MAP_AFFINE = 0, MAP_RESIZE = 1, MAP_GRID = 2 };
 
 // Q5 bilinear from a byte grid (row pitch `pitch`, C = 3 channels), taps at
 // byte offset o (ix, iy) and o + pitch: three aligned words per row, realigned.
@@ -434,6 +435,7 @@ static_assert(RB_Y >= 17 && RB_X >= RT_W + 2, "the box holds an unscaled tile");
 struct RImg {          // per-image values of a warp's current image (warp-uniform)
   int32_t b, prefix, ntiles, tiles_x;
   int32_t OH, OW, cw, ch, wx0, wy0;
+  int32_t steps1;      // the tap rows advance by at most one source row per output row
   const uint8_t* src;
   uint8_t* dst;
   int64_t sstride, dstride;
@@ -442,24 +444,39 @@ struct RTile {         // geometry of one tile
   int32_t ox0, oy0, tw, th, bx0, by0, bw, bh, big;
 };
 
+template <int MAP>
 ALB_D void r_load_img(const Plan& plan, const ImgList& in, const ImgList& out, const PrmList& prm, int32_t b,
                       RImg& k) {
   const alb_image si = in.get(b), so = out.get(b);
   const alb_params& p = prm.get(b);
   k.b = b; k.prefix = plan.prefix[b]; k.ntiles = plan.prefix[b + 1] - k.prefix; k.tiles_x = plan.rows_per_item[b];
-  k.OH = so.h; k.OW = so.w; k.cw = p.cw; k.ch = p.ch; k.wx0 = p.x0; k.wy0 = p.y0;
+  k.OH = so.h; k.OW = so.w;
+  if (MAP == MAP_GRID) {
+    k.cw = si.w; k.ch = si.h; k.wx0 = 0; k.wy0 = 0; k.steps1 = 0;
+  } else {
+    k.cw = p.cw; k.ch = p.ch; k.wx0 = p.x0; k.wy0 = p.y0; k.steps1 = p.ch <= so.h;
+  }
   k.src = (const uint8_t*)si.data; k.dst = (uint8_t*)so.data;
   k.sstride = si.row_stride; k.dstride = so.row_stride;
 }
 
 // Tile geometry; per lane: vcol = Q5 coordinate of tile column `lane`,
 // vrow = that of tile row `lane` (lanes < RT_H), both clamped to the tile.
-ALB_D void r_tile_geo(const RImg& k, int32_t item, int lane, RTile& g, int32_t& vcol, int32_t& vrow) {
+template <int MAP>
+ALB_D void r_tile_geo(const RImg& k, const PrmList& prm, int32_t item, int lane, RTile& g, int32_t& vcol,
+                      int32_t& vrow) {
   const int32_t t = item - k.prefix, ty = t / k.tiles_x, tx = t - ty * k.tiles_x;
   g.ox0 = tx * RT_W; g.oy0 = ty * RT_H;
   g.tw = imin(RT_W, k.OW - g.ox0); g.th = imin(RT_H, k.OH - g.oy0);
-  vcol = rs_q5(g.ox0 + imin(lane, g.tw - 1), k.cw, k.OW);
-  vrow = rs_q5(g.oy0 + imin(lane & (RT_H - 1), g.th - 1), k.ch, k.OH);
+  const int32_t cx = g.ox0 + imin(lane, g.tw - 1), ry = g.oy0 + imin(lane & (RT_H - 1), g.th - 1);
+  if (MAP == MAP_GRID) {
+    const alb_params& p = prm.get(k.b);            // the cell factors stay in the record
+    vcol = p.apply ? grid_q5(p.q, p.k, 0, cx, k.cw) : 32 * cx;
+    vrow = p.apply ? grid_q5(p.q, p.k, 1, ry, k.ch) : 32 * ry;
+  } else {
+    vcol = rs_q5(cx, k.cw, k.OW);
+    vrow = rs_q5(ry, k.ch, k.OH);
+  }
   const int32_t c0 = __shfl_sync(0xffffffffu, vcol, 0), c1 = __shfl_sync(0xffffffffu, vcol, g.tw - 1);
   const int32_t r0 = __shfl_sync(0xffffffffu, vrow, 0), r1 = __shfl_sync(0xffffffffu, vrow, g.th - 1);
   g.bx0 = c0 >> 5; g.by0 = r0 >> 5;
@@ -519,7 +536,7 @@ ALB_D void r_tile_compute(const RImg& k, const RTile& g, int lane, int32_t vcol,
     // at a clamped bottom edge the row below the last tap row is not staged
     // and has weight fy = 0: the last staged row stands in for it
     const int32_t last = g.bh - 1;
-    if (k.ch <= k.OH) {
+    if (k.steps1) {
       // enlargement: the top tap row advances by 0 or 1 per output row, so
       // one new h row per output row, selected without branches
       {
@@ -586,6 +603,7 @@ struct RShared {       // dynamic shared memory of k_resize_rows (above the 48 K
   RTile stile[RWARP][2];
 };
 
+template <int MAP>
 __global__ void __launch_bounds__(32 * RWARP) k_resize_rows(Plan plan, ImgList in, ImgList out, PrmList prm) {
   extern __shared__ __align__(16) uint8_t rs_dyn[];
   RShared& sm = *reinterpret_cast<RShared*>(rs_dyn);
@@ -602,8 +620,8 @@ __global__ void __launch_bounds__(32 * RWARP) k_resize_rows(Plan plan, ImgList i
   {
     RImg k;
     RTile g;
-    r_load_img(plan, in, out, prm, item_image(plan, item), k);
-    r_tile_geo(k, item, lane, g, ccol, crow);
+    r_load_img<MAP>(plan, in, out, prm, item_image(plan, item), k);
+    r_tile_geo<MAP>(k, prm, item, lane, g, ccol, crow);
     if (lane == 0) { simg[w][0] = k; stile[w][0] = g; }
     r_tile_stage(k, g, lane, box[w][0], rowoff[w][0]);
   }
@@ -618,10 +636,10 @@ __global__ void __launch_bounds__(32 * RWARP) k_resize_rows(Plan plan, ImgList i
       if (nitem >= k.prefix + k.ntiles) {
         int32_t b = k.b;
         while (nitem >= plan.prefix[b + 1]) b++;
-        r_load_img(plan, in, out, prm, b, k);
+        r_load_img<MAP>(plan, in, out, prm, b, k);
       }
       RTile g;
-      r_tile_geo(k, nitem, lane, g, ncol, nrow);
+      r_tile_geo<MAP>(k, prm, nitem, lane, g, ncol, nrow);
       __syncwarp();
       if (lane == 0) { simg[w][buf ^ 1] = k; stile[w][buf ^ 1] = g; }
       r_tile_stage(k, g, lane, box[w][buf ^ 1], rowoff[w][buf ^ 1]);
@@ -852,6 +870,122 @@ __global__ void __launch_bounds__(32 * AWARP) k_warp_affine3(Plan plan, ImgList 
   cp_async_wait<0>();
 }
 
+// --------------------------------------------------------------- elastic (RGB, bilinear)
+// A warp owns a 32 x 16 output tile, lane j = output column j.  The tile's
+// lattice points (at most 10 x 6 for the densest lattice, S = 4) are drawn by
+// the lanes into shared memory; per output pixel the displacement is the
+// exact integer blend of its cell's four points, and the two tap pixels of
+// each tap row are read as aligned words from global memory (L1-cached: the
+// field is smooth, neighbouring lanes read neighbouring bytes), reflected
+// per tap at the image border.
+constexpr int ET_W = 32, ET_H = 16, EWARP = 4, ELAT = 64;
+
+// the 6 bytes at p (pixels ix, ix + 1 of a row) as lo = bytes 0..3, hi = 4..5;
+// aligned word loads, the third only when it holds a needed byte
+ALB_D void ldg_pair(const uint8_t* p, uint32_t& lo, uint32_t& hi) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+  const uint32_t* w = reinterpret_cast<const uint32_t*>(a & ~uintptr_t(3));
+  const int s = (int)(a & 3);
+  const uint32_t w0 = __ldg(w), w1 = __ldg(w + 1), w2 = s == 3 ? __ldg(w + 2) : 0u;
+  lo = __funnelshift_r(w0, w1, 8 * s);
+  hi = __funnelshift_r(w1, w2, 8 * s);
+}
+
+// the same pair format from two arbitrary (reflected) pixels
+ALB_D void gather_pair(const uint8_t* row, int32_t xa, int32_t xb, uint32_t& lo, uint32_t& hi) {
+  const uint8_t* a = row + 3 * (int64_t)xa;
+  const uint8_t* b = row + 3 * (int64_t)xb;
+  lo = (uint32_t)__ldg(a) | ((uint32_t)__ldg(a + 1) << 8) | ((uint32_t)__ldg(a + 2) << 16) | ((uint32_t)__ldg(b) << 24);
+  hi = (uint32_t)__ldg(b + 1) | ((uint32_t)__ldg(b + 2) << 8);
+}
+
+__global__ void __launch_bounds__(32 * EWARP) k_elastic3(Plan plan, ImgList in, ImgList out, PrmList prm) {
+  __shared__ int2 lat[EWARP][ELAT];
+  int32_t it0, it1;
+  item_range(plan, it0, it1);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int32_t item = it0 + w;
+  if (item >= it1) return;
+  int32_t b = item_image(plan, item);
+  for (; item < it1; item += EWARP) {
+    while (item >= plan.prefix[b + 1]) b++;
+    const alb_image si = in.get(b), so = out.get(b);
+    const alb_params& p = prm.get(b);
+    const int32_t t = item - plan.prefix[b], tiles_x = plan.rows_per_item[b];
+    const int32_t ty = t / tiles_x, tx = t - ty * tiles_x;
+    const int32_t ox0 = tx * ET_W, oy0 = ty * ET_H;
+    const int32_t tw = imin(ET_W, so.w - ox0), th = imin(ET_H, so.h - oy0);
+    const int32_t W = si.w, H = si.h;
+    const bool act = p.apply != 0;
+    const int sh = act ? p.cw : 2;
+    const int32_t S = 1 << sh;
+    const int32_t ci0 = oy0 >> sh, cj0 = ox0 >> sh;
+    const int32_t ncols = ((ox0 + tw - 1) >> sh) + 2 - cj0;
+    __syncwarp();                                     // the previous tile's reads of lat[w] are done
+    if (act) {
+      const int32_t nrows = ((oy0 + th - 1) >> sh) + 2 - ci0;
+      const int32_t nx = ((W + S - 1) >> sh) + 1;
+      for (int32_t k = lane; k < nrows * ncols; k += 32) {
+        const int32_t r = k / ncols, c = k - r * ncols;
+        int32_t dx, dy;
+        elastic_point(p.q, p.k, (int64_t)(ci0 + r) * nx + cj0 + c, dx, dy);
+        lat[w][k] = make_int2(dx, dy);
+      }
+    }
+    __syncwarp();
+    const int32_t x = ox0 + imin(lane, tw - 1);
+    const int32_t cj = (x >> sh) - cj0, fx = x & (S - 1);
+    const bool store = lane < tw;
+    const uint8_t* __restrict__ src = (const uint8_t*)si.data;
+    const int64_t ss = si.row_stride;
+    uint8_t* od = (uint8_t*)so.data + (int64_t)oy0 * so.row_stride + 3 * (int64_t)(ox0 + lane);
+    const int64_t SS = (int64_t)S * S;
+    // per lane, the horizontal blends (S - fx) p_left + fx p_right of the two
+    // lattice rows around the current output row, refreshed when the row of
+    // lattice cells changes (warp-uniform); 32-bit when A S^2 fits
+    const bool narrow = (int64_t)p.k * SS < (int64_t(1) << 30);
+    int32_t crow = -1;
+    int64_t hax = 0, hay = 0, hbx = 0, hby = 0;
+    for (int r = 0; r < th; r++, od += so.row_stride) {
+      const int32_t y = oy0 + r;
+      int32_t X = 32 * x, Y = 32 * y;
+      if (act) {
+        const int32_t ci = (y >> sh) - ci0, fy = y & (S - 1);
+        if (ci != crow) {
+          const int2 a = lat[w][ci * ncols + cj], bq = lat[w][ci * ncols + cj + 1];
+          const int2 c = lat[w][(ci + 1) * ncols + cj], d = lat[w][(ci + 1) * ncols + cj + 1];
+          hax = (int64_t)(S - fx) * a.x + (int64_t)fx * bq.x;
+          hay = (int64_t)(S - fx) * a.y + (int64_t)fx * bq.y;
+          hbx = (int64_t)(S - fx) * c.x + (int64_t)fx * d.x;
+          hby = (int64_t)(S - fx) * c.y + (int64_t)fx * d.y;
+          crow = ci;
+        }
+        // floor((sum + S^2 / 2) / S^2): S^2 is a power of two, an arithmetic shift floors
+        if (narrow) {
+          X += ((S - fy) * (int32_t)hax + fy * (int32_t)hbx + (int32_t)(SS / 2)) >> (2 * sh);
+          Y += ((S - fy) * (int32_t)hay + fy * (int32_t)hby + (int32_t)(SS / 2)) >> (2 * sh);
+        } else {
+          X += (int32_t)(((int64_t)(S - fy) * hax + (int64_t)fy * hbx + SS / 2) >> (2 * sh));
+          Y += (int32_t)(((int64_t)(S - fy) * hay + (int64_t)fy * hby + SS / 2) >> (2 * sh));
+        }
+      }
+      const int32_t ix = X >> 5, fxq = X & 31, iy = Y >> 5, fyq = Y & 31;
+      uint32_t tl, th2, bl, bh2;
+      if (ix >= 0 && ix + 1 < W && iy >= 0 && iy + 1 < H) {
+        const uint8_t* ra = src + (int64_t)iy * ss + 3 * (int64_t)ix;
+        ldg_pair(ra, tl, th2);
+        ldg_pair(ra + ss, bl, bh2);
+      } else {
+        const int32_t xa = reflect101(ix, W), xb = reflect101(ix + 1, W);
+        gather_pair(src + (int64_t)reflect101(iy, H) * ss, xa, xb, tl, th2);
+        gather_pair(src + (int64_t)reflect101(iy + 1, H) * ss, xa, xb, bl, bh2);
+      }
+      const uint32_t v = bilerp3(tl, th2, bl, bh2, fxq, fyq);
+      if (store) { od[0] = (uint8_t)v; od[1] = (uint8_t)(v >> 8); od[2] = (uint8_t)(v >> 16); }
+    }
+  }
+}
+
 // --------------------------------------------------------------- launcher
 template <class... KArgs, class... Args>
 static alb_status launch_k(void (*kern)(KArgs...), cudaStream_t st, Args... args) {
@@ -868,21 +1002,30 @@ alb_status launch_tile_geometric(int32_t tid, const Plan& plan, const ImgList& i
                                  cudaStream_t st) {
   const bool affine = tid == ALB_ROTATE || tid == ALB_SHIFT_SCALE_ROTATE;
   const bool resize = tid == ALB_RESIZE || tid == ALB_RANDOM_SIZED_CROP || tid == ALB_RANDOM_RESIZED_CROP;
-  if (!affine && !resize) return ALB_EINVAL;
+  const bool grid = tid == ALB_GRID_DISTORTION;
+  if (!affine && !resize && !grid && tid != ALB_ELASTIC) return ALB_EINVAL;
   if (!(channels == 3 && !mask) && !(channels == 1 && mask)) return ALB_EINVAL;
   // the row plan's arrays are rewritten as a tile plan (stream-ordered)
   int32_t* prefix = const_cast<int32_t*>(plan.prefix);
   int32_t* tiles_x = const_cast<int32_t*>(plan.rows_per_item);
-  if (resize && !mask) {
+  if ((resize || grid) && !mask) {
     k_plan_tiles<<<1, 1024, 0, st>>>(out, plan.n, RT_W, RT_H, prefix, tiles_x, chk);
     ALB_CUDA(cudaGetLastError());
     const int smem = (int)sizeof(RShared);
-    ALB_CUDA(cudaFuncSetAttribute(k_resize_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    auto kern = grid ? k_resize_rows<MAP_GRID> : k_resize_rows<MAP_RESIZE>;
+    ALB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_resize_rows, 32 * RWARP, smem);
-    k_resize_rows<<<(per_sm < 1 ? 1 : per_sm) * sm_count(), 32 * RWARP, smem, st>>>(plan, in, out, prm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * RWARP, smem);
+    kern<<<(per_sm < 1 ? 1 : per_sm) * sm_count(), 32 * RWARP, smem, st>>>(plan, in, out, prm);
     ALB_CUDA(cudaGetLastError());
     return ALB_OK;
+  }
+  if (grid) return ALB_EINVAL;   // masks of a grid distortion: the general kernel
+  if (tid == ALB_ELASTIC) {
+    if (mask) return ALB_EINVAL;   // masks: the general kernel
+    k_plan_tiles<<<1, 1024, 0, st>>>(out, plan.n, ET_W, ET_H, prefix, tiles_x, chk);
+    ALB_CUDA(cudaGetLastError());
+    return launch_k(k_elastic3, st, plan, in, out, prm);
   }
   if (affine && !mask) {
     k_plan_tiles<<<1, 1024, 0, st>>>(out, plan.n, AT_W, AT_H, prefix, tiles_x, chk);
