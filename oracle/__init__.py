@@ -117,6 +117,13 @@ def _declare(L):
     L.orc_elastic_point.restype = None
     L.orc_elastic_disp.argtypes = [P(Params), C.c_int64, C.c_int64, C.c_int, P(C.c_int32), P(C.c_int32)]
     L.orc_elastic_disp.restype = None
+    L.orc_chain_mask.argtypes = [P(Params), u8p, C.c_int, C.c_int, C.c_int, C.c_int64, u8p, C.c_int64]
+    L.orc_chain_mask.restype = C.c_int
+    L.orc_chain_boxes.argtypes = [P(Params), P(C.c_float), C.c_int, P(C.c_float)]
+    L.orc_chain_boxes.restype = C.c_int
+    L.orc_sample_chain_box_safe.argtypes = [P(Cfg), C.c_uint64, C.c_uint64, C.c_uint32, C.c_int, C.c_int,
+                                            P(C.c_float), C.c_int, P(Params)]
+    L.orc_sample_chain_box_safe.restype = C.c_int
     L.orc_f32_to_bf16.argtypes = [C.c_float]
     L.orc_f32_to_bf16.restype = C.c_uint16
     L.orc_normalize_consts.argtypes = [P(C.c_double), P(C.c_double), P(C.c_float), P(C.c_float)]
@@ -361,3 +368,34 @@ def warp_photo_bwd(x, angle, scale, tx, ty, alpha, beta, gamma, gy):
     lib().orc_warp_photo_bwd(B, Cc, H, W, _ptr(x, C.c_double), *[_ptr(a, C.c_double) for a in args],
                              _ptr(gy, C.c_double), _ptr(dx, C.c_double), _ptr(dparams, C.c_double))
     return dx, dparams
+
+
+# ---------------------------------------------------------------- chain targets
+def chain_mask(p: Params, mask: np.ndarray) -> np.ndarray:
+    """N-plane uint8 mask (H, W, N) through the chain's crop, nearest resize and flip."""
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    h, w, c = m.shape
+    out = np.zeros((p.out_h, p.out_w, c), np.uint8)
+    rc = lib().orc_chain_mask(C.byref(p), _ptr(m, C.c_uint8), h, w, c, w * c, _ptr(out, C.c_uint8), p.out_w * c)
+    if rc != 0:
+        raise ValueError("chain mask failed")
+    return out
+
+
+def chain_boxes(p: Params, boxes: np.ndarray) -> np.ndarray:
+    b = np.ascontiguousarray(boxes, dtype=np.float32).reshape(-1, 4)
+    out = np.zeros_like(b)
+    n = lib().orc_chain_boxes(C.byref(p), _ptr(b, C.c_float), b.shape[0], _ptr(out, C.c_float))
+    return out[:n]
+
+
+def sample_chain_box_safe(cfg: Cfg, seed: int, stream_id: int, index: int, h: int, w: int,
+                          boxes: np.ndarray) -> Params:
+    b = np.ascontiguousarray(boxes, dtype=np.float32).reshape(-1, 4)
+    p = Params()
+    rc = lib().orc_sample_chain_box_safe(C.byref(cfg), seed, stream_id, index, h, w, _ptr(b, C.c_float),
+                                         b.shape[0], C.byref(p))
+    if rc != 0:
+        raise ValueError(f"orc_sample_chain_box_safe failed with status {rc}")
+    return p
+

@@ -1133,3 +1133,100 @@ EXPORT void orc_warp_photo_bwd(int B, int C, int H, int W, const double* x,
     dp[4] = dal; dp[5] = dbe; dp[6] = dga;
   }
 }
+
+/* ======================================================================
+ * Targets of the fused chain (Sec. II-A: a crop + flip applied to an image
+ * together with its masks and boxes; Fig. 2 detection).
+ *
+ * Masks: an N-plane uint8 mask (HWC, c = N instance planes) goes through the
+ * chain's crop window with nearest resampling to out_h x out_w (the resize
+ * rule of the masks) and the same h-flip.
+ * Boxes: crop to the window (clip there), scale to the output, flip, clip
+ * to the output and drop boxes with no area left, order kept.
+ * Box-safe windows: the chain's crop window is drawn so that it contains the
+ * union of the image's boxes: with the union clipped to the image and
+ * widened to whole pixels [ux0, ux1) x [uy0, uy1), x0 = randint[0, ux0],
+ * x1 = ux1 + randint[0, W - ux1] (window [x0, x1)), then the same for y;
+ * without boxes (or an empty union) the chain's RandomResizedCrop draw is
+ * used.  The flip and jitter draws follow as in the chain.
+ * ====================================================================== */
+EXPORT int orc_chain_mask(const orc_params* p, const uint8_t* in, int h, int w, int c, int64_t is,
+                          uint8_t* out, int64_t os) {
+  int oh = p->out_h, ow = p->out_w;
+  if (p->y0 < 0 || p->x0 < 0 || p->y0 + p->ch > h || p->x0 + p->cw > w) return ORC_ESHAPE;
+  for (int y = 0; y < oh; y++)
+    for (int x = 0; x < ow; x++) {
+      int xr = p->flip ? ow - 1 - x : x;
+      int64_t sy = p->y0 + resize_nearest(y, p->ch, oh), sx = p->x0 + resize_nearest(xr, p->cw, ow);
+      for (int k = 0; k < c; k++) PX(out, os, c, y, x)[k] = PX(in, is, c, sy, sx)[k];
+    }
+  return ORC_OK;
+}
+
+EXPORT int orc_chain_boxes(const orc_params* p, const float* in, int n, float* out) {
+  int oh = p->out_h, ow = p->out_w, kept = 0;
+  for (int i = 0; i < n; i++) {
+    double cx1 = in[4 * i] - p->x0, cy1 = in[4 * i + 1] - p->y0, cx2 = in[4 * i + 2] - p->x0, cy2 = in[4 * i + 3] - p->y0;
+    if (cx1 < 0) cx1 = 0;
+    if (cy1 < 0) cy1 = 0;
+    if (cx2 > p->cw) cx2 = p->cw;
+    if (cy2 > p->ch) cy2 = p->ch;
+    double a1 = cx1 * ow / p->cw, a2 = cx2 * ow / p->cw, b1 = cy1 * oh / p->ch, b2 = cy2 * oh / p->ch;
+    if (p->flip) { double t = a1; a1 = (double)ow - a2; a2 = (double)ow - t; }
+    if (a1 < 0) a1 = 0;
+    if (b1 < 0) b1 = 0;
+    if (a2 > ow) a2 = ow;
+    if (b2 > oh) b2 = oh;
+    if (a2 - a1 <= 0.0 || b2 - b1 <= 0.0) continue;
+    out[4 * kept] = (float)a1; out[4 * kept + 1] = (float)b1;
+    out[4 * kept + 2] = (float)a2; out[4 * kept + 3] = (float)b2;
+    kept++;
+  }
+  return kept;
+}
+
+EXPORT int orc_sample_chain_box_safe(const orc_cfg* cfg, uint64_t seed, uint64_t stream_id, uint32_t index,
+                                     int h, int w, const float* boxes, int nb, orc_params* p) {
+  if (cfg->tid != T_CHAIN) return ORC_EINVAL;
+  memset(p, 0, sizeof(*p));
+  if (h <= 0 || w <= 0) return ORC_ESHAPE;
+  if (cfg->out_h <= 0 || cfg->out_w <= 0) return ORC_ESHAPE;
+  orc_stream s; stream_init(&s, seed, stream_id, index);
+  p->tid = T_CHAIN; p->in_h = h; p->in_w = w;
+  p->alpha = 1.0; p->beta = 0.0; p->gamma = 1.0; p->sat = 1.0; p->scale = 1.0;
+  (void)stream_uniform01(&s);                 /* the probability draw; the chain always applies */
+  p->apply = 1;
+  p->out_h = cfg->out_h; p->out_w = cfg->out_w;
+  double ux1 = 0, uy1 = 0, ux2 = 0, uy2 = 0;
+  int have = 0;
+  for (int i = 0; i < nb; i++) {
+    double a = boxes[4 * i], b = boxes[4 * i + 1], c = boxes[4 * i + 2], d = boxes[4 * i + 3];
+    if (a < 0) a = 0;
+    if (b < 0) b = 0;
+    if (c > w) c = w;
+    if (d > h) d = h;
+    if (c <= a || d <= b) continue;
+    if (!have || a < ux1) ux1 = a;
+    if (!have || b < uy1) uy1 = b;
+    if (!have || c > ux2) ux2 = c;
+    if (!have || d > uy2) uy2 = d;
+    have = 1;
+  }
+  if (have) {
+    int x0i = (int)floor(ux1), y0i = (int)floor(uy1), x1i = (int)ceil(ux2), y1i = (int)ceil(uy2);
+    int x0 = stream_randint(&s, x0i);
+    int x1 = x1i + stream_randint(&s, w - x1i);
+    int y0 = stream_randint(&s, y0i);
+    int y1 = y1i + stream_randint(&s, h - y1i);
+    p->x0 = x0; p->cw = x1 - x0; p->y0 = y0; p->ch = y1 - y0;
+  } else {
+    sample_rrc(&s, h, w, cfg->lo[0], cfg->hi[0], cfg->lo[1], cfg->hi[1], &p->y0, &p->x0, &p->ch, &p->cw);
+  }
+  p->flip = stream_uniform01(&s) < 0.5;
+  p->beta = stream_uniform(&s, cfg->lo[2], cfg->hi[2]);
+  p->alpha = stream_uniform(&s, cfg->lo[2], cfg->hi[2]);
+  p->sat = stream_uniform(&s, cfg->lo[2], cfg->hi[2]);
+  p->k = stream_randint(&s, 5);
+  return ORC_OK;
+}
+
