@@ -335,6 +335,49 @@ def fused_pipeline(dev, stream, steps=3, warmup=2, n=FUSED_N):
     return res
 
 
+def fused_detection(dev, stream, steps=3, warmup=2, n=FUSED_N):
+    """The fused chain with its targets: the ragged batch of the fused
+    pipeline plus a 1-8 plane instance stack and 1-50 boxes per image, box-safe
+    crop windows from the device sampler; fused vs plain (images, masks, boxes)."""
+    from paper_1809_06839_gb300 import alb as A, synth
+    from paper_1809_06839_gb300.ragged import DeviceBatch
+    sizes = synth.uniform_sizes(n, FUSED_LO, FUSED_HI, seed=SEED)
+    din = DeviceBatch(synth.ragged_noise(sizes, seed=SEED, device=dev))
+    planes = [1 + (i * 7) % 8 for i in range(n)]
+    mi = DeviceBatch(synth.instance_stacks(sizes, planes, seed=SEED, device=dev))
+    mo = DeviceBatch(synth.empty_ragged([(224, 224, c) for c in planes], device=dev))
+    cap = 50
+    boxes = torch.zeros((n, cap, 4), dtype=torch.float32)
+    nb = torch.zeros(n, dtype=torch.int32)
+    for i, (h, w) in enumerate(sizes):
+        b = torch.from_numpy(synth.random_boxes(h, w, i, SEED)[:cap])
+        boxes[i, :len(b)] = b
+        nb[i] = len(b)
+    bd, nbd = boxes.to(dev), nb.to(dev)
+    bo, nbo = torch.zeros_like(bd), torch.zeros_like(nbd)
+    cfg = A.sample_cfg(A.CHAIN, out_h=224, out_w=224, lo=(0.08, 3 / 4, 0.6), hi=(1.0, 4 / 3, 1.4))
+    pdev = torch.zeros(n * 232, dtype=torch.uint8, device=dev)
+    ccfg = A.chain_cfg()
+    out = torch.empty((n, 3, 224, 224), dtype=torch.bfloat16, device=dev)
+    ws = A.workspace(A.alb_batch_workspace_size(ccfg, n, A.MODE_PLAIN), dev)
+    res = {}
+    for name, mode in (("fused", A.MODE_FUSED), ("plain", A.MODE_PLAIN)):
+        def run(mode=mode):
+            A.alb_sample_chain_box_safe_batch(cfg, SEED, 20, 0, n, din.dev, bd, nbd, cap, pdev, stream=stream)
+            A.alb_apply_batch_targets(ccfg, n, pdev, din.dev, out, mi.dev, mo.dev, bd, nbd, cap, bo, nbo, mode, ws,
+                                      stream=stream)
+        for _ in range(warmup):
+            run()
+        t = ev_time(run, stream, steps)
+        res[name] = dict(images_per_s=n / t, ms=t * 1e3)
+    res["speedup_vs_plain"] = res["plain"]["ms"] / res["fused"]["ms"]
+    res["workload"] = (f"{n} ragged u8 RGB images H,W~U[{FUSED_LO},{FUSED_HI}] + 1-8 instance planes + 1-50 boxes: "
+                       "box-safe crop -> 224 + flip + jitter + Normalize bf16 NCHW, masks nearest, boxes mapped")
+    del din, mi, mo, out, ws
+    torch.cuda.empty_cache()
+    return res
+
+
 def distortions(dev, stream, hbm, n=SUITE_N):
     """Grid distortion (5 cells per axis, factors 1 +- 0.3) and the elastic
     transform (amplitude 8 px, lattice every 16 px) on the suite's images,
@@ -565,7 +608,7 @@ def main():
     ap.add_argument("--only", default="", help="comma-separated suite transforms (profiling runs)")
     ap.add_argument("--n", type=int, default=SUITE_N, help="suite images (profiling runs)")
     ap.add_argument("--skip-e2e", action="store_true")
-    ap.add_argument("--extras", default="fused,detection,differentiable,large,distort",
+    ap.add_argument("--extras", default="fused,detection,differentiable,large,distort,targets",
                     help="sub-workloads to run after the suite (comma-separated)")
     ap.add_argument("--fused-n", type=int, default=FUSED_N, help="images of the fused workload (profiling runs)")
     args = ap.parse_args()
@@ -631,6 +674,8 @@ def main():
             extra["per_transform_large"] = large_suite(dev, stream, hbm)
         if "distort" in which:
             extra["distortions"] = distortions(dev, stream, hbm)
+        if "targets" in which:
+            extra["fused_detection"] = fused_detection(dev, stream)
     cpu = None
     if rank == 0 and ws == 1 and args.cpu_images > 0:
         # the oracle on the same resident workload, copied to the host

@@ -255,6 +255,46 @@ ALB_API alb_status alb_apply_batch(const alb_chain_cfg* cfg, int32_t n, const al
                            const alb_image* in_dev, void* out_bf16, int32_t mode,
                            void* workspace, size_t workspace_bytes, int32_t* dev_status, void* stream);
 
+/* The chain with its targets (Sec. II-A: a crop and flip applied to an image
+ * and to its masks and boxes in the same way; Fig. 2 detection): as
+ * alb_apply_batch, plus optional per-image instance-mask stacks and boxes.
+ *  mask_in_dev / mask_out_dev: DEVICE arrays of n descriptors (both or
+ *  neither): uint8 HWC with c = N instance planes (N >= 1, per image); the
+ *  input mask has the image's h x w, the output out_h x out_w and the same N.
+ *  A mask is resampled with the nearest rule of the mask resize through the
+ *  same crop window and flip.  An image whose masks do not match records
+ *  ALB_ESHAPE in dev_status and its masks are not written.
+ *  boxes_dev: DEVICE float [n][box_cap][4] xyxy pixel-edge coordinates,
+ *  n_boxes_dev [n]; boxes_out_dev / n_boxes_out_dev likewise: each box is
+ *  cropped to the window (clipped there), scaled, flipped, clipped to the
+ *  output and dropped when it has no area left; order kept.
+ * Fused mode writes the masks from the fused kernel's work items; plain mode
+ * in a launch of their own.  Workspace as for alb_apply_batch. */
+ALB_API alb_status alb_apply_batch_targets(const alb_chain_cfg* cfg, int32_t n, const alb_params* params_dev,
+                                   const alb_image* in_dev, void* out_bf16, const alb_image* mask_in_dev,
+                                   const alb_image* mask_out_dev, const float* boxes_dev,
+                                   const int32_t* n_boxes_dev, int32_t box_cap, float* boxes_out_dev,
+                                   int32_t* n_boxes_out_dev, int32_t mode, void* workspace,
+                                   size_t workspace_bytes, int32_t* dev_status, void* stream);
+
+/* Box-safe crop windows for the chain (for detection): the chain's record
+ * (cfg tid = ALB_CHAIN) with a crop window that contains the union of the
+ * image's boxes, clipped to the image and widened to whole pixels
+ * [ux0, ux1) x [uy0, uy1): x0 = randint[0, ux0], x1 = ux1 + randint[0, W - ux1],
+ * then the same for y (integers by the sampler's rule); without boxes the
+ * chain's RandomResizedCrop draw.  The flip and jitter draws follow as in
+ * alb_sample_params.  Host form: boxes is a HOST float [n_boxes][4]; `out`
+ * a host record.  Batch form: images_dev [n], boxes_dev [n][box_cap][4],
+ * n_boxes_dev [n], params_dev [n] are DEVICE arrays; a count outside
+ * [0, box_cap] records ALB_ECAPACITY and is clamped. */
+ALB_API alb_status alb_sample_chain_box_safe(const alb_sample_cfg* cfg, uint64_t seed, uint64_t stream_id,
+                                     uint32_t index, int32_t h, int32_t w, const float* boxes, int32_t n_boxes,
+                                     alb_params* out);
+ALB_API alb_status alb_sample_chain_box_safe_batch(const alb_sample_cfg* cfg, uint64_t seed, uint64_t stream_id,
+                                           uint32_t first_index, int32_t n, const alb_image* images_dev,
+                                           const float* boxes_dev, const int32_t* n_boxes_dev, int32_t box_cap,
+                                           alb_params* params_dev, int32_t* dev_status, void* stream);
+
 /* Autotuner of the fused kernel's schedule (the paper has no counterpart: it is
  * part of running the chain on a GPU).  Runs alb_apply_batch in fused mode once
  * as warm-up and `reps` times under CUDA events for every candidate (rows per

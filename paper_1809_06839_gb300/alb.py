@@ -108,6 +108,15 @@ def _declare(L):
     L.alb_apply_batch.restype = st
     L.alb_autotune_batch.argtypes = [P(ChainCfg), C.c_int32, vp, vp, vp, vp, C.c_size_t, C.c_int32, P(ChainCfg), vp]
     L.alb_autotune_batch.restype = st
+    L.alb_apply_batch_targets.argtypes = [P(ChainCfg), C.c_int32, vp, vp, vp, vp, vp, vp, vp, C.c_int32, vp, vp,
+                                          C.c_int32, vp, C.c_size_t, vp, vp]
+    L.alb_apply_batch_targets.restype = st
+    L.alb_sample_chain_box_safe.argtypes = [P(SampleCfg), C.c_uint64, C.c_uint64, C.c_uint32, C.c_int32, C.c_int32,
+                                            P(C.c_float), C.c_int32, P(Params)]
+    L.alb_sample_chain_box_safe.restype = st
+    L.alb_sample_chain_box_safe_batch.argtypes = [P(SampleCfg), C.c_uint64, C.c_uint64, C.c_uint32, C.c_int32, vp,
+                                                  vp, vp, C.c_int32, vp, vp, vp]
+    L.alb_sample_chain_box_safe_batch.restype = st
     L.alb_f32_workspace_size.argtypes = [C.c_int32] * 4
     L.alb_f32_workspace_size.restype = C.c_size_t
     for name in ("alb_warp_affine_f32_fwd", "alb_photometric_f32_fwd"):
@@ -340,6 +349,35 @@ def alb_autotune_batch(cfg: ChainCfg, n: int, params_dev, in_dev, out_bf16: torc
     _check(load().alb_autotune_batch(C.byref(cfg), n, _ptr(params_dev), _ptr(in_dev), _ptr(out_bf16), _ptr(ws),
                                      ws.numel(), reps, C.byref(best), _stream(stream)))
     return best
+
+
+def alb_apply_batch_targets(cfg: ChainCfg, n: int, params_dev, in_dev, out_bf16: torch.Tensor, mask_in_dev=None,
+                            mask_out_dev=None, boxes_dev=None, n_boxes_dev=None, box_cap=0, boxes_out_dev=None,
+                            n_boxes_out_dev=None, mode: int = MODE_FUSED, ws=None, dev_status=None, stream=None):
+    _cuda(out_bf16, "out")
+    if ws is None:
+        ws = workspace(alb_batch_workspace_size(cfg, n, mode), out_bf16.device)
+    _check(load().alb_apply_batch_targets(C.byref(cfg), n, _ptr(params_dev), _ptr(in_dev), _ptr(out_bf16),
+                                          _ptr(mask_in_dev), _ptr(mask_out_dev), _ptr(boxes_dev),
+                                          _ptr(n_boxes_dev), box_cap, _ptr(boxes_out_dev), _ptr(n_boxes_out_dev),
+                                          mode, _ptr(ws), ws.numel(), _ptr(dev_status), _stream(stream)))
+
+
+def alb_sample_chain_box_safe(cfg: SampleCfg, seed: int, stream_id: int, index: int, h: int, w: int,
+                              boxes) -> Params:
+    import numpy as np
+    b = np.ascontiguousarray(boxes, dtype=np.float32).reshape(-1, 4)
+    p = Params()
+    _check(load().alb_sample_chain_box_safe(C.byref(cfg), seed, stream_id, index, h, w,
+                                            b.ctypes.data_as(C.POINTER(C.c_float)), b.shape[0], C.byref(p)))
+    return p
+
+
+def alb_sample_chain_box_safe_batch(cfg: SampleCfg, seed: int, stream_id: int, first_index: int, n: int, images_dev,
+                                    boxes_dev, n_boxes_dev, box_cap: int, params_dev, dev_status=None, stream=None):
+    _check(load().alb_sample_chain_box_safe_batch(C.byref(cfg), seed, stream_id, first_index, n, _ptr(images_dev),
+                                                  _ptr(boxes_dev), _ptr(n_boxes_dev), box_cap, _ptr(params_dev),
+                                                  _ptr(dev_status), _stream(stream)))
 
 
 def alb_f32_workspace_size(B, Cc, H, W) -> int:

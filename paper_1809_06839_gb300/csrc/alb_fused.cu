@@ -253,16 +253,47 @@ __global__ void k_chain_luts(int32_t n, const alb_params* __restrict__ prm, uint
 
 // MODE 0: brightness/contrast table (fixed order, pivot 128), float saturation.
 // MODE 1: jitter mode 1 (per-image order; B and C tables [n][512]; uint8 after each op).
-template <int MODE>
+// Instance-mask stacks of the chain: valid when the masks match the image and
+// the output masks have the chain's output size and the same plane count.
+ALB_D bool chain_mask_ok(const alb_image& im, const alb_image& mi, const alb_image& mo, const ChainK& K) {
+  return mi.h == im.h && mi.w == im.w && mi.c >= 1 && mo.c == mi.c && mo.h == K.oh && mo.w == K.ow &&
+         mi.row_stride >= (int64_t)mi.w * mi.c && mo.row_stride >= (int64_t)mo.w * mo.c && mi.data && mo.data;
+}
+
+ALB_D int32_t chain_nn(int32_t d, int32_t n_in, int32_t n_out) {   // nearest rule of the mask resize
+  const int64_t i = ((int64_t)(2 * d + 1) * n_in) / (2 * (int64_t)n_out);
+  return (int32_t)(i < n_in - 1 ? i : n_in - 1);
+}
+
+// rows [r0, r1) of image b's mask stack (nearest, flip folded into the column table)
+ALB_D void chain_mask_rows(const alb_params& p, const alb_image& mi, const alb_image& mo, const int32_t* cnn,
+                           const int32_t* rnn, int32_t r0, int32_t r1, int32_t ow) {
+  const int32_t C = mi.c;
+  const int64_t nbytes = (int64_t)(r1 - r0) * ow * C;
+  const uint8_t* src = (const uint8_t*)mi.data + (int64_t)p.y0 * mi.row_stride + (int64_t)p.x0 * C;
+  for (int64_t i = threadIdx.x; i < nbytes; i += blockDim.x) {
+    const int32_t yy = (int32_t)(i / ((int64_t)ow * C));
+    const int32_t rem = (int32_t)(i - (int64_t)yy * ow * C);
+    const int32_t x = rem / C, c = rem - x * C;
+    ((uint8_t*)mo.data)[(int64_t)(r0 + yy) * mo.row_stride + rem] =
+        __ldg(src + (int64_t)rnn[yy] * mi.row_stride + (int64_t)cnn[x] * C + c);
+  }
+}
+
+template <int MODE, bool MASKS>
 __global__ void __launch_bounds__(256) k_chain_fused(int32_t n, const alb_params* __restrict__ prm,
                                                      const alb_image* __restrict__ imgs,
                                                      const uint8_t* __restrict__ luts, ChainK K, int32_t band,
-                                                     int32_t* __restrict__ queue, __nv_bfloat16* __restrict__ out) {
+                                                     int32_t* __restrict__ queue, __nv_bfloat16* __restrict__ out,
+                                                     const alb_image* __restrict__ mask_in,
+                                                     const alb_image* __restrict__ mask_out, int32_t* status) {
   constexpr int TAB = MODE == 0 ? 256 : 512;
   __shared__ int32_t s_item;
   __shared__ uint8_t s_lut[TAB];
   __shared__ int32_t s_col[1024];
   __shared__ int32_t s_row[kBandMax];
+  __shared__ int32_t s_cnn[1024];      // masks: nearest source column of each output column (flip folded)
+  __shared__ int32_t s_rnn[kBandMax];
   const int32_t bands = (K.oh + band - 1) / band;
   const int64_t total = (int64_t)n * bands;
   const int64_t plane = (int64_t)K.oh * K.ow;
@@ -280,10 +311,14 @@ __global__ void __launch_bounds__(256) k_chain_fused(int32_t n, const alb_params
       for (int x = threadIdx.x; x < K.ow; x += blockDim.x) {
         const int32_t xr = p.flip ? K.ow - 1 - x : x;  // output column x shows resized column xr
         s_col[x] = chain_q5(xr, p.cw, K.ow);
+        if (MASKS) s_cnn[x] = chain_nn(xr, p.cw, K.ow);
       }
       cached = b;
     }
-    if (threadIdx.x < r1 - r0) s_row[threadIdx.x] = chain_q5(r0 + threadIdx.x, p.ch, K.oh);
+    if (threadIdx.x < r1 - r0) {
+      s_row[threadIdx.x] = chain_q5(r0 + threadIdx.x, p.ch, K.oh);
+      if (MASKS) s_rnn[threadIdx.x] = chain_nn(r0 + threadIdx.x, p.ch, K.oh);
+    }
     __syncthreads();
     const alb_image im = imgs[b];
     const uint8_t* win = (const uint8_t*)im.data + (int64_t)p.y0 * im.row_stride + 3 * (int64_t)p.x0;
@@ -339,8 +374,84 @@ __global__ void __launch_bounds__(256) k_chain_fused(int32_t n, const alb_params
         for (int q = 0; q < 3; q++) ob[q * plane + (int64_t)y * K.ow + x] = chain_normalize(v[q], K.k[q], K.m[q]);
       }
     }
+    if (MASKS) {
+      const alb_image mi = mask_in[b], mo = mask_out[b];
+      if (chain_mask_ok(im, mi, mo, K)) chain_mask_rows(p, mi, mo, s_cnn, s_rnn, r0, r1, K.ow);
+      else if (threadIdx.x == 0 && r0 == 0) dev_fail(status, ALB_ESHAPE);
+    }
     __syncthreads();
   }
+}
+
+// Masks of the chain on their own (the plain path): item = (image, band of 32 rows), grid-stride.
+__global__ void __launch_bounds__(256) k_chain_masks(int32_t n, const alb_params* __restrict__ prm,
+                                                     const alb_image* __restrict__ imgs, ChainK K,
+                                                     const alb_image* __restrict__ mask_in,
+                                                     const alb_image* __restrict__ mask_out, int32_t* status) {
+  __shared__ int32_t s_cnn[1024];
+  __shared__ int32_t s_rnn[32];
+  const int32_t bands = (K.oh + 31) / 32;
+  int32_t cached = -1;
+  for (int64_t item = blockIdx.x; item < (int64_t)n * bands; item += gridDim.x) {
+    const int32_t b = (int32_t)(item / bands), r0 = (int32_t)(item - (int64_t)b * bands) * 32;
+    const int32_t r1 = imin(r0 + 32, K.oh);
+    const alb_params& p = prm[b];
+    const alb_image im = imgs[b], mi = mask_in[b], mo = mask_out[b];
+    const bool ok = chain_mask_ok(im, mi, mo, K);
+    __syncthreads();
+    if (ok && b != cached) {
+      for (int x = threadIdx.x; x < K.ow; x += blockDim.x) s_cnn[x] = chain_nn(p.flip ? K.ow - 1 - x : x, p.cw, K.ow);
+      cached = b;
+    }
+    if (threadIdx.x < r1 - r0) s_rnn[threadIdx.x] = chain_nn(r0 + threadIdx.x, p.ch, K.oh);
+    __syncthreads();
+    if (ok) chain_mask_rows(p, mi, mo, s_cnn, s_rnn, r0, r1, K.ow);
+    else if (threadIdx.x == 0 && r0 == 0) dev_fail(status, ALB_ESHAPE);
+  }
+}
+
+// Boxes of the chain: one warp per image; crop to the window (clip there),
+// scale, flip, clip to the output, drop empty boxes, compact in order.
+__global__ void k_chain_boxes(int32_t n, const alb_params* __restrict__ prm, ChainK K, const float* __restrict__ boxes,
+                              const int32_t* __restrict__ nbox, int32_t cap, float* __restrict__ out,
+                              int32_t* __restrict__ nout, int32_t* status) {
+  const int lane = threadIdx.x & 31;
+  const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (b >= n) return;
+  const alb_params& p = prm[b];
+  const int32_t oh = K.oh, ow = K.ow;
+  int32_t cnt = nbox[b];
+  if (cnt > cap || cnt < 0) { if (lane == 0) dev_fail(status, ALB_ECAPACITY); cnt = cnt < 0 ? 0 : cap; }
+  const float* bin = boxes + (int64_t)b * cap * 4;
+  float* bout = out + (int64_t)b * cap * 4;
+  int32_t kept_total = 0;
+  for (int base = 0; base < cnt; base += 32) {
+    const int i = base + lane;
+    double a1 = 0, b1 = 0, a2 = 0, b2 = 0;
+    bool keep = false;
+    if (i < cnt) {
+      double cx1 = bin[4 * i] - p.x0, cy1 = bin[4 * i + 1] - p.y0, cx2 = bin[4 * i + 2] - p.x0, cy2 = bin[4 * i + 3] - p.y0;
+      if (cx1 < 0) cx1 = 0;
+      if (cy1 < 0) cy1 = 0;
+      if (cx2 > p.cw) cx2 = p.cw;
+      if (cy2 > p.ch) cy2 = p.ch;
+      a1 = cx1 * ow / p.cw; a2 = cx2 * ow / p.cw; b1 = cy1 * oh / p.ch; b2 = cy2 * oh / p.ch;
+      if (p.flip) { const double t = a1; a1 = (double)ow - a2; a2 = (double)ow - t; }
+      if (a1 < 0) a1 = 0;
+      if (b1 < 0) b1 = 0;
+      if (a2 > ow) a2 = ow;
+      if (b2 > oh) b2 = oh;
+      keep = !(a2 - a1 <= 0.0 || b2 - b1 <= 0.0);
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (keep) {
+      const int slot = kept_total + __popc(m & ((1u << lane) - 1u));
+      bout[4 * slot] = (float)a1; bout[4 * slot + 1] = (float)b1;
+      bout[4 * slot + 2] = (float)a2; bout[4 * slot + 3] = (float)b2;
+    }
+    kept_total += __popc(m);
+  }
+  if (lane == 0) nout[b] = kept_total;
 }
 
 // ---------------------------------------------------------------- plain path
@@ -502,15 +613,17 @@ static void tune_store(int32_t dev, const alb_chain_cfg& cfg, int32_t n, int32_t
   g_tune.push_back(TuneEntry{dev, cfg.out_h, cfg.out_w, cfg.jitter, bk, band, per_sm});
 }
 
-static int fused_max_per_sm(int jitter) {
+static int fused_max_per_sm(int jitter, bool masks = false) {
   int per_sm = 0;
-  if (jitter) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chain_fused<1>, 256, 0);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chain_fused<0>, 256, 0);
+  auto kern = jitter ? (masks ? k_chain_fused<1, true> : k_chain_fused<1, false>)
+                     : (masks ? k_chain_fused<0, true> : k_chain_fused<0, false>);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0);
   return per_sm < 1 ? 1 : per_sm;
 }
 
 alb_status launch_chain(const alb_chain_cfg& cfg, int32_t n, const alb_params* params, const alb_image* in,
-                        void* out, int32_t mode, Carve& ws, int32_t* status, cudaStream_t st) {
+                        void* out, int32_t mode, Carve& ws, int32_t* status, cudaStream_t st,
+                        const alb_image* mask_in, const alb_image* mask_out) {
   const ChainK K = make_consts(cfg);
   const int jit = cfg.jitter;
   const int64_t npx = (int64_t)cfg.out_h * cfg.out_w;
@@ -537,7 +650,7 @@ alb_status launch_chain(const alb_chain_cfg& cfg, int32_t n, const alb_params* p
       if (cfg.tile_h > 0) band = imin(cfg.tile_h, kBandMax);
       per_sm = cfg.ctas_per_sm;
     }
-    const int max_per_sm = fused_max_per_sm(jit);
+    const int max_per_sm = fused_max_per_sm(jit, mask_in != nullptr);
     if (per_sm <= 0 || per_sm > max_per_sm) per_sm = max_per_sm;
     if (jit) {
       // the contrast pivots first (a reduction over each image), then the C tables
@@ -547,8 +660,9 @@ alb_status launch_chain(const alb_chain_cfg& cfg, int32_t n, const alb_params* p
       ALB_CUDA(cudaGetLastError());
     }
     ALB_CUDA(cudaMemsetAsync(queue, 0, sizeof(int32_t), st));
-    if (jit) k_chain_fused<1><<<per_sm * sm_count(), 256, 0, st>>>(n, params, in, luts, K, band, queue, o);
-    else k_chain_fused<0><<<per_sm * sm_count(), 256, 0, st>>>(n, params, in, luts, K, band, queue, o);
+    auto kern = jit ? (mask_in ? k_chain_fused<1, true> : k_chain_fused<1, false>)
+                    : (mask_in ? k_chain_fused<0, true> : k_chain_fused<0, false>);
+    kern<<<per_sm * sm_count(), 256, 0, st>>>(n, params, in, luts, K, band, queue, o, mask_in, mask_out, status);
     ALB_CUDA(cudaGetLastError());
     return ALB_OK;
   }
@@ -578,6 +692,10 @@ alb_status launch_chain(const alb_chain_cfg& cfg, int32_t n, const alb_params* p
     }
     k_plain_normalize_u8<<<grid, 256, 0, st>>>(n, K, cur, o);
     ALB_CUDA(cudaGetLastError());
+    if (mask_in) {
+      k_chain_masks<<<grid, 256, 0, st>>>(n, params, in, K, mask_in, mask_out, status);
+      ALB_CUDA(cudaGetLastError());
+    }
     return ALB_OK;
   }
   k_plain_lut<<<grid, 256, 0, st>>>(n, K, luts, b, a);
@@ -586,6 +704,10 @@ alb_status launch_chain(const alb_chain_cfg& cfg, int32_t n, const alb_params* p
   ALB_CUDA(cudaGetLastError());
   k_plain_normalize<<<grid, 256, 0, st>>>(n, K, f, o);
   ALB_CUDA(cudaGetLastError());
+  if (mask_in) {
+    k_chain_masks<<<grid, 256, 0, st>>>(n, params, in, K, mask_in, mask_out, status);
+    ALB_CUDA(cudaGetLastError());
+  }
   return ALB_OK;
 }
 
@@ -686,3 +808,46 @@ extern "C" alb_status alb_autotune_batch(const alb_chain_cfg* cfg, int32_t n, co
   best->ctas_per_sm = best_per_sm;
   return ALB_OK;
 }
+
+// The chain with its targets: instance-mask stacks (nearest, the same crop
+// and flip) and boxes.  Fused mode writes the masks from the fused kernel's
+// work items; plain mode in a launch of their own.
+extern "C" alb_status alb_apply_batch_targets(const alb_chain_cfg* cfg, int32_t n, const alb_params* params_dev,
+                                              const alb_image* in_dev, void* out_bf16, const alb_image* mask_in_dev,
+                                              const alb_image* mask_out_dev, const float* boxes_dev,
+                                              const int32_t* n_boxes_dev, int32_t box_cap, float* boxes_out_dev,
+                                              int32_t* n_boxes_out_dev, int32_t mode, void* workspace,
+                                              size_t workspace_bytes, int32_t* dev_status, void* stream) {
+  ALB_REQUIRE(cfg, ALB_EINVAL, "alb_apply_batch_targets: null cfg");
+  ALB_REQUIRE(n >= 0, ALB_EINVAL, "alb_apply_batch_targets: negative n");
+  if (n == 0) return ALB_OK;
+  ALB_REQUIRE(params_dev && in_dev && out_bf16, ALB_EINVAL, "alb_apply_batch_targets: null device array");
+  ALB_REQUIRE(mode == ALB_MODE_FUSED || mode == ALB_MODE_PLAIN, ALB_EINVAL, "alb_apply_batch_targets: bad mode %d",
+              mode);
+  ALB_REQUIRE(cfg->out_h > 0 && cfg->out_w > 0 && cfg->out_w <= 1024, ALB_ESHAPE,
+              "alb_apply_batch_targets: bad output size");
+  ALB_REQUIRE(cfg->tile_w == 0 && cfg->tile_h >= 0 && cfg->tile_h <= kBandMax && cfg->ctas_per_sm >= 0, ALB_EINVAL,
+              "alb_apply_batch_targets: tile_h must be in [0, %d], tile_w 0, ctas_per_sm >= 0", kBandMax);
+  ALB_REQUIRE(cfg->jitter == 0 || cfg->jitter == 1, ALB_EINVAL, "alb_apply_batch_targets: jitter must be 0 or 1");
+  for (int c = 0; c < 3; c++) ALB_REQUIRE(cfg->std[c] > 0, ALB_EINVAL, "alb_apply_batch_targets: std must be > 0");
+  ALB_REQUIRE(!mask_in_dev == !mask_out_dev, ALB_EINVAL, "alb_apply_batch_targets: mask_in and mask_out go together");
+  const bool boxes = boxes_dev || n_boxes_dev || boxes_out_dev || n_boxes_out_dev;
+  ALB_REQUIRE(!boxes || (boxes_dev && n_boxes_dev && boxes_out_dev && n_boxes_out_dev && box_cap > 0), ALB_EINVAL,
+              "alb_apply_batch_targets: box arrays go together and need box_cap > 0");
+  ALB_REQUIRE(workspace && workspace_bytes >= chain_workspace(*cfg, n, mode), ALB_EWORKSPACE,
+              "alb_apply_batch_targets: workspace of %zu bytes is smaller than %zu", workspace_bytes,
+              chain_workspace(*cfg, n, mode));
+  cudaStream_t st = (cudaStream_t)stream;
+  Carve cv{(char*)workspace, 0, workspace_bytes};
+  alb_status rc = launch_chain(*cfg, n, params_dev, in_dev, out_bf16, mode, cv, dev_status, st, mask_in_dev,
+                               mask_out_dev);
+  if (rc != ALB_OK) return rc;
+  if (boxes) {
+    const ChainK K = make_consts(*cfg);
+    k_chain_boxes<<<(n + 3) / 4, 128, 0, st>>>(n, params_dev, K, boxes_dev, n_boxes_dev, box_cap, boxes_out_dev,
+                                               n_boxes_out_dev, dev_status);
+    ALB_CUDA(cudaGetLastError());
+  }
+  return ALB_OK;
+}
+

@@ -33,7 +33,8 @@ alb_status launch_photometric(int32_t tid, int32_t n, const Plan& plan, const Im
 
 // alb_fused.cu
 alb_status launch_chain(const alb_chain_cfg& cfg, int32_t n, const alb_params* params, const alb_image* in,
-                        void* out, int32_t mode, Carve& ws, int32_t* status, cudaStream_t st);
+                        void* out, int32_t mode, Carve& ws, int32_t* status, cudaStream_t st,
+                        const alb_image* mask_in = nullptr, const alb_image* mask_out = nullptr);
 size_t chain_workspace(const alb_chain_cfg& cfg, int32_t n, int32_t mode);
 
 inline bool is_geometric(int32_t tid) {

@@ -248,6 +248,72 @@ ALB_HD int sample_one(const alb_sample_cfg& cfg, uint64_t seed, uint64_t sid, ui
   return ALB_OK;
 }
 
+// The chain's record with a box-safe crop window: the window contains the
+// union of the image's boxes (clipped to the image, widened to whole pixels
+// [ux0, ux1) x [uy0, uy1)): x0 = randint[0, ux0], x1 = ux1 + randint[0, W - ux1],
+// then y; without boxes (or an empty union) the chain's RandomResizedCrop
+// draw.  The probability, flip and jitter draws are those of the chain.
+ALB_HD int sample_chain_box_safe(const alb_sample_cfg& cfg, uint64_t seed, uint64_t sid, uint32_t index, int32_t h,
+                                 int32_t w, const float* boxes, int32_t nb, alb_params& p) {
+  params_identity(p, ALB_CHAIN, h, w);
+  if (cfg.tid != ALB_CHAIN) return ALB_EINVAL;
+  if (h <= 0 || w <= 0 || cfg.out_h <= 0 || cfg.out_w <= 0) return ALB_ESHAPE;
+  Philox s;
+  ph_init(s, seed, sid, index);
+  (void)ph_u01(s);                 // the probability draw; the chain always applies
+  p.apply = 1;
+  p.out_h = cfg.out_h; p.out_w = cfg.out_w;
+  double ux1 = 0, uy1 = 0, ux2 = 0, uy2 = 0;
+  bool have = false;
+  for (int32_t i = 0; i < nb; i++) {
+    double a = boxes[4 * i], b = boxes[4 * i + 1], c = boxes[4 * i + 2], d = boxes[4 * i + 3];
+    if (a < 0) a = 0;
+    if (b < 0) b = 0;
+    if (c > w) c = w;
+    if (d > h) d = h;
+    if (c <= a || d <= b) continue;
+    if (!have || a < ux1) ux1 = a;
+    if (!have || b < uy1) uy1 = b;
+    if (!have || c > ux2) ux2 = c;
+    if (!have || d > uy2) uy2 = d;
+    have = true;
+  }
+  if (have) {
+    const int32_t x0i = (int32_t)floor(ux1), y0i = (int32_t)floor(uy1), x1i = (int32_t)ceil(ux2), y1i = (int32_t)ceil(uy2);
+    const int32_t x0 = ph_randint(s, x0i);
+    const int32_t x1 = x1i + ph_randint(s, w - x1i);
+    const int32_t y0 = ph_randint(s, y0i);
+    const int32_t y1 = y1i + ph_randint(s, h - y1i);
+    p.x0 = x0; p.cw = x1 - x0; p.y0 = y0; p.ch = y1 - y0;
+  } else {
+    sample_rrc(s, h, w, cfg.lo[0], cfg.hi[0], cfg.lo[1], cfg.hi[1], p);
+  }
+  p.flip = ph_u01(s) < 0.5;
+  p.beta = ph_uniform(s, cfg.lo[2], cfg.hi[2]);
+  p.alpha = ph_uniform(s, cfg.lo[2], cfg.hi[2]);
+  p.sat = ph_uniform(s, cfg.lo[2], cfg.hi[2]);
+  p.k = ph_randint(s, 5);
+  return ALB_OK;
+}
+
+__global__ void k_sample_box_safe(alb_sample_cfg cfg, uint64_t seed, uint64_t sid, uint32_t first, int32_t n,
+                                  const alb_image* __restrict__ imgs, const float* __restrict__ boxes,
+                                  const int32_t* __restrict__ nbox, int32_t cap, alb_params* __restrict__ out,
+                                  int32_t* status) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const alb_image im = imgs[i];
+  int32_t nb = nbox[i];
+  if (nb < 0 || nb > cap) { dev_fail(status, ALB_ECAPACITY); nb = nb < 0 ? 0 : cap; }
+  alb_params p;
+  int rc = sample_chain_box_safe(cfg, seed, sid, first + (uint32_t)i, im.h, im.w, boxes + (int64_t)i * cap * 4, nb, p);
+  if (rc != ALB_OK) {
+    params_identity(p, ALB_CHAIN, im.h, im.w);
+    dev_fail(status, rc);
+  }
+  out[i] = p;
+}
+
 __global__ void k_sample(alb_sample_cfg cfg, uint64_t seed, uint64_t sid, uint32_t first, int32_t n,
                          const alb_image* __restrict__ imgs, alb_params* __restrict__ out, int32_t* status) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -290,3 +356,36 @@ extern "C" alb_status alb_sample_params_batch(const alb_sample_cfg* cfg, uint64_
   ALB_CUDA(cudaGetLastError());
   return ALB_OK;
 }
+
+extern "C" alb_status alb_sample_chain_box_safe(const alb_sample_cfg* cfg, uint64_t seed, uint64_t stream_id,
+                                                 uint32_t index, int32_t h, int32_t w, const float* boxes,
+                                                 int32_t n_boxes, alb_params* out) {
+  ALB_REQUIRE(cfg && out && n_boxes >= 0 && (boxes || n_boxes == 0), ALB_EINVAL,
+              "alb_sample_chain_box_safe: bad argument");
+  ALB_REQUIRE(cfg->tid == ALB_CHAIN, ALB_EINVAL, "alb_sample_chain_box_safe: cfg tid must be ALB_CHAIN");
+  int rc = sample_chain_box_safe(*cfg, seed, stream_id, index, h, w, boxes, n_boxes, *out);
+  if (rc != ALB_OK) {
+    set_error("alb_sample_chain_box_safe: status %d for a %dx%d image", rc, h, w);
+    return (alb_status)rc;
+  }
+  return ALB_OK;
+}
+
+extern "C" alb_status alb_sample_chain_box_safe_batch(const alb_sample_cfg* cfg, uint64_t seed, uint64_t stream_id,
+                                                       uint32_t first_index, int32_t n, const alb_image* images_dev,
+                                                       const float* boxes_dev, const int32_t* n_boxes_dev,
+                                                       int32_t box_cap, alb_params* params_dev, int32_t* dev_status,
+                                                       void* stream) {
+  ALB_REQUIRE(cfg, ALB_EINVAL, "alb_sample_chain_box_safe_batch: null cfg");
+  ALB_REQUIRE(cfg->tid == ALB_CHAIN, ALB_EINVAL, "alb_sample_chain_box_safe_batch: cfg tid must be ALB_CHAIN");
+  ALB_REQUIRE(n >= 0, ALB_EINVAL, "alb_sample_chain_box_safe_batch: negative n");
+  if (n == 0) return ALB_OK;
+  ALB_REQUIRE(images_dev && params_dev && boxes_dev && n_boxes_dev && box_cap > 0, ALB_EINVAL,
+              "alb_sample_chain_box_safe_batch: null device array or box_cap <= 0");
+  k_sample_box_safe<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(*cfg, seed, stream_id, first_index, n,
+                                                                      images_dev, boxes_dev, n_boxes_dev, box_cap,
+                                                                      params_dev, dev_status);
+  ALB_CUDA(cudaGetLastError());
+  return ALB_OK;
+}
+

@@ -155,6 +155,18 @@ def ragged_masks(sizes, seed: int = BASE_SEED, device="cpu", n_classes: int = 20
     return rb
 
 
+def instance_stacks(sizes, planes, seed: int = BASE_SEED, device="cpu") -> Ragged:
+    """Per image an N-plane instance stack (uint8 HWC, c = N): plane k is the
+    binary mask (255) of blob class k of a 20-class blob label mask."""
+    shapes = [(h, w, n) for (h, w), n in zip(sizes, planes)]
+    rb = empty_ragged(shapes, device=device)
+    for i, ((h, w), n) in enumerate(zip(sizes, planes)):
+        lab = blob_mask(h, w, i, seed, 20, device=device)
+        k = torch.arange(n, device=lab.device, dtype=lab.dtype)
+        rb.image(i).copy_((lab[:, :, None] == k).to(torch.uint8) * 255)
+    return rb
+
+
 def float_images(b: int, c: int, h: int, w: int, seed: int = BASE_SEED, device="cpu") -> torch.Tensor:
     g = torch.Generator(device="cpu").manual_seed(seed)
     return torch.rand((b, c, h, w), generator=g, dtype=torch.float32).to(device)

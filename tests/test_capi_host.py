@@ -118,6 +118,19 @@ def test_schedule_fields_are_checked_without_cuda(L):
                                 None) == alb.ALB_EWORKSPACE
 
 
+def test_host_box_safe_sampler_matches_oracle(L):
+    oc = O.make_cfg(O.CHAIN, out_h=224, out_w=224, lo=(0.08, 3 / 4, 0.6), hi=(1.0, 4 / 3, 1.4))
+    lc = cfg_to_lib(oc, alb)
+    from paper_1809_06839_gb300 import synth
+    for i in range(80):
+        h, w = 256 + (i * 37) % 700, 256 + (i * 91) % 700
+        boxes = synth.random_boxes(h, w, i, 3)[: i % 7]
+        op = O.sample_chain_box_safe(oc, 1809, 20, i, h, w, boxes)
+        lp = alb.alb_sample_chain_box_safe(lc, 1809, 20, i, h, w, boxes)
+        err = same_params(op, lp)
+        assert err is None, (i, err)
+
+
 def test_distortion_records_are_checked_without_cuda(L):
     """alb_apply rejects boxes with the elastic transform and out-of-range
     distortion records before any device work."""

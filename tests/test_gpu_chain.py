@@ -165,3 +165,81 @@ def test_jitter_mode1_full_size_batch_sampled(dev):
         op = O.sample_params(oc, 1810, 20, i, h, w)
         ref = O.chain_image(op, rb.image(i).cpu().numpy(), jitter=1)
         assert np.array_equal(fb[k], ref), i
+
+
+def test_chain_targets_masks_and_boxes(dev):
+    """Instance-mask stacks (1 to 20 planes) and boxes through the chain,
+    fused and plain, against the oracle; the images are unchanged by the
+    targets; box-safe windows from the device sampler equal the oracle's."""
+    from paper_1809_06839_gb300.ragged import mask_output_batch
+    from helpers import same_params
+    sizes = [(256 + (i * 97) % 769, 256 + (i * 193) % 769) for i in range(10)] + [(3, 900), (1024, 1024)]
+    planes = [1, 3, 20, 8, 1, 5, 2, 20, 4, 1, 7, 3]
+    n = len(sizes)
+    rb = synth.ragged_noise(sizes, seed=12)
+    rng = np.random.default_rng(12)
+    mask_np = [(rng.integers(0, 2, (h, w, c)) * rng.integers(1, 256, c)).astype(np.uint8)
+               for (h, w), c in zip(sizes, planes)]
+    cap = 50
+    boxes = np.zeros((n, cap, 4), np.float32)
+    nb = np.zeros(n, np.int32)
+    for i, (h, w) in enumerate(sizes):
+        b = synth.random_boxes(h, w, i, 12)[: 1 + i * 3]
+        boxes[i, :len(b)] = b
+        nb[i] = len(b)
+    oc = O.make_cfg(O.CHAIN, **CHAIN_CFG)
+    din = DeviceBatch(to_device(rb, dev))
+    bd, nbd = torch.from_numpy(boxes).to(dev), torch.from_numpy(nb).to(dev)
+    pdev = torch.zeros(n * 232, dtype=torch.uint8, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    alb.alb_sample_chain_box_safe_batch(cfg_to_lib(oc, alb), 12, 20, 0, n, din.dev, bd, nbd, cap, pdev, status)
+    got_p = alb.params_from_device(pdev)
+    ops = [O.sample_chain_box_safe(oc, 12, 20, i, h, w, boxes[i, :nb[i]]) for i, (h, w) in enumerate(sizes)]
+    for i in range(n):
+        assert same_params(ops[i], got_p[i]) is None, i
+    mdesc = []
+    flat = []
+    for m in mask_np:
+        t = torch.from_numpy(m).to(dev)
+        flat.append(t)
+        mdesc.append(alb.image_desc(t))
+    mi = alb.descs_to_device(mdesc, dev)
+    results = {}
+    for mode in (alb.MODE_FUSED, alb.MODE_PLAIN):
+        outs = [torch.zeros((224, 224, c), dtype=torch.uint8, device=dev) for c in planes]
+        mo = alb.descs_to_device([alb.image_desc(t) for t in outs], dev)
+        img = torch.empty((n, 3, 224, 224), dtype=torch.bfloat16, device=dev)
+        bo, nbo = torch.zeros_like(bd), torch.zeros_like(nbd)
+        alb.alb_apply_batch_targets(alb.chain_cfg(), n, pdev, din.dev, img, mi, mo, bd, nbd, cap, bo, nbo, mode,
+                                    dev_status=status)
+        torch.cuda.synchronize()
+        assert int(status.item()) == 0
+        results[mode] = (bits(img), [t.cpu().numpy() for t in outs], bo.cpu().numpy(), nbo.cpu().numpy())
+    for mode, (ib, ms, bo, nbo) in results.items():
+        for i, (h, w) in enumerate(sizes):
+            assert np.array_equal(ib[i], O.chain_image(ops[i], rb.image(i).numpy())), (mode, i)
+            assert np.array_equal(ms[i], O.chain_mask(ops[i], mask_np[i])), (mode, "mask", i)
+            bref = O.chain_boxes(ops[i], boxes[i, :nb[i]])
+            assert nbo[i] == len(bref) == nb[i], (mode, "boxes", i)       # box-safe windows keep every box
+            assert np.abs(bo[i, :nbo[i]] - bref).max(initial=0) <= 1e-4
+
+
+def test_chain_target_masks_of_the_wrong_size_are_rejected_on_device(dev):
+    sizes = [(300, 400), (280, 260)]
+    rb = synth.ragged_noise(sizes, seed=2)
+    oc = O.make_cfg(O.CHAIN, **CHAIN_CFG)
+    ops = [O.sample_params(oc, 2, 20, i, h, w) for i, (h, w) in enumerate(sizes)]
+    din = DeviceBatch(to_device(rb, dev))
+    good = torch.ones((300, 400, 2), dtype=torch.uint8, device=dev)
+    bad = torch.ones((200, 260, 2), dtype=torch.uint8, device=dev)         # height differs from its image
+    mi = alb.descs_to_device([alb.image_desc(good), alb.image_desc(bad)], dev)
+    outs = [torch.full((224, 224, 2), 7, dtype=torch.uint8, device=dev) for _ in range(2)]
+    mo = alb.descs_to_device([alb.image_desc(t) for t in outs], dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    img = torch.empty((2, 3, 224, 224), dtype=torch.bfloat16, device=dev)
+    alb.alb_apply_batch_targets(alb.chain_cfg(), 2, alb.params_to_device([to_lib(o, alb) for o in ops], dev), din.dev,
+                                img, mi, mo, dev_status=status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == alb.ALB_ESHAPE
+    assert (outs[1] == 7).all()                                              # untouched
+    assert np.array_equal(outs[0].cpu().numpy(), O.chain_mask(ops[0], good.cpu().numpy()))
