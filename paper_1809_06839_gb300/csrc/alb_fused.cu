@@ -269,14 +269,17 @@ ALB_D int32_t chain_nn(int32_t d, int32_t n_in, int32_t n_out) {   // nearest ru
 ALB_D void chain_mask_rows(const alb_params& p, const alb_image& mi, const alb_image& mo, const int32_t* cnn,
                            const int32_t* rnn, int32_t r0, int32_t r1, int32_t ow) {
   const int32_t C = mi.c;
-  const int64_t nbytes = (int64_t)(r1 - r0) * ow * C;
+  const int32_t npx = (r1 - r0) * ow;        // at most 32 rows x 1024 columns
   const uint8_t* src = (const uint8_t*)mi.data + (int64_t)p.y0 * mi.row_stride + (int64_t)p.x0 * C;
-  for (int64_t i = threadIdx.x; i < nbytes; i += blockDim.x) {
-    const int32_t yy = (int32_t)(i / ((int64_t)ow * C));
-    const int32_t rem = (int32_t)(i - (int64_t)yy * ow * C);
-    const int32_t x = rem / C, c = rem - x * C;
-    ((uint8_t*)mo.data)[(int64_t)(r0 + yy) * mo.row_stride + rem] =
-        __ldg(src + (int64_t)rnn[yy] * mi.row_stride + (int64_t)cnn[x] * C + c);
+  for (int32_t i = threadIdx.x; i < npx; i += blockDim.x) {
+    const int32_t yy = i / ow, x = i - yy * ow;
+    const uint8_t* s = src + (int64_t)rnn[yy] * mi.row_stride + (int64_t)cnn[x] * C;
+    uint8_t* d = (uint8_t*)mo.data + (int64_t)(r0 + yy) * mo.row_stride + (int64_t)x * C;
+    if (C == 1) {
+      *d = __ldg(s);
+    } else {
+      for (int32_t c = 0; c < C; c++) d[c] = __ldg(s + c);
+    }
   }
 }
 
