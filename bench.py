@@ -37,12 +37,13 @@ sys.path.insert(0, ROOT)
 METRIC = "images/s per transform & fused ragged-batch pipeline; HBM GB/s vs GB300 peak"
 UNIT = "images/s"
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per image of the
-# resampling kernel, from one ncu --set full capture of 256 images of the suite
-# workload (same H, W distribution), scaled per image; the roofline's traffic
-# figure is this times the images of one launch.  Only kernels whose code is
-# unchanged since that capture are listed.
-NCU_DRAM_BYTES_PER_IMAGE = {"Rotate": 1004318.0, "ShiftScaleRotate": 965409.0, "Resize512": 1125015.0}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per image of a
+# transform's kernel, from one ncu --set full capture of 256 images of the
+# suite workload (same H, W distribution), scaled per image; the roofline's
+# traffic figure is this times the images of one launch.  Only kernels whose
+# code is unchanged since that capture are listed.
+NCU_DRAM_BYTES_PER_IMAGE = {"Rotate": 977333.0, "Resize512": 1134236.0, "Brightness": 842170.0,
+                            "ShiftHSV": 846090.0, "PadToSize512": 1179525.0}
 SUITE_N, SUITE_LO, SUITE_HI = 2000, 333, 500
 FUSED_N, FUSED_LO, FUSED_HI = 4096, 256, 1024
 DET_N, DET_HW = 256, 1024
