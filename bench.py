@@ -618,6 +618,7 @@ def main():
         reference_arm(args, ws, rank, dist)
         return
     from paper_1809_06839_gb300 import alb as A
+    from paper_1809_06839_gb300.replicas import max_over_ranks
     A.load()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
@@ -633,10 +634,7 @@ def main():
     clk.start()
     t = time_steps(lambda: suite.step(stream), stream, args.steps, args.warmup, barrier)
     clocks = clk.stop()
-    if dist is not None:
-        tt = torch.tensor([t], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
+    t = max_over_ranks(t, dist, dev)          # the slowest rank's time (replicas: no data exchange)
     per_step = t / args.steps
     value = ws * suite.n * len(suite.ops) / per_step
     ops_t = per_op_times(suite, stream)
