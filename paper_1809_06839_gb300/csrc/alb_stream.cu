@@ -57,7 +57,7 @@ ALB_D void lut_px(const uint8_t* tab, int lb, uint32_t& r, uint32_t& g, uint32_t
 // each end of a run and images that are not contiguous and 16-byte aligned take
 // a per-byte / per-pixel path.
 constexpr int kBulkChunk = 12288;   // bytes per stage: 768 vectors, a multiple of 3 and 16
-constexpr int kBulkStages = 4;
+constexpr int kBulkStages = 3;
 static_assert(kBulkChunk % 48 == 0, "a stage starts on the same channel phase as the previous one");
 
 // Streams bytes [0, total) of src (and, with dst, back to dst) through the
@@ -244,17 +244,8 @@ __global__ void __launch_bounds__(256) k_hist_bulk(Plan plan, ImgList in, uint32
       const int phi = (int)(A % 3);
       dead = !bulk_pipeline(sm.stage, sm.full, seq, ip + A, nullptr, E - A, status,
                             [&](uint8_t* sb, int nbytes, int64_t) {
-        // lane l of warp w takes vectors 24 l + ((3 w + j + l) mod 24), j = 0..2: the
-        // lanes of a warp histogram pixels ~128 apart (neighbours of a smooth image
-        // repeat values, and equal bins in one atomic instruction serialise); the
-        // rotation by l keeps each quarter-warp's 16-byte loads in distinct banks
-        static_assert(kBulkChunk == 768 * 16, "24 vectors per lane, 256 threads");
         const int nv = nbytes >> 4;
-        const int lane = tid & 31, wid = tid >> 5;
-#pragma unroll
-        for (int j = 0; j < 3; j++) {
-          const int v = 24 * lane + (3 * wid + j + lane) % 24;
-          if (v >= nv) continue;
+        for (int v = tid; v < nv; v += bs) {
           const uint4 x = *reinterpret_cast<const uint4*>(sb + 16 * v);
           const int rho = (phi + v) % 3;
           uint32_t* h0 = my + 256 * rho;
