@@ -1038,14 +1038,11 @@ alb_status launch_tile_geometric(int32_t tid, const Plan& plan, const ImgList& i
     ALB_CUDA(cudaGetLastError());
     return ALB_OK;
   }
+  // single-plane masks of the warps and resizes (RGB images returned above)
   k_plan_tiles<<<1, 1024, 0, st>>>(out, plan.n, WT, WT, prefix, tiles_x, chk);
   ALB_CUDA(cudaGetLastError());
-  if (affine) {
-    if (mask) return launch_k(k_resample_warp<MAP_AFFINE, true, 1>, st, plan, in, out, prm);
-    return launch_k(k_resample_warp<MAP_AFFINE, false, 3>, st, plan, in, out, prm);
-  }
-  if (mask) return launch_k(k_resample_warp<MAP_RESIZE, true, 1>, st, plan, in, out, prm);
-  return launch_k(k_resample_warp<MAP_RESIZE, false, 3>, st, plan, in, out, prm);
+  if (affine) return launch_k(k_resample_warp<MAP_AFFINE, true, 1>, st, plan, in, out, prm);
+  return launch_k(k_resample_warp<MAP_RESIZE, true, 1>, st, plan, in, out, prm);
 }
 
 }  // namespace alb
