@@ -213,18 +213,27 @@ __global__ void __launch_bounds__(256) k_chain_pivot(int32_t n, const alb_params
     const uint8_t* win = (const uint8_t*)im.data + (int64_t)p.y0 * im.row_stride + 3 * (int64_t)p.x0;
     const int pos_c = jitter_pos_c(p.k);
     const float s = (float)p.sat;
-    uint64_t acc = 0;
-    const int32_t npx = (r1 - r0) * K.ow;
-    for (int32_t i = threadIdx.x; i < npx; i += blockDim.x) {
-      const int32_t yy = i / K.ow, x = i - yy * K.ow;
-      uint32_t rgb[3];
-      chain_bilinear(win, im.row_stride, p.ch, p.cw, s_col[x], s_row[yy], rgb);
-      jitter_ops(rgb, p.k, 0, pos_c, s_tb, s_tb, s);
-      acc += grey_bt601(rgb);
+    uint32_t acc = 0;       // < 256 * 2 * 32 * 1024 per thread and item: fits 32 bits
+    const int32_t hw = (K.ow + 1) >> 1;                 // pixel pairs per row (the last may be single)
+    const int32_t npair = (r1 - r0) * hw;
+    for (int32_t i = threadIdx.x; i < npair; i += blockDim.x) {
+      const int32_t yy = i / hw, x = 2 * (i - yy * hw);
+      const int32_t yq = s_row[yy];
+      uint32_t a[3];
+      chain_bilinear(win, im.row_stride, p.ch, p.cw, s_col[x], yq, a);
+      jitter_ops(a, p.k, 0, pos_c, s_tb, s_tb, s);
+      acc += grey_bt601(a);
+      if (x + 1 < K.ow) {
+        uint32_t c[3];
+        chain_bilinear(win, im.row_stride, p.ch, p.cw, s_col[x + 1], yq, c);
+        jitter_ops(c, p.k, 0, pos_c, s_tb, s_tb, s);
+        acc += grey_bt601(c);
+      }
     }
+    unsigned long long acc64 = acc;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = acc;
+    for (int o = 16; o > 0; o >>= 1) acc64 += __shfl_down_sync(0xffffffffu, acc64, o);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = acc64;
     __syncthreads();
     if (threadIdx.x == 0) {
       unsigned long long t = 0;
@@ -657,7 +666,9 @@ alb_status launch_chain(const alb_chain_cfg& cfg, int32_t n, const alb_params* p
     if (per_sm <= 0 || per_sm > max_per_sm) per_sm = max_per_sm;
     if (jit) {
       // the contrast pivots first (a reduction over each image), then the C tables
-      k_chain_pivot<<<4 * sm_count(), 256, 0, st>>>(n, params, in, luts, K, 16, sums);
+      int pv = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pv, k_chain_pivot, 256, 0);
+      k_chain_pivot<<<(pv < 1 ? 1 : pv) * sm_count(), 256, 0, st>>>(n, params, in, luts, K, 32, sums);
       ALB_CUDA(cudaGetLastError());
       k_jitter_luts<<<n, 256, 0, st>>>(n, params, sums, npx, 1, luts);
       ALB_CUDA(cudaGetLastError());
