@@ -416,21 +416,23 @@ __global__ void __launch_bounds__(32 * NWARP, 5) k_resample_warp(Plan plan, ImgL
 // separability of the Q5 weights: out = ((32 - fy) h(iy) + fy h(iy + 1) + 512)
 // >> 10 with h(i) = (32 - fx) p(i, ix) + fx p(i, ix + 1) exact in integers, so
 // h of a source row is computed once per output column and reused by every
-// output row whose tap rows include it.  A warp owns a 32 x 16 output tile,
+// output row whose tap rows include it.  A warp owns a 32 x 32 output tile,
 // lane j = output column j; it walks the tile's rows top to bottom keeping the
 // two current tap rows' h in registers (for an enlargement most output rows
 // reuse both, or shift by one source row).  The tile's source box (up to
 // RB_X x RB_Y pixels: enlargements and reductions to ~0.95) is staged per warp
-// in shared memory by cp.async, double-buffered; the box is kept small so that
-// ~36 warps fit on an SM (the row chain is latency-bound).  Larger footprints
-// read their taps from global memory.
-constexpr int RT_W = 32, RT_H = 16;   // output tile (columns x rows)
-constexpr int RB_X = 36, RB_Y = 20;   // staged box (source pixels x rows)
+// in shared memory by cp.async, double-buffered.  Measured trade-off: a taller
+// tile amortises the per-tile geometry, a larger box costs warps per SM (the
+// row chain is latency-bound); 32 x 32 with a 36 x 36 box beat 32 x 16 with
+// 36 x 20 and 32 x 32 with 36 x 28.  Larger footprints read global memory.
+constexpr int RT_W = 32, RT_H = 32;   // output tile (columns x rows)
+constexpr int RB_X = 36, RB_Y = 36;   // staged box (source pixels x rows)
 constexpr int RPITCH = 144;           // staged row pitch in bytes
 constexpr int RWARP = 4;              // warps per CTA
 static_assert(RPITCH % 16 == 0, "cp.async destinations must be 16-byte aligned");
 static_assert(RPITCH >= 15 + 3 * (RB_X - 1) + 12, "a tap read (3 words from the pair's word) stays in its row");
-static_assert(RB_Y >= 17 && RB_X >= RT_W + 2, "the box holds an unscaled tile");
+static_assert(RB_Y >= RT_H + 1 && RB_X >= RT_W + 2, "the box holds an unscaled tile");
+static_assert(RT_H <= 32 && (RT_H & (RT_H - 1)) == 0, "lane r holds the coordinate of tile row r");
 
 struct RImg {          // per-image values of a warp's current image (warp-uniform)
   int32_t b, prefix, ntiles, tiles_x;
