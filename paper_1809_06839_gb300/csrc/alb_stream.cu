@@ -529,18 +529,26 @@ __global__ void __launch_bounds__(256, 3) k_pixmap3(Plan plan, ImgList in, ImgLi
         }
         st48(op + 48 * u, o);
       }
-      // units with a reflection point or a row end inside: lanes 0..15 take
-      // one pixel each of every such unit of the warp
-      uint32_t todo = __ballot_sync(0xffffffffu, valid && kind == 2);
-      while (todo) {
-        const int src = __ffs(todo) - 1;
-        todo &= todo - 1;
+      // units with a reflection point or a row end inside: their pixels,
+      // listed unit by unit, are spread over the lanes (one pixel per lane
+      // and round), so the warp waits one load latency for up to two units
+      const uint32_t todo = __ballot_sync(0xffffffffu, valid && kind == 2);
+      const int npx = 16 * __popc(todo);
+      for (int base = 0; base < npx; base += 32) {
+        const int idx = base + lane;
+        int src = 0;                       // lane holding the (idx / 16)-th such unit
+        if (idx < npx) {
+          uint32_t mm = todo;
+          for (int k = idx >> 4; k > 0; k--) mm &= mm - 1;   // clear the lower set bits
+          src = __ffs(mm) - 1;
+        }
         const int64_t su = __shfl_sync(0xffffffffu, u, src);
-        if (lane < 16) {
+        if (idx < npx) {
+          const int j = idx & 15;
           int32_t y, x;
-          flat_rc(16 * su + lane, OW, y, x);
+          flat_rc(16 * su + j, OW, y, x);
           const uint8_t* s = src_px(y, x);
-          uint8_t* d = op + 48 * su + 3 * lane;
+          uint8_t* d = op + 48 * su + 3 * j;
           d[0] = s[0]; d[1] = s[1]; d[2] = s[2];
         }
       }
