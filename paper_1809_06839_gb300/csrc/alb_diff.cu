@@ -9,10 +9,10 @@
 // scale, tx, ty) with the shift in fractions of W and H; photometric [B][3] =
 // (alpha, beta, gamma).
 //
-// Input adjoint of the warp: each output sample scatters g * weight to its four
-// taps with fire-and-forget atomic adds (red.global.add.f32); parameter
-// gradients: per-CTA block reductions written to a partials buffer and reduced
-// by one CTA per image in a fixed order (deterministic).
+// Input adjoint of the warp: a gather over the output samples whose taps touch
+// each source pixel (no atomics); parameter gradients: per-CTA block
+// reductions written to a partials buffer and reduced by one CTA per image in
+// a fixed order.  Both are deterministic.
 #include "alb_common.cuh"
 
 namespace alb {
@@ -45,29 +45,165 @@ ALB_D float tapf(const float* __restrict__ img, int H, int W, int x, int y) {
 }
 
 // ------------------------------------------------------------------ warp
-// one thread per output pixel (all channels); blocks of 256 over H*W, grid.y = B
-__global__ void __launch_bounds__(256) k_warp_f32_fwd(int B, int C, int H, int W, const float* __restrict__ x,
-                                                      const float* __restrict__ prm, float* __restrict__ y) {
-  const int b = blockIdx.y;
+// Both warp kernels work on 32x16 pixel tiles with 256 threads (two pixels a
+// thread, rows r and r+8) and stage the tile's counterpart in shared memory:
+// the forward stages the source box its outputs sample, the backward the
+// output box whose samples touch its source tile.  Work units are (tile,
+// group of up to three channels); a CTA owns every gridDim.x-th tile of one
+// image and copies unit u+1's box in with 4-byte cp.async (zero-filled
+// outside the image) while it computes unit u from the other buffer.  A box
+// that does not fit a buffer (extreme zoom) is read from global memory
+// instead; results are identical either way.
+constexpr int kWT_W = 32, kWT_H = 16, kWT_THREADS = 256;
+constexpr int kWT_CG = 3;                 // channels staged per unit
+constexpr int kWT_BUF = 6144;             // floats per staging buffer (two buffers: 48 KB)
+
+struct WarpBox {
+  int x0, y0, x1, y1;  // inclusive box corners (x1 < x0: empty)
+  int pitch;           // row pitch in floats of the staged copy
+  int staged;          // the box of `cn` channels fits one buffer
+};
+
+ALB_D void warp_box_finish(WarpBox& bx, int cn) {
+  const int w = bx.x1 - bx.x0 + 1, h = bx.y1 - bx.y0 + 1;
+  bx.pitch = w | 1;  // odd pitch: rotated access patterns spread over banks
+  bx.staged = (w > 0 && h > 0 && (int64_t)cn * h * bx.pitch <= kWT_BUF) ? 1 : 0;
+}
+
+ALB_D void cp_async4(float* dst, const float* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 4 : 0) : "memory");
+}
+ALB_D void cp_async_commit_f() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+ALB_D void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// issue the copies of channels [0, cn) of the box of a [C][H][W] plane stack
+// (src points at the group's first plane); zero outside the image, which is
+// the warp's zero border
+ALB_D void warp_stage_async(float* __restrict__ sm, const float* __restrict__ src, int cn, int H, int W,
+                            const WarpBox& bx) {
+  const int w = bx.x1 - bx.x0 + 1, h = bx.y1 - bx.y0 + 1;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int k = 0; k < cn; k++) {
+    const float* img = src + (int64_t)k * H * W;
+    float* dst = sm + k * h * bx.pitch;
+    for (int r = wid; r < h; r += kWT_THREADS / 32) {
+      const int y = bx.y0 + r;
+      const bool rin = y >= 0 && y < H;
+      const float* row = img + (int64_t)(rin ? y : 0) * W;
+      for (int c = lane; c < w; c += 32) {
+        const int xx = bx.x0 + c;
+        const bool in = rin && xx >= 0 && xx < W;
+        cp_async4(dst + r * bx.pitch + c, in ? row + xx : img, in);
+      }
+    }
+  }
+}
+
+// source box of an output tile: the tile's corners mapped by the inverse map,
+// one pixel of margin for the taps and for rounding (computed identically by
+// every thread)
+ALB_D WarpBox warp_fwd_box(const WarpF& g, int ox0, int oy0, int H, int W, int cn) {
+  const float xa = (float)ox0, xb = (float)min(ox0 + kWT_W, W) - 1.0f;
+  const float ya = (float)oy0, yb = (float)min(oy0 + kWT_H, H) - 1.0f;
+  float sxl = 3e38f, sxh = -3e38f, syl = 3e38f, syh = -3e38f;
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    const float ox = (k & 1) ? xb : xa, oy = (k & 2) ? yb : ya;
+    const float sx = __fmaf_rn(g.a00, ox, __fmaf_rn(g.a01, oy, g.b0));
+    const float sy = __fmaf_rn(g.a10, ox, __fmaf_rn(g.a11, oy, g.b1));
+    sxl = fminf(sxl, sx); sxh = fmaxf(sxh, sx); syl = fminf(syl, sy); syh = fmaxf(syh, sy);
+  }
+  WarpBox bx{0, 0, -1, -1, 1, 0};
+  if (fabsf(sxl) < 1e7f && fabsf(sxh) < 1e7f && fabsf(syl) < 1e7f && fabsf(syh) < 1e7f) {
+    bx.x0 = (int)floorf(sxl) - 1; bx.x1 = (int)floorf(sxh) + 2;
+    bx.y0 = (int)floorf(syl) - 1; bx.y1 = (int)floorf(syh) + 2;
+  }
+  warp_box_finish(bx, cn);
+  return bx;
+}
+
+// (tile origin, first channel) of unit u of this CTA
+ALB_D void warp_unit(int u, int groups, int tiles_x, int& X0, int& Y0, int& c0) {
+  const int t = blockIdx.x + (u / groups) * gridDim.x;
+  c0 = (u % groups) * kWT_CG;
+  X0 = (t % tiles_x) * kWT_W;
+  Y0 = (t / tiles_x) * kWT_H;
+}
+
+ALB_D int warp_units(int tiles, int groups) {
+  const int mine = tiles > (int)blockIdx.x ? (tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+  return mine * groups;
+}
+
+// forward: grid (CTAs per image, B); each CTA sets up its image's map once
+// and runs the unit pipeline
+__global__ void __launch_bounds__(kWT_THREADS) k_warp_f32_fwd(int B, int C, int H, int W, int tiles_x, int tiles,
+                                                              const float* __restrict__ x,
+                                                              const float* __restrict__ prm, float* __restrict__ y) {
+  extern __shared__ float sm[];
   __shared__ WarpF sg;
+  const int b = blockIdx.y;
   if (threadIdx.x == 0) sg = warp_setup(prm, b, H, W);
   __syncthreads();
   const WarpF g = sg;
   const int64_t plane = (int64_t)H * W;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < plane; i += (int64_t)gridDim.x * blockDim.x) {
-    const int oy = (int)(i / W), ox = (int)(i - (int64_t)oy * W);
-    const float sx = __fmaf_rn(g.a00, (float)ox, __fmaf_rn(g.a01, (float)oy, g.b0));
-    const float sy = __fmaf_rn(g.a10, (float)ox, __fmaf_rn(g.a11, (float)oy, g.b1));
-    const float fx0 = floorf(sx), fy0 = floorf(sy);
-    const float fx = sx - fx0, fy = sy - fy0;
-    const int ix = (int)fx0, iy = (int)fy0;
-    const float w00 = (1.0f - fx) * (1.0f - fy), w10 = fx * (1.0f - fy), w01 = (1.0f - fx) * fy, w11 = fx * fy;
-    for (int c = 0; c < C; c++) {
-      const float* img = x + ((int64_t)b * C + c) * plane;
-      const float v = w00 * tapf(img, H, W, ix, iy) + w10 * tapf(img, H, W, ix + 1, iy) +
-                      w01 * tapf(img, H, W, ix, iy + 1) + w11 * tapf(img, H, W, ix + 1, iy + 1);
-      y[((int64_t)b * C + c) * plane + i] = v;
+  const float* xb = x + (int64_t)b * C * plane;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int groups = (C + kWT_CG - 1) / kWT_CG;
+  const int units = warp_units(tiles, groups);
+  WarpBox nb{0, 0, -1, -1, 1, 0};
+  if (units > 0) {
+    int X0, Y0, c0;
+    warp_unit(0, groups, tiles_x, X0, Y0, c0);
+    nb = warp_fwd_box(g, X0, Y0, H, W, min(C - c0, kWT_CG));
+    if (nb.staged) warp_stage_async(sm, xb + c0 * plane, min(C - c0, kWT_CG), H, W, nb);
+  }
+  cp_async_commit_f();
+  for (int u = 0; u < units; u++) {
+    const WarpBox bx = nb;
+    int ox0, oy0, c0;
+    warp_unit(u, groups, tiles_x, ox0, oy0, c0);
+    const int cn = min(C - c0, kWT_CG);
+    if (u + 1 < units) {
+      int X1, Y1, c1;
+      warp_unit(u + 1, groups, tiles_x, X1, Y1, c1);
+      nb = warp_fwd_box(g, X1, Y1, H, W, min(C - c1, kWT_CG));
+      if (nb.staged) warp_stage_async(sm + ((u + 1) & 1) * kWT_BUF, xb + c1 * plane, min(C - c1, kWT_CG), H, W, nb);
     }
+    cp_async_commit_f();
+    cp_async_wait_prev();
+    __syncthreads();
+    const float* buf = sm + (u & 1) * kWT_BUF;
+    const float* src = xb + c0 * plane;
+    const int bw = bx.x1 - bx.x0 + 1, bh = bx.y1 - bx.y0 + 1;
+#pragma unroll
+    for (int j = 0; j < 2; j++) {
+      const int ox = ox0 + tx, oy = oy0 + ty + 8 * j;
+      if (ox >= W || oy >= H) continue;
+      const float sx = __fmaf_rn(g.a00, (float)ox, __fmaf_rn(g.a01, (float)oy, g.b0));
+      const float sy = __fmaf_rn(g.a10, (float)ox, __fmaf_rn(g.a11, (float)oy, g.b1));
+      const float fx0 = floorf(sx), fy0 = floorf(sy);
+      const float fx = sx - fx0, fy = sy - fy0;
+      const int ix = (int)fx0, iy = (int)fy0;
+      const float w00 = (1.0f - fx) * (1.0f - fy), w10 = fx * (1.0f - fy), w01 = (1.0f - fx) * fy, w11 = fx * fy;
+      const int lx = ix - bx.x0, ly = iy - bx.y0;
+      float* out = y + ((int64_t)b * C + c0) * plane + (int64_t)oy * W + ox;
+      if (bx.staged && (unsigned)lx < (unsigned)(bw - 1) && (unsigned)ly < (unsigned)(bh - 1)) {
+        const float* s0 = buf + ly * bx.pitch + lx;
+        for (int k = 0; k < cn; k++) {
+          const float* s = s0 + k * bh * bx.pitch;
+          out[k * plane] = w00 * s[0] + w10 * s[1] + w01 * s[bx.pitch] + w11 * s[bx.pitch + 1];
+        }
+      } else {
+        for (int k = 0; k < cn; k++) {
+          const float* img = src + k * plane;
+          out[k * plane] = w00 * tapf(img, H, W, ix, iy) + w10 * tapf(img, H, W, ix + 1, iy) +
+                           w01 * tapf(img, H, W, ix, iy + 1) + w11 * tapf(img, H, W, ix + 1, iy + 1);
+        }
+      }
+    }
+    __syncthreads();  // buffer (u & 1) is refilled by unit u + 2
   }
 }
 
@@ -84,55 +220,210 @@ ALB_D float block_sum(float v, float* sh) {
   return t;  // valid in thread 0
 }
 
-__global__ void __launch_bounds__(256) k_warp_f32_bwd(int B, int C, int H, int W, const float* __restrict__ x,
-                                                      const float* __restrict__ prm, const float* __restrict__ gy,
-                                                      float* __restrict__ gx, float* __restrict__ partials) {
-  const int b = blockIdx.y;
+struct WarpInv {
+  float m00, m01, m10, m11;  // forward map (inverse of the sampling map's linear part)
+};
+
+// output box of the source region [X0-1, X0+32] x [Y0-1, Y0+16] of a source
+// tile: its corners mapped by the forward map, two pixels of margin, clipped
+// to the image (computed identically by every thread)
+ALB_D WarpBox warp_bwd_box(const WarpF& g, const WarpInv& M, bool finite, int X0, int Y0, int H, int W, int cn) {
+  WarpBox bx{0, 0, -1, -1, 1, 0};
+  if (finite) {
+    float ol = 3e38f, oh = -3e38f, pl = 3e38f, ph = -3e38f;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const float sx = ((k & 1) ? (float)(X0 + kWT_W) : (float)(X0 - 1)) - g.b0;
+      const float sy = ((k & 2) ? (float)(Y0 + kWT_H) : (float)(Y0 - 1)) - g.b1;
+      const float ox = M.m00 * sx + M.m01 * sy, oy = M.m10 * sx + M.m11 * sy;
+      ol = fminf(ol, ox); oh = fmaxf(oh, ox); pl = fminf(pl, oy); ph = fmaxf(ph, oy);
+    }
+    ol = fmaxf(ol - 2.0f, 0.0f); oh = fminf(oh + 2.0f, (float)(W - 1));
+    pl = fmaxf(pl - 2.0f, 0.0f); ph = fminf(ph + 2.0f, (float)(H - 1));
+    if (ol <= oh && pl <= ph) {
+      bx.x0 = (int)floorf(ol); bx.x1 = (int)ceilf(oh);
+      bx.y0 = (int)floorf(pl); bx.y1 = (int)ceilf(ph);
+    }
+  }
+  warp_box_finish(bx, cn);
+  return bx;
+}
+
+// one slab constraint of the gather search: a*ox within [u - r, u + r]
+ALB_D void warp_slab(float a, float ra, float u, float r, float& lo, float& hi) {
+  if (fabsf(a) > 1e-30f) {
+    const float t0 = (u - r) * ra, t1 = (u + r) * ra;
+    lo = fmaxf(lo, fminf(t0, t1));
+    hi = fminf(hi, fmaxf(t0, t1));
+  } else if (fabsf(u) > r) {
+    hi = -1.0f;  // never satisfied
+    lo = 1.0f;
+  }
+}
+
+// Backward as a gather.  Source pixel p is a tap of output q exactly when
+// floor(sx_q) is px-1 or px and floor(sy_q) is py-1 or py, with (sx_q, sy_q)
+// the float32 coordinate the forward computes.  Each source pixel walks the
+// output rows of the parallelogram q = M (p + [-1,1]^2 - b) (M the forward map,
+// widened by a rounding margin), solves each row for its ox interval, and
+// re-tests every candidate with the forward's own arithmetic, so it sums
+// exactly the forward's (q, weight) pairs, in a fixed order (rows, then
+// columns): the input gradient is deterministic and needs no atomics.  The
+// same pairs carry the parameter gradient: pair (p, q) adds g_q x_p times the
+// weight's derivative to dL/dsx_q, dL/dsy_q, and those are folded against the
+// coordinate's derivatives through eight running sums per thread.
+__global__ void __launch_bounds__(kWT_THREADS) k_warp_f32_bwd(int B, int C, int H, int W, int tiles_x, int tiles,
+                                                              const float* __restrict__ x,
+                                                              const float* __restrict__ prm,
+                                                              const float* __restrict__ gy, float* __restrict__ gx,
+                                                              float* __restrict__ partials) {
+  extern __shared__ float sm[];
   __shared__ WarpF sg;
+  __shared__ float sM[6];  // forward map rows (m00, m01, m10, m11), search margins (source, output)
   __shared__ float red[32];
-  if (threadIdx.x == 0) sg = warp_setup(prm, b, H, W);
+  const int b = blockIdx.y;
+  const int64_t plane = (int64_t)H * W;
+  if (threadIdx.x == 0) {
+    const WarpF g = warp_setup(prm, b, H, W);
+    sg = g;
+    const double det = (double)g.a00 * g.a11 - (double)g.a01 * g.a10;
+    sM[0] = (float)(g.a11 / det); sM[1] = (float)(-g.a01 / det);
+    sM[2] = (float)(-g.a10 / det); sM[3] = (float)(g.a00 / det);
+    // source-space margin: a few float32 ulps of the largest coordinate
+    const float big = 2.0f * (float)(H > W ? H : W) + fabsf(g.b0) + fabsf(g.b1);
+    sM[4] = 1e-3f + 8.0f * big * 1.1920929e-7f;
+    sM[5] = 1e-3f + 1e-6f * (float)(H + W);
+  }
   __syncthreads();
   const WarpF g = sg;
-  const int64_t plane = (int64_t)H * W;
-  float dth = 0.f, dsc = 0.f, dtx = 0.f, dty = 0.f;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < plane; i += (int64_t)gridDim.x * blockDim.x) {
-    const int oy = (int)(i / W), ox = (int)(i - (int64_t)oy * W);
-    const float sx = __fmaf_rn(g.a00, (float)ox, __fmaf_rn(g.a01, (float)oy, g.b0));
-    const float sy = __fmaf_rn(g.a10, (float)ox, __fmaf_rn(g.a11, (float)oy, g.b1));
-    const float fx0 = floorf(sx), fy0 = floorf(sy);
-    const float fx = sx - fx0, fy = sy - fy0;
-    const int ix = (int)fx0, iy = (int)fy0;
-    const bool in00 = ix >= 0 && ix < W && iy >= 0 && iy < H;
-    const bool in10 = ix + 1 >= 0 && ix + 1 < W && iy >= 0 && iy < H;
-    const bool in01 = ix >= 0 && ix < W && iy + 1 >= 0 && iy + 1 < H;
-    const bool in11 = ix + 1 >= 0 && ix + 1 < W && iy + 1 >= 0 && iy + 1 < H;
-    float dsx = 0.f, dsy = 0.f;
-    for (int c = 0; c < C; c++) {
-      const int64_t base = ((int64_t)b * C + c) * plane;
-      const float gw = __ldg(gy + base + i);
-      if (gw == 0.0f) continue;
-      const float* img = x + base;
-      float* dimg = gx + base;
-      const float v00 = tapf(img, H, W, ix, iy), v10 = tapf(img, H, W, ix + 1, iy);
-      const float v01 = tapf(img, H, W, ix, iy + 1), v11 = tapf(img, H, W, ix + 1, iy + 1);
-      if (in00) atomicAdd(dimg + (int64_t)iy * W + ix, gw * (1.0f - fx) * (1.0f - fy));
-      if (in10) atomicAdd(dimg + (int64_t)iy * W + ix + 1, gw * fx * (1.0f - fy));
-      if (in01) atomicAdd(dimg + (int64_t)(iy + 1) * W + ix, gw * (1.0f - fx) * fy);
-      if (in11) atomicAdd(dimg + (int64_t)(iy + 1) * W + ix + 1, gw * fx * fy);
-      dsx += gw * ((1.0f - fy) * (v10 - v00) + fy * (v11 - v01));
-      dsy += gw * ((1.0f - fx) * (v01 - v00) + fx * (v11 - v10));
-    }
-    const float xp = (float)ox - g.cx - g.txp, yp = (float)oy - g.cy - g.typ;
-    dth += dsx * ((-g.sn * xp - g.cs * yp) / g.s) + dsy * ((g.cs * xp - g.sn * yp) / g.s);
-    dsc += dsx * (-(sx - g.cx) / g.s) + dsy * (-(sy - g.cy) / g.s);
-    dtx += dsx * (-g.cs * g.W / g.s) + dsy * (-g.sn * g.W / g.s);
-    dty += dsx * (g.sn * g.H / g.s) + dsy * (-g.cs * g.H / g.s);
+  const WarpInv M{sM[0], sM[1], sM[2], sM[3]};
+  const float dsrc = sM[4], dout = sM[5];
+  const bool finite = isfinite(M.m00) && isfinite(M.m01) && isfinite(M.m10) && isfinite(M.m11) && isfinite(g.b0) &&
+                      isfinite(g.b1);
+  const float ra00 = 1.0f / g.a00, ra10 = 1.0f / g.a10;
+  const float ry = (1.0f + dsrc) * (fabsf(M.m10) + fabsf(M.m11)) + dout;
+  const float oxc = g.cx + g.txp, oyc = g.cy + g.typ;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const float* gyb = gy + (int64_t)b * C * plane;
+  const int groups = (C + kWT_CG - 1) / kWT_CG;
+  const int units = warp_units(tiles, groups);
+  float S[8];
+#pragma unroll
+  for (int k = 0; k < 8; k++) S[k] = 0.0f;
+
+  WarpBox nb{0, 0, -1, -1, 1, 0};
+  if (units > 0) {
+    int X0, Y0, c0;
+    warp_unit(0, groups, tiles_x, X0, Y0, c0);
+    nb = warp_bwd_box(g, M, finite, X0, Y0, H, W, min(C - c0, kWT_CG));
+    if (nb.staged) warp_stage_async(sm, gyb + c0 * plane, min(C - c0, kWT_CG), H, W, nb);
   }
-  const float r0 = block_sum(dth, red), r1 = block_sum(dsc, red), r2 = block_sum(dtx, red), r3 = block_sum(dty, red);
+  cp_async_commit_f();
+  for (int u = 0; u < units; u++) {
+    const WarpBox bx = nb;
+    int X0, Y0, c0;
+    warp_unit(u, groups, tiles_x, X0, Y0, c0);
+    const int cn = min(C - c0, kWT_CG);
+    if (u + 1 < units) {
+      int X1, Y1, c1;
+      warp_unit(u + 1, groups, tiles_x, X1, Y1, c1);
+      nb = warp_bwd_box(g, M, finite, X1, Y1, H, W, min(C - c1, kWT_CG));
+      if (nb.staged) warp_stage_async(sm + ((u + 1) & 1) * kWT_BUF, gyb + c1 * plane, min(C - c1, kWT_CG), H, W, nb);
+    }
+    cp_async_commit_f();
+    // this unit's source values, loaded while its copies land
+    float xv[2][kWT_CG];
+#pragma unroll
+    for (int j = 0; j < 2; j++) {
+      const int px = X0 + tx, py = Y0 + ty + 8 * j;
+      const bool in = px < W && py < H;
+      const float* xs = x + ((int64_t)b * C + c0) * plane + (int64_t)(in ? py : 0) * W + (in ? px : 0);
+#pragma unroll
+      for (int k = 0; k < kWT_CG; k++) xv[j][k] = (in && k < cn) ? __ldg(xs + k * plane) : 0.0f;
+    }
+    cp_async_wait_prev();
+    __syncthreads();
+    const int bh = bx.y1 - bx.y0 + 1;
+    // staged copy (box-relative rows and columns) or the image itself
+    const float* gb = bx.staged ? sm + (u & 1) * kWT_BUF : gyb + c0 * plane;
+    const int gp = bx.staged ? bx.pitch : W;
+    const int64_t gpl = bx.staged ? (int64_t)bh * bx.pitch : plane;
+    const int oyb = bx.staged ? bx.y0 : 0, oxb = bx.staged ? bx.x0 : 0;
+#pragma unroll 1
+    for (int j = 0; j < 2; j++) {
+      const int px = X0 + tx, py = Y0 + ty + 8 * j;
+      if (px >= W || py >= H) continue;
+      float acc[kWT_CG];
+#pragma unroll
+      for (int k = 0; k < kWT_CG; k++) acc[k] = 0.0f;
+      if (!finite) {
+#pragma unroll
+        for (int k = 0; k < kWT_CG; k++) acc[k] = __int_as_float(0x7fc00000);
+      } else if (bx.x1 >= bx.x0) {
+        const float u0 = (float)px - g.b0, v0 = (float)py - g.b1;
+        const float oc = M.m10 * u0 + M.m11 * v0;
+        const int ylo = max(bx.y0, (int)ceilf(fmaxf(oc - ry, -1.0f)));
+        const int yhi = min(bx.y1, (int)floorf(fminf(oc + ry, (float)H)));
+        const float rs = 1.0f + dsrc;
+        for (int oy = ylo; oy <= yhi; oy++) {
+          const float txr = __fmaf_rn(g.a01, (float)oy, g.b0), tyr = __fmaf_rn(g.a11, (float)oy, g.b1);
+          float lo = -1.0f, hi = (float)W;
+          warp_slab(g.a00, ra00, (float)px - txr, rs, lo, hi);
+          warp_slab(g.a10, ra10, (float)py - tyr, rs, lo, hi);
+          const int xlo = max(bx.x0, (int)ceilf(fmaxf(lo - dout, -1.0f)));
+          const int xhi = min(bx.x1, (int)floorf(fminf(hi + dout, (float)W)));
+          const float* grow = gb + (int64_t)(oy - oyb) * gp;
+          for (int ox = xlo; ox <= xhi; ox++) {
+            const float sx = __fmaf_rn(g.a00, (float)ox, txr);
+            const float sy = __fmaf_rn(g.a10, (float)ox, tyr);
+            const float fx0 = floorf(sx), fy0 = floorf(sy);
+            const int dx = px - (int)fx0, dy = py - (int)fy0;
+            if ((unsigned)dx > 1u || (unsigned)dy > 1u) continue;
+            const float fx = sx - fx0, fy = sy - fy0;
+            const float wx = dx ? fx : 1.0f - fx, wy = dy ? fy : 1.0f - fy;
+            const float w = wx * wy;
+            float a = 0.0f;
+#pragma unroll
+            for (int k = 0; k < kWT_CG; k++) {
+              if (k < cn) {
+                const float gv = grow[k * gpl + (ox - oxb)];
+                acc[k] = __fmaf_rn(gv, w, acc[k]);
+                a = __fmaf_rn(gv, xv[j][k], a);
+              }
+            }
+            const float dsx = dx ? a * wy : -a * wy;
+            const float dsy = dy ? a * wx : -a * wx;
+            const float xp = (float)ox - oxc, yp = (float)oy - oyc;
+            S[0] = __fmaf_rn(dsx, xp, S[0]);
+            S[1] = __fmaf_rn(dsx, yp, S[1]);
+            S[2] = __fmaf_rn(dsy, xp, S[2]);
+            S[3] = __fmaf_rn(dsy, yp, S[3]);
+            S[4] = __fmaf_rn(dsx, sx - g.cx, S[4]);
+            S[5] = __fmaf_rn(dsy, sy - g.cy, S[5]);
+            S[6] += dsx;
+            S[7] += dsy;
+          }
+        }
+      }
+      float* out = gx + ((int64_t)b * C + c0) * plane + (int64_t)py * W + px;
+#pragma unroll
+      for (int k = 0; k < kWT_CG; k++)
+        if (k < cn) out[k * plane] = acc[k];
+    }
+    __syncthreads();  // buffer (u & 1) is refilled by unit u + 2
+  }
+  float R[8];
+#pragma unroll
+  for (int k = 0; k < 8; k++) R[k] = block_sum(S[k], red);
   if (threadIdx.x == 0) {
     float* pp = partials + ((int64_t)b * gridDim.x + blockIdx.x) * 4;
-    pp[0] = r0 * (float)(3.14159265358979323846 / 180.0);
-    pp[1] = r1; pp[2] = r2; pp[3] = r3;
+    const float is = 1.0f / g.s;
+    const float dth = (-g.sn * R[0] - g.cs * R[1] + g.cs * R[2] - g.sn * R[3]) * is;
+    const float nan = __int_as_float(0x7fc00000);
+    pp[0] = finite ? dth * (float)(3.14159265358979323846 / 180.0) : nan;
+    pp[1] = finite ? -(R[4] + R[5]) * is : nan;
+    pp[2] = finite ? -(g.cs * R[6] + g.sn * R[7]) * g.W * is : nan;
+    pp[3] = finite ? (g.sn * R[6] - g.cs * R[7]) * g.H * is : nan;
   }
 }
 
@@ -150,6 +441,38 @@ __global__ void k_reduce_partials(int nblk, int k, const float* __restrict__ par
 }
 
 // ------------------------------------------------------------------ photometric
+// Elementwise over [C][H][W] per image, four values a thread a step (one
+// 16-byte access when the image's element count is a multiple of four, which
+// keeps every image's base 16-byte aligned), two steps in flight.
+ALB_D float photo_fwd1(float al, float be, float ga, float v) {
+  const float z = __fmaf_rn(al, v, be);
+  const float zc = fminf(fmaxf(z, 0.0f), 1.0f);
+  return zc > 0.0f ? powf(zc, ga) : 0.0f;
+}
+
+template <bool VEC>
+ALB_D void ld4(const float* p, int64_t i, int64_t n, float (&v)[4]) {
+  if (VEC) {
+    const float4 t = __ldg(reinterpret_cast<const float4*>(p + i));
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; k++) v[k] = i + k < n ? __ldg(p + i + k) : 0.0f;
+  }
+}
+
+template <bool VEC>
+ALB_D void st4(float* p, int64_t i, int64_t n, const float (&v)[4]) {
+  if (VEC) {
+    *reinterpret_cast<float4*>(p + i) = make_float4(v[0], v[1], v[2], v[3]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+      if (i + k < n) p[i + k] = v[k];
+  }
+}
+
+template <bool VEC>
 __global__ void __launch_bounds__(256) k_photo_f32_fwd(int B, int C, int H, int W, const float* __restrict__ x,
                                                        const float* __restrict__ prm, float* __restrict__ y) {
   const int b = blockIdx.y;
@@ -157,13 +480,37 @@ __global__ void __launch_bounds__(256) k_photo_f32_fwd(int B, int C, int H, int 
   const int64_t n = (int64_t)C * H * W;
   const float* xb = x + (int64_t)b * n;
   float* yb = y + (int64_t)b * n;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const float z = __fmaf_rn(al, __ldg(xb + i), be);
-    const float zc = fminf(fmaxf(z, 0.0f), 1.0f);
-    yb[i] = zc > 0.0f ? powf(zc, ga) : 0.0f;
+  const int64_t step = (int64_t)gridDim.x * blockDim.x * 4;
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; i < n; i += 2 * step) {
+    const int64_t i2 = i + step;
+    float v[4], w[4];
+    ld4<VEC>(xb, i, n, v);
+    if (i2 < n) ld4<VEC>(xb, i2, n, w);
+#pragma unroll
+    for (int k = 0; k < 4; k++) v[k] = photo_fwd1(al, be, ga, v[k]);
+    st4<VEC>(yb, i, n, v);
+    if (i2 < n) {
+#pragma unroll
+      for (int k = 0; k < 4; k++) w[k] = photo_fwd1(al, be, ga, w[k]);
+      st4<VEC>(yb, i2, n, w);
+    }
   }
 }
 
+// input gradient of one value; accumulates the parameter gradients
+ALB_D float photo_bwd1(float al, float be, float ga, float xv, float g, float& da, float& db, float& dg) {
+  const float z = __fmaf_rn(al, xv, be);
+  if (!(z > 0.0f && z < 1.0f)) return 0.0f;
+  const float lz = logf(z);
+  const float zg = expf(ga * lz);                    // z^gamma
+  const float gz = g * ga * expf((ga - 1.0f) * lz);  // g * gamma * z^(gamma-1)
+  dg += g * zg * lz;
+  da += gz * xv;
+  db += gz;
+  return gz * al;
+}
+
+template <bool VEC>
 __global__ void __launch_bounds__(256) k_photo_f32_bwd(int B, int C, int H, int W, const float* __restrict__ x,
                                                        const float* __restrict__ prm, const float* __restrict__ gy,
                                                        float* __restrict__ gx, float* __restrict__ partials) {
@@ -175,20 +522,24 @@ __global__ void __launch_bounds__(256) k_photo_f32_bwd(int B, int C, int H, int 
   const float* gb = gy + (int64_t)b * n;
   float* dxb = gx + (int64_t)b * n;
   float da = 0.f, db = 0.f, dg = 0.f;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const float xv = __ldg(xb + i), g = __ldg(gb + i);
-    const float z = __fmaf_rn(al, xv, be);
-    float gxv = 0.0f;
-    if (z > 0.0f && z < 1.0f) {
-      const float lz = logf(z);
-      const float zg = expf(ga * lz);                 // z^gamma
-      const float gz = g * ga * expf((ga - 1.0f) * lz);  // g * gamma * z^(gamma-1)
-      dg += g * zg * lz;
-      da += gz * xv;
-      db += gz;
-      gxv = gz * al;
+  const int64_t step = (int64_t)gridDim.x * blockDim.x * 4;
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; i < n; i += 2 * step) {
+    const int64_t i2 = i + step;
+    float xv[4], gv[4], xw[4], gw[4];
+    ld4<VEC>(xb, i, n, xv);
+    ld4<VEC>(gb, i, n, gv);
+    if (i2 < n) {
+      ld4<VEC>(xb, i2, n, xw);
+      ld4<VEC>(gb, i2, n, gw);
     }
-    dxb[i] = gxv;
+#pragma unroll
+    for (int k = 0; k < 4; k++) xv[k] = i + k < n ? photo_bwd1(al, be, ga, xv[k], gv[k], da, db, dg) : 0.0f;
+    st4<VEC>(dxb, i, n, xv);
+    if (i2 < n) {
+#pragma unroll
+      for (int k = 0; k < 4; k++) xw[k] = i2 + k < n ? photo_bwd1(al, be, ga, xw[k], gw[k], da, db, dg) : 0.0f;
+      st4<VEC>(dxb, i2, n, xw);
+    }
   }
   const float r0 = block_sum(da, red), r1 = block_sum(db, red), r2 = block_sum(dg, red);
   if (threadIdx.x == 0) {
@@ -197,10 +548,42 @@ __global__ void __launch_bounds__(256) k_photo_f32_bwd(int B, int C, int H, int 
   }
 }
 
-static int blocks_per_image(int64_t elems, int B) {
-  const int64_t want = (int64_t)sm_count() * 8;
-  int64_t per = (want + B - 1) / B;
-  const int64_t cap = (elems + 255) / 256;
+// the warp kernels' two staging buffers plus their static shared variables
+// exceed the default 48 KB: opt in once per device
+static alb_status warp_smem_optin() {
+  static bool done[64] = {false};
+  int dev = 0;
+  ALB_CUDA(cudaGetDevice(&dev));
+  if (dev >= 0 && dev < 64 && done[dev]) return ALB_OK;
+  const int bytes = 2 * kWT_BUF * (int)sizeof(float);
+  ALB_CUDA(cudaFuncSetAttribute((const void*)k_warp_f32_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  ALB_CUDA(cudaFuncSetAttribute((const void*)k_warp_f32_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  if (dev >= 0 && dev < 64) done[dev] = true;
+  return ALB_OK;
+}
+
+// CTAs per image of the tiled warp kernels: about eight waves of resident
+// CTAs over the whole batch (the per-image map is set up once per CTA, which
+// then loops over tiles), at most one per tile and at most 1024
+static int warp_ctas_per_image(const void* kernel, int tiles, int B) {
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kWT_THREADS, 2 * kWT_BUF * sizeof(float)) !=
+          cudaSuccess || occ < 1)
+    occ = 1;
+  const int64_t want = ((int64_t)sm_count() * occ * 8 + B - 1) / B;
+  int64_t n = want < tiles ? want : tiles;
+  if (n > 1024) n = 1024;
+  return n < 1 ? 1 : (int)n;
+}
+
+// CTAs per image of the elementwise kernels: four full waves of resident
+// 256-thread CTAs over the batch, rounded down so that no nearly-empty last
+// wave doubles the time; at most one CTA per 256 units and at most 1024
+static int blocks_per_image(const void* kernel, int64_t units, int B) {
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, 256, 0) != cudaSuccess || occ < 1) occ = 1;
+  int64_t per = (int64_t)sm_count() * occ * 4 / B;
+  const int64_t cap = (units + 255) / 256;
   if (per > cap) per = cap;
   if (per < 1) per = 1;
   if (per > 1024) per = 1024;
@@ -225,8 +608,15 @@ extern "C" alb_status alb_warp_affine_f32_fwd(int32_t B, int32_t C, int32_t H, i
                                               const float* prm, float* y, void* stream) {
   alb_status rc = check_f32(B, C, H, W, x, prm, y);
   if (rc != ALB_OK || B == 0) return rc;
-  dim3 grid(blocks_per_image((int64_t)H * W, B), B);
-  k_warp_f32_fwd<<<grid, 256, 0, (cudaStream_t)stream>>>(B, C, H, W, x, prm, y);
+  ALB_REQUIRE(B <= 65535, ALB_ESHAPE, "alb_warp_affine_f32_fwd: batch %d above 65535", B);
+  const int tiles_x = (W + kWT_W - 1) / kWT_W, tiles_y = (H + kWT_H - 1) / kWT_H;
+  ALB_REQUIRE((int64_t)tiles_x * tiles_y < (1LL << 31), ALB_ESHAPE, "alb_warp_affine_f32_fwd: image too large");
+  const int tiles = tiles_x * tiles_y;
+  rc = warp_smem_optin();
+  if (rc != ALB_OK) return rc;
+  const int nblk = warp_ctas_per_image((const void*)k_warp_f32_fwd, tiles, B);
+  k_warp_f32_fwd<<<dim3(nblk, B), kWT_THREADS, 2 * kWT_BUF * sizeof(float), (cudaStream_t)stream>>>(
+      B, C, H, W, tiles_x, tiles, x, prm, y);
   ALB_CUDA(cudaGetLastError());
   return ALB_OK;
 }
@@ -237,12 +627,18 @@ extern "C" alb_status alb_warp_affine_f32_bwd(int32_t B, int32_t C, int32_t H, i
   alb_status rc = check_f32(B, C, H, W, x, prm, gy);
   if (rc != ALB_OK || B == 0) return rc;
   ALB_REQUIRE(gx && gprm, ALB_EINVAL, "alb_warp_affine_f32_bwd: null output");
-  const int nblk = blocks_per_image((int64_t)H * W, B);
+  ALB_REQUIRE(B <= 65535, ALB_ESHAPE, "alb_warp_affine_f32_bwd: batch %d above 65535", B);
+  const int tiles_x = (W + kWT_W - 1) / kWT_W, tiles_y = (H + kWT_H - 1) / kWT_H;
+  ALB_REQUIRE((int64_t)tiles_x * tiles_y < (1LL << 31), ALB_ESHAPE, "alb_warp_affine_f32_bwd: image too large");
+  const int tiles = tiles_x * tiles_y;
+  rc = warp_smem_optin();
+  if (rc != ALB_OK) return rc;
+  const int nblk = warp_ctas_per_image((const void*)k_warp_f32_bwd, tiles, B);
   ALB_REQUIRE(workspace && workspace_bytes >= (size_t)B * nblk * 4 * sizeof(float), ALB_EWORKSPACE,
               "alb_warp_affine_f32_bwd: workspace too small");
   cudaStream_t st = (cudaStream_t)stream;
-  ALB_CUDA(cudaMemsetAsync(gx, 0, (size_t)B * C * H * W * sizeof(float), st));
-  k_warp_f32_bwd<<<dim3(nblk, B), 256, 0, st>>>(B, C, H, W, x, prm, gy, gx, (float*)workspace);
+  k_warp_f32_bwd<<<dim3(nblk, B), kWT_THREADS, 2 * kWT_BUF * sizeof(float), st>>>(
+      B, C, H, W, tiles_x, tiles, x, prm, gy, gx, (float*)workspace);
   ALB_CUDA(cudaGetLastError());
   k_reduce_partials<<<B, 256, 0, st>>>(nblk, 4, (const float*)workspace, gprm);
   ALB_CUDA(cudaGetLastError());
@@ -253,8 +649,15 @@ extern "C" alb_status alb_photometric_f32_fwd(int32_t B, int32_t C, int32_t H, i
                                               const float* prm, float* y, void* stream) {
   alb_status rc = check_f32(B, C, H, W, x, prm, y);
   if (rc != ALB_OK || B == 0) return rc;
-  dim3 grid(blocks_per_image((int64_t)C * H * W, B), B);
-  k_photo_f32_fwd<<<grid, 256, 0, (cudaStream_t)stream>>>(B, C, H, W, x, prm, y);
+  ALB_REQUIRE(B <= 65535, ALB_ESHAPE, "alb_photometric_f32_fwd: batch %d above 65535", B);
+  const int64_t n = (int64_t)C * H * W;
+  const bool vec = n % 4 == 0 && ((uintptr_t)x % 16) == 0 && ((uintptr_t)y % 16) == 0;
+  const void* kern = vec ? (const void*)k_photo_f32_fwd<true> : (const void*)k_photo_f32_fwd<false>;
+  dim3 grid(blocks_per_image(kern, (n + 3) / 4, B), B);
+  if (vec)
+    k_photo_f32_fwd<true><<<grid, 256, 0, (cudaStream_t)stream>>>(B, C, H, W, x, prm, y);
+  else
+    k_photo_f32_fwd<false><<<grid, 256, 0, (cudaStream_t)stream>>>(B, C, H, W, x, prm, y);
   ALB_CUDA(cudaGetLastError());
   return ALB_OK;
 }
@@ -265,11 +668,18 @@ extern "C" alb_status alb_photometric_f32_bwd(int32_t B, int32_t C, int32_t H, i
   alb_status rc = check_f32(B, C, H, W, x, prm, gy);
   if (rc != ALB_OK || B == 0) return rc;
   ALB_REQUIRE(gx && gprm, ALB_EINVAL, "alb_photometric_f32_bwd: null output");
-  const int nblk = blocks_per_image((int64_t)C * H * W, B);
+  ALB_REQUIRE(B <= 65535, ALB_ESHAPE, "alb_photometric_f32_bwd: batch %d above 65535", B);
+  const int64_t n = (int64_t)C * H * W;
+  const bool vec = n % 4 == 0 && ((uintptr_t)x % 16) == 0 && ((uintptr_t)gy % 16) == 0 && ((uintptr_t)gx % 16) == 0;
+  const void* kern = vec ? (const void*)k_photo_f32_bwd<true> : (const void*)k_photo_f32_bwd<false>;
+  const int nblk = blocks_per_image(kern, (n + 3) / 4, B);
   ALB_REQUIRE(workspace && workspace_bytes >= (size_t)B * nblk * 3 * sizeof(float), ALB_EWORKSPACE,
               "alb_photometric_f32_bwd: workspace too small");
   cudaStream_t st = (cudaStream_t)stream;
-  k_photo_f32_bwd<<<dim3(nblk, B), 256, 0, st>>>(B, C, H, W, x, prm, gy, gx, (float*)workspace);
+  if (vec)
+    k_photo_f32_bwd<true><<<dim3(nblk, B), 256, 0, st>>>(B, C, H, W, x, prm, gy, gx, (float*)workspace);
+  else
+    k_photo_f32_bwd<false><<<dim3(nblk, B), 256, 0, st>>>(B, C, H, W, x, prm, gy, gx, (float*)workspace);
   ALB_CUDA(cudaGetLastError());
   k_reduce_partials<<<B, 256, 0, st>>>(nblk, 3, (const float*)workspace, gprm);
   ALB_CUDA(cudaGetLastError());
