@@ -50,10 +50,12 @@ ALB_D float tapf(const float* __restrict__ img, int H, int W, int x, int y) {
 // the forward stages the source box its outputs sample, the backward the
 // output box whose samples touch its source tile.  Work units are (tile,
 // group of up to three channels); a CTA owns every gridDim.x-th tile of one
-// image and copies unit u+1's box in with 4-byte cp.async (zero-filled
-// outside the image) while it computes unit u from the other buffer.  A box
-// that does not fit a buffer (extreme zoom) is read from global memory
-// instead; results are identical either way.
+// image and copies unit u+1's box in with cp.async (zero-filled outside the
+// image) while it computes unit u from the other buffer.  With W a multiple
+// of four (AL) boxes are widened to 16-byte columns and copied 16 bytes at a
+// time; otherwise 4 bytes at a time.  A box that does not fit a buffer
+// (extreme zoom) is read from global memory instead; results are identical
+// either way.
 constexpr int kWT_W = 32, kWT_H = 16, kWT_THREADS = 256;
 constexpr int kWT_CG = 3;                 // channels staged per unit
 constexpr int kWT_BUF = 6144;             // floats per staging buffer (two buffers: 48 KB)
@@ -64,9 +66,16 @@ struct WarpBox {
   int staged;          // the box of `cn` channels fits one buffer
 };
 
+// pitch and fit of a box; AL widens it to 16-byte columns (x0 down, x1 up to
+// multiples of four) with a pitch of an odd number of 16-byte columns
+template <bool AL>
 ALB_D void warp_box_finish(WarpBox& bx, int cn) {
+  if (AL && bx.x1 >= bx.x0) {
+    bx.x0 &= ~3;
+    bx.x1 = bx.x0 + (((bx.x1 - bx.x0 + 1) + 3) & ~3) - 1;
+  }
   const int w = bx.x1 - bx.x0 + 1, h = bx.y1 - bx.y0 + 1;
-  bx.pitch = w | 1;  // odd pitch: rotated access patterns spread over banks
+  bx.pitch = AL ? (((w >> 2) | 1) << 2) : (w | 1);  // rotated access patterns spread over banks
   bx.staged = (w > 0 && h > 0 && (int64_t)cn * h * bx.pitch <= kWT_BUF) ? 1 : 0;
 }
 
@@ -74,28 +83,39 @@ ALB_D void cp_async4(float* dst, const float* src, bool valid) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 4 : 0) : "memory");
 }
+ALB_D void cp_async16z(float* dst, const float* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 16 : 0) : "memory");
+}
 ALB_D void cp_async_commit_f() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 ALB_D void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 // issue the copies of channels [0, cn) of the box of a [C][H][W] plane stack
 // (src points at the group's first plane); zero outside the image, which is
-// the warp's zero border
+// the warp's zero border.  Copy items (row, column) are spread over all
+// threads; the row is recovered with a float reciprocal, exact for the item
+// counts of a buffer.
+template <bool AL>
 ALB_D void warp_stage_async(float* __restrict__ sm, const float* __restrict__ src, int cn, int H, int W,
                             const WarpBox& bx) {
-  const int w = bx.x1 - bx.x0 + 1, h = bx.y1 - bx.y0 + 1;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int h = bx.y1 - bx.y0 + 1;
+  const int ncol = AL ? (bx.x1 - bx.x0 + 1) >> 2 : bx.x1 - bx.x0 + 1;  // copy items per row
+  const int items = h * ncol;
+  const float rinv = 1.0f / (float)ncol;
   for (int k = 0; k < cn; k++) {
     const float* img = src + (int64_t)k * H * W;
     float* dst = sm + k * h * bx.pitch;
-    for (int r = wid; r < h; r += kWT_THREADS / 32) {
+    for (int t = threadIdx.x; t < items; t += kWT_THREADS) {
+      const int r = (int)__fmul_rn(__fadd_rn((float)t, 0.5f), rinv);
+      const int c = t - r * ncol;
       const int y = bx.y0 + r;
-      const bool rin = y >= 0 && y < H;
-      const float* row = img + (int64_t)(rin ? y : 0) * W;
-      for (int c = lane; c < w; c += 32) {
-        const int xx = bx.x0 + c;
-        const bool in = rin && xx >= 0 && xx < W;
-        cp_async4(dst + r * bx.pitch + c, in ? row + xx : img, in);
-      }
+      const int xx = bx.x0 + (AL ? 4 * c : c);
+      const bool in = y >= 0 && y < H && xx >= 0 && xx < W;  // AL: a 16-byte column is wholly in or out
+      const float* gp = in ? img + (int64_t)y * W + xx : img;
+      if (AL)
+        cp_async16z(dst + r * bx.pitch + 4 * c, gp, in);
+      else
+        cp_async4(dst + r * bx.pitch + c, gp, in);
     }
   }
 }
@@ -103,6 +123,7 @@ ALB_D void warp_stage_async(float* __restrict__ sm, const float* __restrict__ sr
 // source box of an output tile: the tile's corners mapped by the inverse map,
 // one pixel of margin for the taps and for rounding (computed identically by
 // every thread)
+template <bool AL>
 ALB_D WarpBox warp_fwd_box(const WarpF& g, int ox0, int oy0, int H, int W, int cn) {
   const float xa = (float)ox0, xb = (float)min(ox0 + kWT_W, W) - 1.0f;
   const float ya = (float)oy0, yb = (float)min(oy0 + kWT_H, H) - 1.0f;
@@ -119,7 +140,7 @@ ALB_D WarpBox warp_fwd_box(const WarpF& g, int ox0, int oy0, int H, int W, int c
     bx.x0 = (int)floorf(sxl) - 1; bx.x1 = (int)floorf(sxh) + 2;
     bx.y0 = (int)floorf(syl) - 1; bx.y1 = (int)floorf(syh) + 2;
   }
-  warp_box_finish(bx, cn);
+  warp_box_finish<AL>(bx, cn);
   return bx;
 }
 
@@ -138,17 +159,20 @@ ALB_D int warp_units(int tiles, int groups) {
 
 // forward: grid (CTAs per image, B); each CTA sets up its image's map once
 // and runs the unit pipeline
+template <bool AL>
 __global__ void __launch_bounds__(kWT_THREADS) k_warp_f32_fwd(int B, int C, int H, int W, int tiles_x, int tiles,
                                                               const float* __restrict__ x,
                                                               const float* __restrict__ prm, float* __restrict__ y) {
-  extern __shared__ float sm[];
+  extern __shared__ __align__(16) float sm[];
   __shared__ WarpF sg;
   const int b = blockIdx.y;
   if (threadIdx.x == 0) sg = warp_setup(prm, b, H, W);
   __syncthreads();
+  const float a00 = sg.a00, a01 = sg.a01, a10 = sg.a10, a11 = sg.a11, b0 = sg.b0, b1 = sg.b1;
   const WarpF g = sg;
-  const int64_t plane = (int64_t)H * W;
+  const int plane = H * W;
   const float* xb = x + (int64_t)b * C * plane;
+  float* yb = y + (int64_t)b * C * plane;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int groups = (C + kWT_CG - 1) / kWT_CG;
   const int units = warp_units(tiles, groups);
@@ -156,8 +180,8 @@ __global__ void __launch_bounds__(kWT_THREADS) k_warp_f32_fwd(int B, int C, int 
   if (units > 0) {
     int X0, Y0, c0;
     warp_unit(0, groups, tiles_x, X0, Y0, c0);
-    nb = warp_fwd_box(g, X0, Y0, H, W, min(C - c0, kWT_CG));
-    if (nb.staged) warp_stage_async(sm, xb + c0 * plane, min(C - c0, kWT_CG), H, W, nb);
+    nb = warp_fwd_box<AL>(g, X0, Y0, H, W, min(C - c0, kWT_CG));
+    if (nb.staged) warp_stage_async<AL>(sm, xb + (int64_t)c0 * plane, min(C - c0, kWT_CG), H, W, nb);
   }
   cp_async_commit_f();
   for (int u = 0; u < units; u++) {
@@ -168,38 +192,43 @@ __global__ void __launch_bounds__(kWT_THREADS) k_warp_f32_fwd(int B, int C, int 
     if (u + 1 < units) {
       int X1, Y1, c1;
       warp_unit(u + 1, groups, tiles_x, X1, Y1, c1);
-      nb = warp_fwd_box(g, X1, Y1, H, W, min(C - c1, kWT_CG));
-      if (nb.staged) warp_stage_async(sm + ((u + 1) & 1) * kWT_BUF, xb + c1 * plane, min(C - c1, kWT_CG), H, W, nb);
+      nb = warp_fwd_box<AL>(g, X1, Y1, H, W, min(C - c1, kWT_CG));
+      if (nb.staged)
+        warp_stage_async<AL>(sm + ((u + 1) & 1) * kWT_BUF, xb + (int64_t)c1 * plane, min(C - c1, kWT_CG), H, W, nb);
     }
     cp_async_commit_f();
     cp_async_wait_prev();
     __syncthreads();
     const float* buf = sm + (u & 1) * kWT_BUF;
-    const float* src = xb + c0 * plane;
-    const int bw = bx.x1 - bx.x0 + 1, bh = bx.y1 - bx.y0 + 1;
+    const float* src = xb + (int64_t)c0 * plane;
+    float* dstp = yb + (int64_t)c0 * plane;
+    const int bw = bx.x1 - bx.x0 + 1, bh = bx.y1 - bx.y0 + 1, bp = bx.pitch, bpl = bh * bx.pitch;
 #pragma unroll
     for (int j = 0; j < 2; j++) {
       const int ox = ox0 + tx, oy = oy0 + ty + 8 * j;
       if (ox >= W || oy >= H) continue;
-      const float sx = __fmaf_rn(g.a00, (float)ox, __fmaf_rn(g.a01, (float)oy, g.b0));
-      const float sy = __fmaf_rn(g.a10, (float)ox, __fmaf_rn(g.a11, (float)oy, g.b1));
+      const float sx = __fmaf_rn(a00, (float)ox, __fmaf_rn(a01, (float)oy, b0));
+      const float sy = __fmaf_rn(a10, (float)ox, __fmaf_rn(a11, (float)oy, b1));
       const float fx0 = floorf(sx), fy0 = floorf(sy);
       const float fx = sx - fx0, fy = sy - fy0;
       const int ix = (int)fx0, iy = (int)fy0;
       const float w00 = (1.0f - fx) * (1.0f - fy), w10 = fx * (1.0f - fy), w01 = (1.0f - fx) * fy, w11 = fx * fy;
       const int lx = ix - bx.x0, ly = iy - bx.y0;
-      float* out = y + ((int64_t)b * C + c0) * plane + (int64_t)oy * W + ox;
+      const int o = oy * W + ox;
       if (bx.staged && (unsigned)lx < (unsigned)(bw - 1) && (unsigned)ly < (unsigned)(bh - 1)) {
-        const float* s0 = buf + ly * bx.pitch + lx;
-        for (int k = 0; k < cn; k++) {
-          const float* s = s0 + k * bh * bx.pitch;
-          out[k * plane] = w00 * s[0] + w10 * s[1] + w01 * s[bx.pitch] + w11 * s[bx.pitch + 1];
+        const int s0 = ly * bp + lx;
+#pragma unroll
+        for (int k = 0; k < kWT_CG; k++) {
+          if (k < cn) {
+            const float* s = buf + k * bpl + s0;
+            dstp[k * plane + o] = w00 * s[0] + w10 * s[1] + w01 * s[bp] + w11 * s[bp + 1];
+          }
         }
       } else {
         for (int k = 0; k < cn; k++) {
-          const float* img = src + k * plane;
-          out[k * plane] = w00 * tapf(img, H, W, ix, iy) + w10 * tapf(img, H, W, ix + 1, iy) +
-                           w01 * tapf(img, H, W, ix, iy + 1) + w11 * tapf(img, H, W, ix + 1, iy + 1);
+          const float* img = src + (int64_t)k * plane;
+          dstp[k * plane + o] = w00 * tapf(img, H, W, ix, iy) + w10 * tapf(img, H, W, ix + 1, iy) +
+                                w01 * tapf(img, H, W, ix, iy + 1) + w11 * tapf(img, H, W, ix + 1, iy + 1);
         }
       }
     }
@@ -227,6 +256,7 @@ struct WarpInv {
 // output box of the source region [X0-1, X0+32] x [Y0-1, Y0+16] of a source
 // tile: its corners mapped by the forward map, two pixels of margin, clipped
 // to the image (computed identically by every thread)
+template <bool AL>
 ALB_D WarpBox warp_bwd_box(const WarpF& g, const WarpInv& M, bool finite, int X0, int Y0, int H, int W, int cn) {
   WarpBox bx{0, 0, -1, -1, 1, 0};
   if (finite) {
@@ -245,7 +275,7 @@ ALB_D WarpBox warp_bwd_box(const WarpF& g, const WarpInv& M, bool finite, int X0
       bx.y0 = (int)floorf(pl); bx.y1 = (int)ceilf(ph);
     }
   }
-  warp_box_finish(bx, cn);
+  warp_box_finish<AL>(bx, cn);
   return bx;
 }
 
@@ -261,6 +291,68 @@ ALB_D void warp_slab(float a, float ra, float u, float r, float& lo, float& hi) 
   }
 }
 
+// per-image constants of the gather search
+struct GatherK {
+  float a00, a01, a10, a11, b0, b1, ra00, ra10;
+  float m10, m11, ry, rs, dout, oxc, oyc, cx, cy;
+};
+
+// Gather of one source pixel p = (px, py) over the output rows [ylo, yhi] of
+// the search box: accumulates the input gradient of the cn channels in acc and
+// the eight parameter sums in S.  G: the gradient rows (staged box: `gp` row
+// pitch, `gpl` channel pitch, rows and columns relative to (oxb, oyb); or the
+// image itself).
+template <typename GPtr>
+ALB_D void warp_gather_pixel(const GatherK& K, const WarpBox& bx, GPtr G, int gp, int gpl, int oxb, int oyb,
+                             int px, int py, int cn, const float (&xv)[kWT_CG], float (&acc)[kWT_CG], float (&S)[8]) {
+  const float u0 = (float)px - K.b0, v0 = (float)py - K.b1;
+  const float oc = K.m10 * u0 + K.m11 * v0;
+  const int ylo = max(bx.y0, (int)ceilf(fmaxf(oc - K.ry, -1.0f)));
+  const int yhi = min(bx.y1, (int)floorf(fminf(oc + K.ry, 3e7f)));
+  for (int oy = ylo; oy <= yhi; oy++) {
+    const float oyf = (float)oy;
+    const float txr = __fmaf_rn(K.a01, oyf, K.b0), tyr = __fmaf_rn(K.a11, oyf, K.b1);
+    float lo = -1.0f, hi = 3e7f;
+    warp_slab(K.a00, K.ra00, (float)px - txr, K.rs, lo, hi);
+    warp_slab(K.a10, K.ra10, (float)py - tyr, K.rs, lo, hi);
+    const int xlo = max(bx.x0, (int)ceilf(fmaxf(lo - K.dout, -1.0f)));
+    const int xhi = min(bx.x1, (int)floorf(fminf(hi + K.dout, 3e7f)));
+    const int rowoff = (oy - oyb) * gp - oxb;
+    const float yp = oyf - K.oyc;
+    float oxf = (float)xlo;
+    for (int ox = xlo; ox <= xhi; ox++, oxf += 1.0f) {
+      const float sx = __fmaf_rn(K.a00, oxf, txr);
+      const float sy = __fmaf_rn(K.a10, oxf, tyr);
+      const float fx0 = floorf(sx), fy0 = floorf(sy);
+      const int dx = px - (int)fx0, dy = py - (int)fy0;
+      if ((unsigned)dx > 1u || (unsigned)dy > 1u) continue;
+      const float fx = sx - fx0, fy = sy - fy0;
+      const float wx = dx ? fx : 1.0f - fx, wy = dy ? fy : 1.0f - fy;
+      const float w = wx * wy;
+      float a = 0.0f;
+#pragma unroll
+      for (int k = 0; k < kWT_CG; k++) {
+        if (k < cn) {
+          const float gv = G[k * gpl + rowoff + ox];
+          acc[k] = __fmaf_rn(gv, w, acc[k]);
+          a = __fmaf_rn(gv, xv[k], a);
+        }
+      }
+      const float dsx = dx ? a * wy : -a * wy;
+      const float dsy = dy ? a * wx : -a * wx;
+      const float xp = oxf - K.oxc;
+      S[0] = __fmaf_rn(dsx, xp, S[0]);
+      S[1] = __fmaf_rn(dsx, yp, S[1]);
+      S[2] = __fmaf_rn(dsy, xp, S[2]);
+      S[3] = __fmaf_rn(dsy, yp, S[3]);
+      S[4] = __fmaf_rn(dsx, sx - K.cx, S[4]);
+      S[5] = __fmaf_rn(dsy, sy - K.cy, S[5]);
+      S[6] += dsx;
+      S[7] += dsy;
+    }
+  }
+}
+
 // Backward as a gather.  Source pixel p is a tap of output q exactly when
 // floor(sx_q) is px-1 or px and floor(sy_q) is py-1 or py, with (sx_q, sy_q)
 // the float32 coordinate the forward computes.  Each source pixel walks the
@@ -272,17 +364,18 @@ ALB_D void warp_slab(float a, float ra, float u, float r, float& lo, float& hi) 
 // same pairs carry the parameter gradient: pair (p, q) adds g_q x_p times the
 // weight's derivative to dL/dsx_q, dL/dsy_q, and those are folded against the
 // coordinate's derivatives through eight running sums per thread.
-__global__ void __launch_bounds__(kWT_THREADS) k_warp_f32_bwd(int B, int C, int H, int W, int tiles_x, int tiles,
+template <bool AL>
+__global__ void __launch_bounds__(kWT_THREADS, 3) k_warp_f32_bwd(int B, int C, int H, int W, int tiles_x, int tiles,
                                                               const float* __restrict__ x,
                                                               const float* __restrict__ prm,
                                                               const float* __restrict__ gy, float* __restrict__ gx,
                                                               float* __restrict__ partials) {
-  extern __shared__ float sm[];
+  extern __shared__ __align__(16) float sm[];
   __shared__ WarpF sg;
   __shared__ float sM[6];  // forward map rows (m00, m01, m10, m11), search margins (source, output)
   __shared__ float red[32];
   const int b = blockIdx.y;
-  const int64_t plane = (int64_t)H * W;
+  const int plane = H * W;
   if (threadIdx.x == 0) {
     const WarpF g = warp_setup(prm, b, H, W);
     sg = g;
@@ -297,14 +390,20 @@ __global__ void __launch_bounds__(kWT_THREADS) k_warp_f32_bwd(int B, int C, int 
   __syncthreads();
   const WarpF g = sg;
   const WarpInv M{sM[0], sM[1], sM[2], sM[3]};
-  const float dsrc = sM[4], dout = sM[5];
+  const float dsrc = sM[4];
   const bool finite = isfinite(M.m00) && isfinite(M.m01) && isfinite(M.m10) && isfinite(M.m11) && isfinite(g.b0) &&
                       isfinite(g.b1);
-  const float ra00 = 1.0f / g.a00, ra10 = 1.0f / g.a10;
-  const float ry = (1.0f + dsrc) * (fabsf(M.m10) + fabsf(M.m11)) + dout;
-  const float oxc = g.cx + g.txp, oyc = g.cy + g.typ;
+  GatherK K;
+  K.a00 = g.a00; K.a01 = g.a01; K.a10 = g.a10; K.a11 = g.a11; K.b0 = g.b0; K.b1 = g.b1;
+  K.ra00 = 1.0f / g.a00; K.ra10 = 1.0f / g.a10;
+  K.m10 = M.m10; K.m11 = M.m11;
+  K.ry = (1.0f + dsrc) * (fabsf(M.m10) + fabsf(M.m11)) + sM[5];
+  K.rs = 1.0f + dsrc; K.dout = sM[5];
+  K.oxc = g.cx + g.txp; K.oyc = g.cy + g.typ; K.cx = g.cx; K.cy = g.cy;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const float* xb = x + (int64_t)b * C * plane;
   const float* gyb = gy + (int64_t)b * C * plane;
+  float* gxb = gx + (int64_t)b * C * plane;
   const int groups = (C + kWT_CG - 1) / kWT_CG;
   const int units = warp_units(tiles, groups);
   float S[8];
@@ -315,8 +414,8 @@ __global__ void __launch_bounds__(kWT_THREADS) k_warp_f32_bwd(int B, int C, int 
   if (units > 0) {
     int X0, Y0, c0;
     warp_unit(0, groups, tiles_x, X0, Y0, c0);
-    nb = warp_bwd_box(g, M, finite, X0, Y0, H, W, min(C - c0, kWT_CG));
-    if (nb.staged) warp_stage_async(sm, gyb + c0 * plane, min(C - c0, kWT_CG), H, W, nb);
+    nb = warp_bwd_box<AL>(g, M, finite, X0, Y0, H, W, min(C - c0, kWT_CG));
+    if (nb.staged) warp_stage_async<AL>(sm, gyb + (int64_t)c0 * plane, min(C - c0, kWT_CG), H, W, nb);
   }
   cp_async_commit_f();
   for (int u = 0; u < units; u++) {
@@ -327,31 +426,29 @@ __global__ void __launch_bounds__(kWT_THREADS) k_warp_f32_bwd(int B, int C, int 
     if (u + 1 < units) {
       int X1, Y1, c1;
       warp_unit(u + 1, groups, tiles_x, X1, Y1, c1);
-      nb = warp_bwd_box(g, M, finite, X1, Y1, H, W, min(C - c1, kWT_CG));
-      if (nb.staged) warp_stage_async(sm + ((u + 1) & 1) * kWT_BUF, gyb + c1 * plane, min(C - c1, kWT_CG), H, W, nb);
+      nb = warp_bwd_box<AL>(g, M, finite, X1, Y1, H, W, min(C - c1, kWT_CG));
+      if (nb.staged)
+        warp_stage_async<AL>(sm + ((u + 1) & 1) * kWT_BUF, gyb + (int64_t)c1 * plane, min(C - c1, kWT_CG), H, W, nb);
     }
     cp_async_commit_f();
     // this unit's source values, loaded while its copies land
+    const int px = X0 + tx;
     float xv[2][kWT_CG];
 #pragma unroll
     for (int j = 0; j < 2; j++) {
-      const int px = X0 + tx, py = Y0 + ty + 8 * j;
+      const int py = Y0 + ty + 8 * j;
       const bool in = px < W && py < H;
-      const float* xs = x + ((int64_t)b * C + c0) * plane + (int64_t)(in ? py : 0) * W + (in ? px : 0);
+      const int o = in ? py * W + px : 0;
 #pragma unroll
-      for (int k = 0; k < kWT_CG; k++) xv[j][k] = (in && k < cn) ? __ldg(xs + k * plane) : 0.0f;
+      for (int k = 0; k < kWT_CG; k++) xv[j][k] = (in && k < cn) ? __ldg(xb + (int64_t)(c0 + k) * plane + o) : 0.0f;
     }
     cp_async_wait_prev();
     __syncthreads();
     const int bh = bx.y1 - bx.y0 + 1;
-    // staged copy (box-relative rows and columns) or the image itself
-    const float* gb = bx.staged ? sm + (u & 1) * kWT_BUF : gyb + c0 * plane;
-    const int gp = bx.staged ? bx.pitch : W;
-    const int64_t gpl = bx.staged ? (int64_t)bh * bx.pitch : plane;
-    const int oyb = bx.staged ? bx.y0 : 0, oxb = bx.staged ? bx.x0 : 0;
-#pragma unroll 1
+    const float* buf = sm + (u & 1) * kWT_BUF;
+#pragma unroll
     for (int j = 0; j < 2; j++) {
-      const int px = X0 + tx, py = Y0 + ty + 8 * j;
+      const int py = Y0 + ty + 8 * j;
       if (px >= W || py >= H) continue;
       float acc[kWT_CG];
 #pragma unroll
@@ -360,55 +457,15 @@ __global__ void __launch_bounds__(kWT_THREADS) k_warp_f32_bwd(int B, int C, int 
 #pragma unroll
         for (int k = 0; k < kWT_CG; k++) acc[k] = __int_as_float(0x7fc00000);
       } else if (bx.x1 >= bx.x0) {
-        const float u0 = (float)px - g.b0, v0 = (float)py - g.b1;
-        const float oc = M.m10 * u0 + M.m11 * v0;
-        const int ylo = max(bx.y0, (int)ceilf(fmaxf(oc - ry, -1.0f)));
-        const int yhi = min(bx.y1, (int)floorf(fminf(oc + ry, (float)H)));
-        const float rs = 1.0f + dsrc;
-        for (int oy = ylo; oy <= yhi; oy++) {
-          const float txr = __fmaf_rn(g.a01, (float)oy, g.b0), tyr = __fmaf_rn(g.a11, (float)oy, g.b1);
-          float lo = -1.0f, hi = (float)W;
-          warp_slab(g.a00, ra00, (float)px - txr, rs, lo, hi);
-          warp_slab(g.a10, ra10, (float)py - tyr, rs, lo, hi);
-          const int xlo = max(bx.x0, (int)ceilf(fmaxf(lo - dout, -1.0f)));
-          const int xhi = min(bx.x1, (int)floorf(fminf(hi + dout, (float)W)));
-          const float* grow = gb + (int64_t)(oy - oyb) * gp;
-          for (int ox = xlo; ox <= xhi; ox++) {
-            const float sx = __fmaf_rn(g.a00, (float)ox, txr);
-            const float sy = __fmaf_rn(g.a10, (float)ox, tyr);
-            const float fx0 = floorf(sx), fy0 = floorf(sy);
-            const int dx = px - (int)fx0, dy = py - (int)fy0;
-            if ((unsigned)dx > 1u || (unsigned)dy > 1u) continue;
-            const float fx = sx - fx0, fy = sy - fy0;
-            const float wx = dx ? fx : 1.0f - fx, wy = dy ? fy : 1.0f - fy;
-            const float w = wx * wy;
-            float a = 0.0f;
-#pragma unroll
-            for (int k = 0; k < kWT_CG; k++) {
-              if (k < cn) {
-                const float gv = grow[k * gpl + (ox - oxb)];
-                acc[k] = __fmaf_rn(gv, w, acc[k]);
-                a = __fmaf_rn(gv, xv[j][k], a);
-              }
-            }
-            const float dsx = dx ? a * wy : -a * wy;
-            const float dsy = dy ? a * wx : -a * wx;
-            const float xp = (float)ox - oxc, yp = (float)oy - oyc;
-            S[0] = __fmaf_rn(dsx, xp, S[0]);
-            S[1] = __fmaf_rn(dsx, yp, S[1]);
-            S[2] = __fmaf_rn(dsy, xp, S[2]);
-            S[3] = __fmaf_rn(dsy, yp, S[3]);
-            S[4] = __fmaf_rn(dsx, sx - g.cx, S[4]);
-            S[5] = __fmaf_rn(dsy, sy - g.cy, S[5]);
-            S[6] += dsx;
-            S[7] += dsy;
-          }
-        }
+        if (bx.staged)
+          warp_gather_pixel(K, bx, buf, bx.pitch, bh * bx.pitch, bx.x0, bx.y0, px, py, cn, xv[j], acc, S);
+        else
+          warp_gather_pixel(K, bx, gyb + (int64_t)c0 * plane, W, plane, 0, 0, px, py, cn, xv[j], acc, S);
       }
-      float* out = gx + ((int64_t)b * C + c0) * plane + (int64_t)py * W + px;
+      const int o = py * W + px;
 #pragma unroll
       for (int k = 0; k < kWT_CG; k++)
-        if (k < cn) out[k * plane] = acc[k];
+        if (k < cn) gxb[(int64_t)(c0 + k) * plane + o] = acc[k];
     }
     __syncthreads();  // buffer (u & 1) is refilled by unit u + 2
   }
@@ -556,8 +613,9 @@ static alb_status warp_smem_optin() {
   ALB_CUDA(cudaGetDevice(&dev));
   if (dev >= 0 && dev < 64 && done[dev]) return ALB_OK;
   const int bytes = 2 * kWT_BUF * (int)sizeof(float);
-  ALB_CUDA(cudaFuncSetAttribute((const void*)k_warp_f32_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  ALB_CUDA(cudaFuncSetAttribute((const void*)k_warp_f32_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  const void* kernels[4] = {(const void*)k_warp_f32_fwd<true>, (const void*)k_warp_f32_fwd<false>,
+                            (const void*)k_warp_f32_bwd<true>, (const void*)k_warp_f32_bwd<false>};
+  for (const void* k : kernels) ALB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
   if (dev >= 0 && dev < 64) done[dev] = true;
   return ALB_OK;
 }
@@ -604,19 +662,38 @@ extern "C" size_t alb_f32_workspace_size(int32_t B, int32_t C, int32_t H, int32_
   return (size_t)(B > 0 ? B : 1) * 1024 * 4 * sizeof(float) + 256;
 }
 
+// warp shapes: batch within the grid's y limit, per-image offsets of a channel
+// group within int32
+static alb_status check_warp_shape(int32_t B, int32_t H, int32_t W, const char* what) {
+  ALB_REQUIRE(B <= 65535, ALB_ESHAPE, "%s: batch %d above 65535", what, B);
+  ALB_REQUIRE((int64_t)(kWT_CG + 1) * H * W < (1LL << 31), ALB_ESHAPE, "%s: image %dx%d too large", what, H, W);
+  return ALB_OK;
+}
+
+// 16-byte staging: W a multiple of four and 16-byte aligned planes
+static bool warp_aligned(int32_t W, const void* a, const void* b) {
+  return W % 4 == 0 && ((uintptr_t)a % 16) == 0 && ((uintptr_t)b % 16) == 0;
+}
+
 extern "C" alb_status alb_warp_affine_f32_fwd(int32_t B, int32_t C, int32_t H, int32_t W, const float* x,
                                               const float* prm, float* y, void* stream) {
   alb_status rc = check_f32(B, C, H, W, x, prm, y);
   if (rc != ALB_OK || B == 0) return rc;
-  ALB_REQUIRE(B <= 65535, ALB_ESHAPE, "alb_warp_affine_f32_fwd: batch %d above 65535", B);
-  const int tiles_x = (W + kWT_W - 1) / kWT_W, tiles_y = (H + kWT_H - 1) / kWT_H;
-  ALB_REQUIRE((int64_t)tiles_x * tiles_y < (1LL << 31), ALB_ESHAPE, "alb_warp_affine_f32_fwd: image too large");
-  const int tiles = tiles_x * tiles_y;
+  rc = check_warp_shape(B, H, W, "alb_warp_affine_f32_fwd");
+  if (rc != ALB_OK) return rc;
   rc = warp_smem_optin();
   if (rc != ALB_OK) return rc;
-  const int nblk = warp_ctas_per_image((const void*)k_warp_f32_fwd, tiles, B);
-  k_warp_f32_fwd<<<dim3(nblk, B), kWT_THREADS, 2 * kWT_BUF * sizeof(float), (cudaStream_t)stream>>>(
-      B, C, H, W, tiles_x, tiles, x, prm, y);
+  const int tiles_x = (W + kWT_W - 1) / kWT_W, tiles_y = (H + kWT_H - 1) / kWT_H;
+  const int tiles = tiles_x * tiles_y;
+  const bool al = warp_aligned(W, x, x);
+  const void* kern = al ? (const void*)k_warp_f32_fwd<true> : (const void*)k_warp_f32_fwd<false>;
+  const int nblk = warp_ctas_per_image(kern, tiles, B);
+  const dim3 grid(nblk, B);
+  const size_t smem = 2 * kWT_BUF * sizeof(float);
+  if (al)
+    k_warp_f32_fwd<true><<<grid, kWT_THREADS, smem, (cudaStream_t)stream>>>(B, C, H, W, tiles_x, tiles, x, prm, y);
+  else
+    k_warp_f32_fwd<false><<<grid, kWT_THREADS, smem, (cudaStream_t)stream>>>(B, C, H, W, tiles_x, tiles, x, prm, y);
   ALB_CUDA(cudaGetLastError());
   return ALB_OK;
 }
@@ -627,18 +704,26 @@ extern "C" alb_status alb_warp_affine_f32_bwd(int32_t B, int32_t C, int32_t H, i
   alb_status rc = check_f32(B, C, H, W, x, prm, gy);
   if (rc != ALB_OK || B == 0) return rc;
   ALB_REQUIRE(gx && gprm, ALB_EINVAL, "alb_warp_affine_f32_bwd: null output");
-  ALB_REQUIRE(B <= 65535, ALB_ESHAPE, "alb_warp_affine_f32_bwd: batch %d above 65535", B);
-  const int tiles_x = (W + kWT_W - 1) / kWT_W, tiles_y = (H + kWT_H - 1) / kWT_H;
-  ALB_REQUIRE((int64_t)tiles_x * tiles_y < (1LL << 31), ALB_ESHAPE, "alb_warp_affine_f32_bwd: image too large");
-  const int tiles = tiles_x * tiles_y;
+  rc = check_warp_shape(B, H, W, "alb_warp_affine_f32_bwd");
+  if (rc != ALB_OK) return rc;
   rc = warp_smem_optin();
   if (rc != ALB_OK) return rc;
-  const int nblk = warp_ctas_per_image((const void*)k_warp_f32_bwd, tiles, B);
+  const int tiles_x = (W + kWT_W - 1) / kWT_W, tiles_y = (H + kWT_H - 1) / kWT_H;
+  const int tiles = tiles_x * tiles_y;
+  const bool al = warp_aligned(W, gy, gy);
+  const void* kern = al ? (const void*)k_warp_f32_bwd<true> : (const void*)k_warp_f32_bwd<false>;
+  const int nblk = warp_ctas_per_image(kern, tiles, B);
   ALB_REQUIRE(workspace && workspace_bytes >= (size_t)B * nblk * 4 * sizeof(float), ALB_EWORKSPACE,
               "alb_warp_affine_f32_bwd: workspace too small");
   cudaStream_t st = (cudaStream_t)stream;
-  k_warp_f32_bwd<<<dim3(nblk, B), kWT_THREADS, 2 * kWT_BUF * sizeof(float), st>>>(
-      B, C, H, W, tiles_x, tiles, x, prm, gy, gx, (float*)workspace);
+  const dim3 grid(nblk, B);
+  const size_t smem = 2 * kWT_BUF * sizeof(float);
+  if (al)
+    k_warp_f32_bwd<true><<<grid, kWT_THREADS, smem, st>>>(B, C, H, W, tiles_x, tiles, x, prm, gy, gx,
+                                                          (float*)workspace);
+  else
+    k_warp_f32_bwd<false><<<grid, kWT_THREADS, smem, st>>>(B, C, H, W, tiles_x, tiles, x, prm, gy, gx,
+                                                           (float*)workspace);
   ALB_CUDA(cudaGetLastError());
   k_reduce_partials<<<B, 256, 0, st>>>(nblk, 4, (const float*)workspace, gprm);
   ALB_CUDA(cudaGetLastError());
