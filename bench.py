@@ -42,7 +42,8 @@ UNIT = "images/s"
 # suite workload (same H, W distribution), scaled per image; the roofline's
 # traffic figure is this times the images of one launch.  Only kernels whose
 # code is unchanged since that capture are listed.
-NCU_DRAM_BYTES_PER_IMAGE = {"Rotate": 977333.0, "ShiftScaleRotate": 946247.0, "ShiftHSV": 846090.0}
+NCU_DRAM_BYTES_PER_IMAGE = {"Rotate": 977333.0, "ShiftScaleRotate": 946247.0, "ShiftHSV": 846090.0,
+                            "Resize512": 1137000.0, "PadToSize512": 1172000.0, "Brightness": 848000.0}
 SUITE_N, SUITE_LO, SUITE_HI = 2000, 333, 500
 FUSED_N, FUSED_LO, FUSED_HI = 4096, 256, 1024
 DET_N, DET_HW = 256, 1024
@@ -490,9 +491,9 @@ def detection(dev, stream, steps=3, warmup=2):
     return res
 
 
-def differentiable(dev, stream, steps=3, warmup=2):
+def differentiable(dev, stream, steps=3, warmup=2, n=DIFF_B):
     from paper_1809_06839_gb300 import alb as A
-    B, Cc, H, W = DIFF_B, 3, DIFF_HW, DIFF_HW
+    B, Cc, H, W = n, 3, DIFF_HW, DIFF_HW
     g = torch.Generator(device=dev).manual_seed(SEED)
     x = torch.rand((B, Cc, H, W), device=dev, generator=g)
     gy = torch.randn((B, Cc, H, W), device=dev, generator=g)
@@ -525,7 +526,7 @@ def differentiable(dev, stream, steps=3, warmup=2):
     nb = x.numel() * 4
     res = dict(fwd_images_per_s=B / tf, bwd_images_per_s=B / tb, fwd_ms=tf * 1e3, bwd_ms=tb * 1e3,
                fwd_gbs=4 * nb / tf / 1e9, bwd_gbs=(3 * nb + 3 * nb) / tb / 1e9,
-               workload="f32 256x3x512x512 warp (bilinear, zero border) + photometric, fwd and bwd")
+               workload=f"f32 {B}x3x512x512 warp (bilinear, zero border) + photometric, fwd and bwd")
     del x, gy, w, y, gw, gx
     torch.cuda.empty_cache()
     return res
@@ -625,6 +626,7 @@ def main():
     ap.add_argument("--extras", default="fused,detection,differentiable,large,distort,targets",
                     help="sub-workloads to run after the suite (comma-separated)")
     ap.add_argument("--fused-n", type=int, default=FUSED_N, help="images of the fused workload (profiling runs)")
+    ap.add_argument("--diff-b", type=int, default=DIFF_B, help="batch of the differentiable workload (profiling runs)")
     args = ap.parse_args()
     ws, rank, local, dist = dist_setup(args)
     if args.impl == "reference":
@@ -681,7 +683,7 @@ def main():
         if "detection" in which:
             extra["detection"] = detection(dev, stream)
         if "differentiable" in which:
-            extra["differentiable"] = differentiable(dev, stream)
+            extra["differentiable"] = differentiable(dev, stream, n=args.diff_b)
         if "large" in which:
             extra["per_transform_large"] = large_suite(dev, stream, hbm)
         if "distort" in which:
