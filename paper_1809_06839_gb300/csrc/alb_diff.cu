@@ -144,12 +144,21 @@ ALB_D WarpBox warp_fwd_box(const WarpF& g, int ox0, int oy0, int H, int W, int c
   return bx;
 }
 
-// (tile origin, first channel) of unit u of this CTA
-ALB_D void warp_unit(int u, int groups, int tiles_x, int& X0, int& Y0, int& c0) {
-  const int t = blockIdx.x + (u / groups) * gridDim.x;
-  c0 = (u % groups) * kWT_CG;
-  X0 = (t % tiles_x) * kWT_W;
-  Y0 = (t / tiles_x) * kWT_H;
+// (tile origin, first channel) of unit u of this CTA.  No integer division on
+// the common path: one channel group needs none, and the tile row comes from a
+// float reciprocal of tiles_x, exact for tile indices below 2^21 and tiles_x up
+// to 2048 (checked on every such pair); larger grids divide.
+ALB_D void warp_unit(int u, int groups, int tiles_x, float rtx, int& X0, int& Y0, int& c0) {
+  int tu = u;
+  c0 = 0;
+  if (groups != 1) {
+    tu = u / groups;
+    c0 = (u - tu * groups) * kWT_CG;
+  }
+  const int t = blockIdx.x + tu * gridDim.x;
+  const int ty = (t < (1 << 21) && tiles_x <= 2048) ? (int)__fmul_rn(__fadd_rn((float)t, 0.5f), rtx) : t / tiles_x;
+  X0 = (t - ty * tiles_x) * kWT_W;
+  Y0 = ty * kWT_H;
 }
 
 ALB_D int warp_units(int tiles, int groups) {
@@ -176,10 +185,11 @@ __global__ void __launch_bounds__(kWT_THREADS) k_warp_f32_fwd(int B, int C, int 
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int groups = (C + kWT_CG - 1) / kWT_CG;
   const int units = warp_units(tiles, groups);
+  const float rtx = 1.0f / (float)tiles_x;
   WarpBox nb{0, 0, -1, -1, 1, 0};
   if (units > 0) {
     int X0, Y0, c0;
-    warp_unit(0, groups, tiles_x, X0, Y0, c0);
+    warp_unit(0, groups, tiles_x, rtx, X0, Y0, c0);
     nb = warp_fwd_box<AL>(g, X0, Y0, H, W, min(C - c0, kWT_CG));
     if (nb.staged) warp_stage_async<AL>(sm, xb + (int64_t)c0 * plane, min(C - c0, kWT_CG), H, W, nb);
   }
@@ -187,11 +197,11 @@ __global__ void __launch_bounds__(kWT_THREADS) k_warp_f32_fwd(int B, int C, int 
   for (int u = 0; u < units; u++) {
     const WarpBox bx = nb;
     int ox0, oy0, c0;
-    warp_unit(u, groups, tiles_x, ox0, oy0, c0);
+    warp_unit(u, groups, tiles_x, rtx, ox0, oy0, c0);
     const int cn = min(C - c0, kWT_CG);
     if (u + 1 < units) {
       int X1, Y1, c1;
-      warp_unit(u + 1, groups, tiles_x, X1, Y1, c1);
+      warp_unit(u + 1, groups, tiles_x, rtx, X1, Y1, c1);
       nb = warp_fwd_box<AL>(g, X1, Y1, H, W, min(C - c1, kWT_CG));
       if (nb.staged)
         warp_stage_async<AL>(sm + ((u + 1) & 1) * kWT_BUF, xb + (int64_t)c1 * plane, min(C - c1, kWT_CG), H, W, nb);
@@ -406,6 +416,7 @@ __global__ void __launch_bounds__(kWT_THREADS, 4) k_warp_f32_bwd(int B, int C, i
   float* gxb = gx + (int64_t)b * C * plane;
   const int groups = (C + kWT_CG - 1) / kWT_CG;
   const int units = warp_units(tiles, groups);
+  const float rtx = 1.0f / (float)tiles_x;
   float S[8];
 #pragma unroll
   for (int k = 0; k < 8; k++) S[k] = 0.0f;
@@ -413,7 +424,7 @@ __global__ void __launch_bounds__(kWT_THREADS, 4) k_warp_f32_bwd(int B, int C, i
   WarpBox nb{0, 0, -1, -1, 1, 0};
   if (units > 0) {
     int X0, Y0, c0;
-    warp_unit(0, groups, tiles_x, X0, Y0, c0);
+    warp_unit(0, groups, tiles_x, rtx, X0, Y0, c0);
     nb = warp_bwd_box<AL>(g, M, finite, X0, Y0, H, W, min(C - c0, kWT_CG));
     if (nb.staged) warp_stage_async<AL>(sm, gyb + (int64_t)c0 * plane, min(C - c0, kWT_CG), H, W, nb);
   }
@@ -421,11 +432,11 @@ __global__ void __launch_bounds__(kWT_THREADS, 4) k_warp_f32_bwd(int B, int C, i
   for (int u = 0; u < units; u++) {
     const WarpBox bx = nb;
     int X0, Y0, c0;
-    warp_unit(u, groups, tiles_x, X0, Y0, c0);
+    warp_unit(u, groups, tiles_x, rtx, X0, Y0, c0);
     const int cn = min(C - c0, kWT_CG);
     if (u + 1 < units) {
       int X1, Y1, c1;
-      warp_unit(u + 1, groups, tiles_x, X1, Y1, c1);
+      warp_unit(u + 1, groups, tiles_x, rtx, X1, Y1, c1);
       nb = warp_bwd_box<AL>(g, M, finite, X1, Y1, H, W, min(C - c1, kWT_CG));
       if (nb.staged)
         warp_stage_async<AL>(sm + ((u + 1) & 1) * kWT_BUF, gyb + (int64_t)c1 * plane, min(C - c1, kWT_CG), H, W, nb);
@@ -670,9 +681,10 @@ static alb_status check_warp_shape(int32_t B, int32_t H, int32_t W, const char* 
   return ALB_OK;
 }
 
-// 16-byte staging: W a multiple of four and 16-byte aligned planes
-static bool warp_aligned(int32_t W, const void* a, const void* b) {
-  return W % 4 == 0 && ((uintptr_t)a % 16) == 0 && ((uintptr_t)b % 16) == 0;
+// 16-byte staging of the staged tensor: W a multiple of four and 16-byte
+// aligned planes
+static bool warp_aligned(int32_t W, const void* staged) {
+  return W % 4 == 0 && ((uintptr_t)staged % 16) == 0;
 }
 
 extern "C" alb_status alb_warp_affine_f32_fwd(int32_t B, int32_t C, int32_t H, int32_t W, const float* x,
@@ -685,7 +697,7 @@ extern "C" alb_status alb_warp_affine_f32_fwd(int32_t B, int32_t C, int32_t H, i
   if (rc != ALB_OK) return rc;
   const int tiles_x = (W + kWT_W - 1) / kWT_W, tiles_y = (H + kWT_H - 1) / kWT_H;
   const int tiles = tiles_x * tiles_y;
-  const bool al = warp_aligned(W, x, x);
+  const bool al = warp_aligned(W, x);
   const void* kern = al ? (const void*)k_warp_f32_fwd<true> : (const void*)k_warp_f32_fwd<false>;
   const int nblk = warp_ctas_per_image(kern, tiles, B);
   const dim3 grid(nblk, B);
@@ -710,7 +722,7 @@ extern "C" alb_status alb_warp_affine_f32_bwd(int32_t B, int32_t C, int32_t H, i
   if (rc != ALB_OK) return rc;
   const int tiles_x = (W + kWT_W - 1) / kWT_W, tiles_y = (H + kWT_H - 1) / kWT_H;
   const int tiles = tiles_x * tiles_y;
-  const bool al = warp_aligned(W, gy, gy);
+  const bool al = warp_aligned(W, gy);
   const void* kern = al ? (const void*)k_warp_f32_bwd<true> : (const void*)k_warp_f32_bwd<false>;
   const int nblk = warp_ctas_per_image(kern, tiles, B);
   ALB_REQUIRE(workspace && workspace_bytes >= (size_t)B * nblk * 4 * sizeof(float), ALB_EWORKSPACE,
