@@ -3,12 +3,15 @@
 // the resizes (Sec. II-B scaling; Sec. II-A random sized crop), for images
 // (Q5 bilinear) and their masks (nearest), with reflect-101 borders for warps.
 //
-// Work item = one 16 x 16 output tile, owned by ONE warp: there is no
-// block-wide barrier anywhere.  Each warp double-buffers its own staging box in
-// shared memory: while it computes tile i it has the source footprint of tile
-// i + 1 (the bounding box of the mapped tile plus the +1 tap) in flight as raw,
-// aligned 16-byte cp.async copies, one staged row per lane with the row's byte
-// phase kept beside it.  Rows are reflected (warps) or clamped (resizes) when
+// Work item = one output tile, owned by ONE warp: there is no block-wide
+// barrier anywhere.  Each warp stages the source footprint of its tile (the
+// bounding box of the mapped tile plus the +1 tap) in its own shared-memory box
+// as raw, aligned 16-byte cp.async copies, one staged row per lane with the
+// row's byte phase kept beside it.  The general kernel (16 x 16 tiles, masks)
+// double-buffers the box: while it computes tile i, tile i + 1's copies are in
+// flight.  The RGB kernels below single-buffer it instead: half the shared
+// memory per warp lets more warps reside, and other warps hide the copies
+// better than a second buffer does (measured: resize -16 %, affine -12 %).  Rows are reflected (warps) or clamped (resizes) when
 // they are copied; for tiles whose box crosses the image's left/right border
 // the staged span is the reflected column range and each tap column goes
 // through the border map.  Lane l computes output column l & 15 for rows
@@ -421,7 +424,8 @@ __global__ void __launch_bounds__(32 * NWARP, 5) k_resample_warp(Plan plan, ImgL
 // two current tap rows' h in registers (for an enlargement most output rows
 // reuse both, or shift by one source row).  The tile's source box (up to
 // RB_X x RB_Y pixels: enlargements and reductions to ~0.95) is staged per warp
-// in shared memory by cp.async, double-buffered.  Measured trade-off: a taller
+// in shared memory by cp.async, one buffer per warp (the per-tile image and
+// geometry stay in registers).  Measured trade-off: a taller
 // tile amortises the per-tile geometry, a larger box costs warps per SM (the
 // row chain is latency-bound); 32 x 32 with a 36 x 36 box beat 32 x 16 with
 // 36 x 20 and 32 x 32 with 36 x 28.  Larger footprints read global memory.
@@ -599,8 +603,8 @@ ALB_D void r_tile_compute(const RImg& k, const RTile& g, int lane, int32_t vcol,
 }
 
 struct RShared {       // dynamic shared memory of k_resize_rows (above the 48 KB static limit)
-  uint8_t box[RWARP][2][RB_Y * RPITCH + 16];   // +16: the last row's tap read past the staged bytes
-  int32_t rowoff[RWARP][2][RB_Y];
+  uint8_t box[RWARP][1][RB_Y * RPITCH + 16];   // +16: the last row's tap read past the staged bytes
+  int32_t rowoff[RWARP][1][RB_Y];
   RImg simg[RWARP][2];
   RTile stile[RWARP][2];
 };
@@ -609,51 +613,29 @@ template <int MAP>
 __global__ void __launch_bounds__(32 * RWARP) k_resize_rows(Plan plan, ImgList in, ImgList out, PrmList prm) {
   extern __shared__ __align__(16) uint8_t rs_dyn[];
   RShared& sm = *reinterpret_cast<RShared*>(rs_dyn);
-  auto& box = sm.box;
-  auto& rowoff = sm.rowoff;
-  auto& simg = sm.simg;
-  auto& stile = sm.stile;
   int32_t it0, it1;
   item_range(plan, it0, it1);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int32_t item = it0 + w;
   if (item >= it1) return;
-  int32_t ccol, crow;          // this lane's coordinates of the current tile
-  {
-    RImg k;
-    RTile g;
-    r_load_img<MAP>(plan, in, out, prm, item_image(plan, item), k);
-    r_tile_geo<MAP>(k, prm, item, lane, g, ccol, crow);
-    if (lane == 0) { simg[w][0] = k; stile[w][0] = g; }
-    r_tile_stage(k, g, lane, box[w][0], rowoff[w][0]);
-  }
-  cp_async_commit();
-  int buf = 0;
-  for (; item < it1; item += RWARP, buf ^= 1) {
-    const int32_t nitem = item + RWARP;
-    int32_t ncol = 0, nrow = 0;
-    if (nitem < it1) {
-      __syncwarp();
-      RImg k = simg[w][buf];
-      if (nitem >= k.prefix + k.ntiles) {
-        int32_t b = k.b;
-        while (nitem >= plan.prefix[b + 1]) b++;
-        r_load_img<MAP>(plan, in, out, prm, b, k);
-      }
-      RTile g;
-      r_tile_geo<MAP>(k, prm, nitem, lane, g, ncol, nrow);
-      __syncwarp();
-      if (lane == 0) { simg[w][buf ^ 1] = k; stile[w][buf ^ 1] = g; }
-      r_tile_stage(k, g, lane, box[w][buf ^ 1], rowoff[w][buf ^ 1]);
+  RImg k;
+  r_load_img<MAP>(plan, in, out, prm, item_image(plan, item), k);
+  for (; item < it1; item += RWARP) {
+    if (item >= k.prefix + k.ntiles) {
+      int32_t b = k.b;
+      while (item >= plan.prefix[b + 1]) b++;
+      r_load_img<MAP>(plan, in, out, prm, b, k);
     }
-    cp_async_commit();
-    cp_async_wait<1>();
+    RTile g;
+    int32_t ccol, crow;
+    r_tile_geo<MAP>(k, prm, item, lane, g, ccol, crow);
     __syncwarp();
-    r_tile_compute(simg[w][buf], stile[w][buf], lane, ccol, crow, box[w][buf], rowoff[w][buf]);
-    __syncwarp();      // every lane is done with box[buf] before it is refilled
-    ccol = ncol; crow = nrow;
+    r_tile_stage(k, g, lane, sm.box[w][0], sm.rowoff[w][0]);
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncwarp();
+    r_tile_compute(k, g, lane, ccol, crow, sm.box[w][0], sm.rowoff[w][0]);
   }
-  cp_async_wait<0>();
 }
 
 // --------------------------------------------------------------- affine warp (RGB, bilinear)
@@ -661,11 +643,12 @@ __global__ void __launch_bounds__(32 * RWARP) k_resize_rows(Plan plan, ImgList i
 // lane j = output column j, and walks the tile's rows: the Q16 source
 // coordinates of a lane advance by (q1, q4) per row, already offset to the
 // tile's staged box and biased by the Q16 -> Q5 rounding constant.  The box
-// (up to AB - 1 pixels each way: the whole tile at any angle for scales >= 0.9;
-// the box is kept at 40 so that 16 warps fit on an SM: the kernel is
-// latency-sensitive)
-// is staged per warp by cp.async, rows reflected at copy time, double-
-// buffered; a per-row table holds row * pitch + byte phase, so a tap row's
+// (up to AB - 1 pixels each way: the whole tile at any angle for scales >= 0.9)
+// is staged per warp by cp.async, rows reflected at copy time, one buffer per
+// warp with the image and tile state in registers (at most 85 registers: six
+// CTAs, 24 warps per SM -- the kernel is latency-bound, so resident warps
+// matter more than a second buffer); a per-row table holds row * pitch + byte
+// phase, so a tap row's
 // offset is one shared load.  Tiles whose box crosses the left/right image
 // border map each tap column through reflect-101; tiles whose footprint does
 // not fit read their taps from global memory.
@@ -823,13 +806,13 @@ ALB_D void a_tile_compute(const AImg& k, const ATile& g, int lane, const uint8_t
 }
 
 struct AShared {       // dynamic shared memory of k_warp_affine3
-  uint8_t box[AWARP][2][AB * APITCH + 16];   // +16: the last row's tap read past the staged bytes
-  int32_t rowoff[AWARP][2][AB];
+  uint8_t box[AWARP][1][AB * APITCH + 16];
+  int32_t rowoff[AWARP][1][AB];
   AImg simg[AWARP][2];
   ATile stile[AWARP][2];
 };
 
-__global__ void __launch_bounds__(32 * AWARP) k_warp_affine3(Plan plan, ImgList in, ImgList out, PrmList prm) {
+__global__ void __launch_bounds__(32 * AWARP, 6) k_warp_affine3(Plan plan, ImgList in, ImgList out, PrmList prm) {
   extern __shared__ __align__(16) uint8_t aw_dyn[];
   AShared& sm = *reinterpret_cast<AShared*>(aw_dyn);
   int32_t it0, it1;
@@ -837,39 +820,23 @@ __global__ void __launch_bounds__(32 * AWARP) k_warp_affine3(Plan plan, ImgList 
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int32_t item = it0 + w;
   if (item >= it1) return;
-  {
-    AImg k;
-    ATile g;
-    a_load_img(plan, in, out, prm, item_image(plan, item), k);
-    a_tile_geo(k, item, g);
-    if (lane == 0) { sm.simg[w][0] = k; sm.stile[w][0] = g; }
-    a_tile_stage(k, g, lane, sm.box[w][0], sm.rowoff[w][0]);
-  }
-  cp_async_commit();
-  int buf = 0;
-  for (; item < it1; item += AWARP, buf ^= 1) {
-    const int32_t nitem = item + AWARP;
-    if (nitem < it1) {
-      __syncwarp();
-      AImg k = sm.simg[w][buf];
-      if (nitem >= k.prefix + k.ntiles) {
-        int32_t b = k.b;
-        while (nitem >= plan.prefix[b + 1]) b++;
-        a_load_img(plan, in, out, prm, b, k);
-      }
-      ATile g;
-      a_tile_geo(k, nitem, g);
-      __syncwarp();
-      if (lane == 0) { sm.simg[w][buf ^ 1] = k; sm.stile[w][buf ^ 1] = g; }
-      a_tile_stage(k, g, lane, sm.box[w][buf ^ 1], sm.rowoff[w][buf ^ 1]);
+  AImg k;
+  a_load_img(plan, in, out, prm, item_image(plan, item), k);
+  for (; item < it1; item += AWARP) {
+    if (item >= k.prefix + k.ntiles) {
+      int32_t b = k.b;
+      while (item >= plan.prefix[b + 1]) b++;
+      a_load_img(plan, in, out, prm, b, k);
     }
-    cp_async_commit();
-    cp_async_wait<1>();
+    ATile g;
+    a_tile_geo(k, item, g);
     __syncwarp();
-    a_tile_compute(sm.simg[w][buf], sm.stile[w][buf], lane, sm.box[w][buf], sm.rowoff[w][buf]);
-    __syncwarp();      // every lane is done with box[buf] before it is refilled
+    a_tile_stage(k, g, lane, sm.box[w][0], sm.rowoff[w][0]);
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncwarp();
+    a_tile_compute(k, g, lane, sm.box[w][0], sm.rowoff[w][0]);
   }
-  cp_async_wait<0>();
 }
 
 // --------------------------------------------------------------- elastic (RGB, bilinear)
