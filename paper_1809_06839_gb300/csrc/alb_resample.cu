@@ -639,22 +639,25 @@ __global__ void __launch_bounds__(32 * RWARP) k_resize_rows(Plan plan, ImgList i
 }
 
 // --------------------------------------------------------------- affine warp (RGB, bilinear)
-// Rotate / ShiftScaleRotate on RGB images.  A warp owns a 32 x 12 output tile,
+// Rotate / ShiftScaleRotate on RGB images.  A warp owns a 32 x 20 output tile,
 // lane j = output column j, and walks the tile's rows: the Q16 source
 // coordinates of a lane advance by (q1, q4) per row, already offset to the
 // tile's staged box and biased by the Q16 -> Q5 rounding constant.  The box
-// (up to AB - 1 pixels each way: the whole tile at any angle for scales >= 0.9)
+// (up to AB - 1 = 47 pixels each way: the whole tile at any angle for scales
+// >= 0.9, whose footprint is at most 52 * 0.71 / 0.9 + 2 = 43 pixels)
 // is staged per warp by cp.async, rows reflected at copy time, one buffer per
 // warp with the image and tile state in registers (at most 85 registers: six
 // CTAs, 24 warps per SM -- the kernel is latency-bound, so resident warps
-// matter more than a second buffer); a per-row table holds row * pitch + byte
+// matter more than a second buffer; with one buffer a taller tile pays:
+// 32 x 20 beat 32 x 12 by 4 %, 32 x 24 and 32 x 28 lost on Rotate); a per-row
+// table holds row * pitch + byte
 // phase, so a tap row's
 // offset is one shared load.  Tiles whose box crosses the left/right image
 // border map each tap column through reflect-101; tiles whose footprint does
 // not fit read their taps from global memory.
-constexpr int AT_W = 32, AT_H = 12;   // output tile (columns x rows)
-constexpr int AB = 40;                // staged box side (pixels)
-constexpr int APITCH = 144;           // staged row pitch in bytes
+constexpr int AT_W = 32, AT_H = 20;   // output tile (columns x rows)
+constexpr int AB = 48;                // staged box side (pixels)
+constexpr int APITCH = 176;           // staged row pitch in bytes
 constexpr int AWARP = 4;              // warps per CTA
 static_assert(APITCH % 16 == 0, "cp.async destinations must be 16-byte aligned");
 static_assert(APITCH >= 15 + 3 * (AB - 1) + 12, "a tap read (3 words from the pair's word) stays in its row");
