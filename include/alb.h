@@ -318,7 +318,12 @@ ALB_API alb_status alb_autotune_batch(const alb_chain_cfg* cfg, int32_t n, const
  * zero border.  Photometric: y = clamp(alpha x + beta, 0, 1)^gamma.
  * Backward kernels recompute sampling coordinates from prm (nothing is
  * stored by the forward), write the input gradient gx (same layout as x)
- * and ACCUMULATE nothing: gprm [B][4] / [B][3] is overwritten. */
+ * and ACCUMULATE nothing: gprm [B][4] / [B][3] is overwritten.  The warp's
+ * input gradient is a gather over the forward's exact (output, weight)
+ * pairs and every reduction runs in a fixed order, so both backward calls
+ * are bitwise repeatable.  Limits: B <= 65535 and 4*H*W < 2^31 for the warp
+ * (ALB_ESHAPE otherwise); workspace of alb_f32_workspace_size bytes for the
+ * backward calls (ALB_EWORKSPACE when smaller). */
 ALB_API size_t alb_f32_workspace_size(int32_t B, int32_t C, int32_t H, int32_t W);
 ALB_API alb_status alb_warp_affine_f32_fwd(int32_t B, int32_t C, int32_t H, int32_t W, const float* x,
                                    const float* prm, float* y, void* stream);
