@@ -162,3 +162,26 @@ def test_workspace_sizes(L):
     cfg = alb.chain_cfg()
     assert alb.alb_batch_workspace_size(cfg, 64, alb.MODE_PLAIN) > alb.alb_batch_workspace_size(cfg, 64,
                                                                                                 alb.MODE_FUSED)
+
+
+def test_float_path_shape_limits_without_cuda(L):
+    """The float entry points reject a bad shape, a null pointer, a batch above
+    the grid's y limit or an image whose per-image offsets leave int32 before
+    any device work (the pointers below are never dereferenced)."""
+    fake = C.c_void_p(16)
+    fwd, bwd = L.alb_warp_affine_f32_fwd, L.alb_warp_affine_f32_bwd
+    pfwd, pbwd = L.alb_photometric_f32_fwd, L.alb_photometric_f32_bwd
+    assert fwd(2, 3, 0, 8, fake, fake, fake, None) == alb.ALB_ESHAPE
+    assert fwd(2, 3, 8, 8, None, fake, fake, None) == alb.ALB_EINVAL
+    assert fwd(70000, 3, 8, 8, fake, fake, fake, None) == alb.ALB_ESHAPE
+    assert "65535" in alb.alb_last_error()
+    assert fwd(1, 3, 1 << 15, 1 << 14, fake, fake, fake, None) == alb.ALB_ESHAPE
+    assert "too large" in alb.alb_last_error()
+    assert bwd(70000, 3, 8, 8, fake, fake, fake, fake, fake, fake, 1 << 40, None) == alb.ALB_ESHAPE
+    assert bwd(1, 3, 8, 8, fake, fake, fake, None, fake, fake, 1 << 40, None) == alb.ALB_EINVAL
+    assert bwd(1, 3, 1 << 15, 1 << 14, fake, fake, fake, fake, fake, fake, 1 << 40, None) == alb.ALB_ESHAPE
+    assert pfwd(70000, 3, 8, 8, fake, fake, fake, None) == alb.ALB_ESHAPE
+    assert pbwd(70000, 3, 8, 8, fake, fake, fake, fake, fake, fake, 1 << 40, None) == alb.ALB_ESHAPE
+    # an empty batch is a no-op
+    assert fwd(0, 3, 8, 8, None, None, None, None) == alb.ALB_OK
+    assert bwd(0, 3, 8, 8, None, None, None, None, None, None, 0, None) == alb.ALB_OK
