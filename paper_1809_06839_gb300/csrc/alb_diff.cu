@@ -304,26 +304,33 @@ ALB_D void warp_slab(float a, float ra, float u, float r, float& lo, float& hi) 
 // per-image constants of the gather search
 struct GatherK {
   float a00, a01, a10, a11, b0, b1, ra00, ra10;
-  float m10, m11, ry, rs, dout, oxc, oyc, cx, cy;
+  float m10, m11, ry, rs, rs2, dout, oxc, oyc, cx, cy;
 };
 
-// Gather of one source pixel p = (px, py) over the output rows [ylo, yhi] of
-// the search box: accumulates the input gradient of the cn channels in acc and
-// the eight parameter sums in S.  G: the gradient rows (staged box: `gp` row
-// pitch, `gpl` channel pitch, rows and columns relative to (oxb, oyb); or the
-// image itself).
+// Gather of two horizontally adjacent source pixels p = (px, py) and
+// p' = (px + 1, py) (p' absent when has1 is false): their candidate outputs are
+// those sampled in [px - 1, px + 2) x [py - 1, py + 1), searched row by row
+// once for both.  A candidate with floor(sx) - px in {-1, 0, 1} is a tap of p
+// (px - floor(sx) in {0, 1}), of p' (px + 1 - floor(sx) in {0, 1}) or of both;
+// its gradient values are read once, each pixel's input gradient accumulates
+// g w in acc0 / acc1, and the two pixels' terms of the same output are folded
+// into dL/dsx, dL/dsy before the eight parameter sums S.  G: the gradient rows
+// (staged box: `gp` row pitch, `gpl` channel pitch, rows and columns relative
+// to (oxb, oyb); or the image itself).
 template <typename GPtr>
-ALB_D void warp_gather_pixel(const GatherK& K, const WarpBox& bx, GPtr G, int gp, int gpl, int oxb, int oyb,
-                             int px, int py, int cn, const float (&xv)[kWT_CG], float (&acc)[kWT_CG], float (&S)[8]) {
+ALB_D void warp_gather_pair(const GatherK& K, const WarpBox& bx, GPtr G, int gp, int gpl, int oxb, int oyb,
+                            int px, int py, int cn, bool has1, const float (&xa)[kWT_CG], const float (&xc)[kWT_CG],
+                            float (&acc0)[kWT_CG], float (&acc1)[kWT_CG], float (&S)[8]) {
   const float u0 = (float)px - K.b0, v0 = (float)py - K.b1;
   const float oc = K.m10 * u0 + K.m11 * v0;
-  const int ylo = max(bx.y0, (int)ceilf(fmaxf(oc - K.ry, -1.0f)));
-  const int yhi = min(bx.y1, (int)floorf(fminf(oc + K.ry, 3e7f)));
+  const float ocl = fminf(oc, oc + K.m10), och = fmaxf(oc, oc + K.m10);
+  const int ylo = max(bx.y0, (int)ceilf(fmaxf(ocl - K.ry, -1.0f)));
+  const int yhi = min(bx.y1, (int)floorf(fminf(och + K.ry, 3e7f)));
   for (int oy = ylo; oy <= yhi; oy++) {
     const float oyf = (float)oy;
     const float txr = __fmaf_rn(K.a01, oyf, K.b0), tyr = __fmaf_rn(K.a11, oyf, K.b1);
     float lo = -1.0f, hi = 3e7f;
-    warp_slab(K.a00, K.ra00, (float)px - txr, K.rs, lo, hi);
+    warp_slab(K.a00, K.ra00, (float)px + 0.5f - txr, K.rs2, lo, hi);
     warp_slab(K.a10, K.ra10, (float)py - tyr, K.rs, lo, hi);
     const int xlo = max(bx.x0, (int)ceilf(fmaxf(lo - K.dout, -1.0f)));
     const int xhi = min(bx.x1, (int)floorf(fminf(hi + K.dout, 3e7f)));
@@ -334,22 +341,35 @@ ALB_D void warp_gather_pixel(const GatherK& K, const WarpBox& bx, GPtr G, int gp
       const float sx = __fmaf_rn(K.a00, oxf, txr);
       const float sy = __fmaf_rn(K.a10, oxf, tyr);
       const float fx0 = floorf(sx), fy0 = floorf(sy);
-      const int dx = px - (int)fx0, dy = py - (int)fy0;
-      if ((unsigned)dx > 1u || (unsigned)dy > 1u) continue;
+      const int dxa = px - (int)fx0, dy = py - (int)fy0;
+      if ((unsigned)(dxa + 1) > 2u || (unsigned)dy > 1u) continue;
+      const bool h0 = dxa >= 0, h1 = has1 && dxa <= 0;
       const float fx = sx - fx0, fy = sy - fy0;
-      const float wx = dx ? fx : 1.0f - fx, wy = dy ? fy : 1.0f - fy;
-      const float w = wx * wy;
-      float a = 0.0f;
+      const float wy = dy ? fy : 1.0f - fy;
+      const float wx0 = dxa == 1 ? fx : 1.0f - fx;   // p: right tap when dxa = 1
+      const float wx1 = dxa == 0 ? fx : 1.0f - fx;   // p': right tap when dxa = 0
+      const float w0 = wx0 * wy, w1 = wx1 * wy;
+      float a0 = 0.0f, a1 = 0.0f;
 #pragma unroll
       for (int k = 0; k < kWT_CG; k++) {
         if (k < cn) {
           const float gv = G[k * gpl + rowoff + ox];
-          acc[k] = __fmaf_rn(gv, w, acc[k]);
-          a = __fmaf_rn(gv, xv[k], a);
+          if (h0) {
+            acc0[k] = __fmaf_rn(gv, w0, acc0[k]);
+            a0 = __fmaf_rn(gv, xa[k], a0);
+          }
+          if (h1) {
+            acc1[k] = __fmaf_rn(gv, w1, acc1[k]);
+            a1 = __fmaf_rn(gv, xc[k], a1);
+          }
         }
       }
-      const float dsx = dx ? a * wy : -a * wy;
-      const float dsy = dy ? a * wx : -a * wx;
+      // d w / d sx is +wy for a right tap, -wy for a left one; d w / d sy is
+      // +wx for a lower tap, -wx for an upper one
+      const float ex = (dxa == 1 ? a0 : -a0) + (dxa == 0 ? a1 : -a1);   // a0 = 0 unless h0, a1 = 0 unless h1
+      const float ey = __fmaf_rn(a0, wx0, a1 * wx1);
+      const float dsx = ex * wy;
+      const float dsy = dy ? ey : -ey;
       const float xp = oxf - K.oxc;
       S[0] = __fmaf_rn(dsx, xp, S[0]);
       S[1] = __fmaf_rn(dsx, yp, S[1]);
@@ -408,9 +428,9 @@ __global__ void __launch_bounds__(kWT_THREADS, 4) k_warp_f32_bwd(int B, int C, i
   K.ra00 = 1.0f / g.a00; K.ra10 = 1.0f / g.a10;
   K.m10 = M.m10; K.m11 = M.m11;
   K.ry = (1.0f + dsrc) * (fabsf(M.m10) + fabsf(M.m11)) + sM[5];
-  K.rs = 1.0f + dsrc; K.dout = sM[5];
+  K.rs = 1.0f + dsrc; K.rs2 = 1.5f + dsrc; K.dout = sM[5];
   K.oxc = g.cx + g.txp; K.oyc = g.cy + g.typ; K.cx = g.cx; K.cy = g.cy;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int tp = threadIdx.x & 15, tr = threadIdx.x >> 4;   // pixel pair 2 tp, 2 tp + 1 of tile row tr
   const float* xb = x + (int64_t)b * C * plane;
   const float* gyb = gy + (int64_t)b * C * plane;
   float* gxb = gx + (int64_t)b * C * plane;
@@ -442,41 +462,42 @@ __global__ void __launch_bounds__(kWT_THREADS, 4) k_warp_f32_bwd(int B, int C, i
         warp_stage_async<AL>(sm + ((u + 1) & 1) * kWT_BUF, gyb + (int64_t)c1 * plane, min(C - c1, kWT_CG), H, W, nb);
     }
     cp_async_commit_f();
-    // this unit's source values, loaded while its copies land
-    const int px = X0 + tx;
-    float xv[2][kWT_CG];
+    // this unit's source values, loaded while its copies land: each thread
+    // owns the horizontal pixel pair (px, px + 1) of tile row tr
+    const int px = X0 + 2 * tp, py = Y0 + tr;
+    const bool in0 = px < W && py < H, has1 = in0 && px + 1 < W;
+    float xa[kWT_CG], xc[kWT_CG];
+    {
+      const int o = in0 ? py * W + px : 0;
 #pragma unroll
-    for (int j = 0; j < 2; j++) {
-      const int py = Y0 + ty + 8 * j;
-      const bool in = px < W && py < H;
-      const int o = in ? py * W + px : 0;
-#pragma unroll
-      for (int k = 0; k < kWT_CG; k++) xv[j][k] = (in && k < cn) ? __ldg(xb + (int64_t)(c0 + k) * plane + o) : 0.0f;
+      for (int k = 0; k < kWT_CG; k++) {
+        xa[k] = (in0 && k < cn) ? __ldg(xb + (int64_t)(c0 + k) * plane + o) : 0.0f;
+        xc[k] = (has1 && k < cn) ? __ldg(xb + (int64_t)(c0 + k) * plane + o + 1) : 0.0f;
+      }
     }
     cp_async_wait_prev();
     __syncthreads();
     const int bh = bx.y1 - bx.y0 + 1;
     const float* buf = sm + (u & 1) * kWT_BUF;
+    if (in0) {
+      float acc0[kWT_CG], acc1[kWT_CG];
 #pragma unroll
-    for (int j = 0; j < 2; j++) {
-      const int py = Y0 + ty + 8 * j;
-      if (px >= W || py >= H) continue;
-      float acc[kWT_CG];
-#pragma unroll
-      for (int k = 0; k < kWT_CG; k++) acc[k] = 0.0f;
-      if (!finite) {
-#pragma unroll
-        for (int k = 0; k < kWT_CG; k++) acc[k] = __int_as_float(0x7fc00000);
-      } else if (bx.x1 >= bx.x0) {
+      for (int k = 0; k < kWT_CG; k++) acc0[k] = acc1[k] = finite ? 0.0f : __int_as_float(0x7fc00000);
+      if (finite && bx.x1 >= bx.x0) {
         if (bx.staged)
-          warp_gather_pixel(K, bx, buf, bx.pitch, bh * bx.pitch, bx.x0, bx.y0, px, py, cn, xv[j], acc, S);
+          warp_gather_pair(K, bx, buf, bx.pitch, bh * bx.pitch, bx.x0, bx.y0, px, py, cn, has1, xa, xc, acc0, acc1,
+                           S);
         else
-          warp_gather_pixel(K, bx, gyb + (int64_t)c0 * plane, W, plane, 0, 0, px, py, cn, xv[j], acc, S);
+          warp_gather_pair(K, bx, gyb + (int64_t)c0 * plane, W, plane, 0, 0, px, py, cn, has1, xa, xc, acc0, acc1, S);
       }
       const int o = py * W + px;
 #pragma unroll
-      for (int k = 0; k < kWT_CG; k++)
-        if (k < cn) gxb[(int64_t)(c0 + k) * plane + o] = acc[k];
+      for (int k = 0; k < kWT_CG; k++) {
+        if (k < cn) {
+          gxb[(int64_t)(c0 + k) * plane + o] = acc0[k];
+          if (has1) gxb[(int64_t)(c0 + k) * plane + o + 1] = acc1[k];
+        }
+      }
     }
     __syncthreads();  // buffer (u & 1) is refilled by unit u + 2
   }
