@@ -602,11 +602,9 @@ ALB_D void r_tile_compute(const RImg& k, const RTile& g, int lane, int32_t vcol,
   }
 }
 
-struct RShared {       // dynamic shared memory of k_resize_rows (above the 48 KB static limit)
-  uint8_t box[RWARP][1][RB_Y * RPITCH + 16];   // +16: the last row's tap read past the staged bytes
-  int32_t rowoff[RWARP][1][RB_Y];
-  RImg simg[RWARP][2];
-  RTile stile[RWARP][2];
+struct RShared {       // dynamic shared memory of k_resize_rows: one staging box per warp
+  uint8_t box[RWARP][RB_Y * RPITCH + 16];   // +16: the last row's tap read past the staged bytes
+  int32_t rowoff[RWARP][RB_Y];
 };
 
 template <int MAP>
@@ -630,11 +628,11 @@ __global__ void __launch_bounds__(32 * RWARP) k_resize_rows(Plan plan, ImgList i
     int32_t ccol, crow;
     r_tile_geo<MAP>(k, prm, item, lane, g, ccol, crow);
     __syncwarp();
-    r_tile_stage(k, g, lane, sm.box[w][0], sm.rowoff[w][0]);
+    r_tile_stage(k, g, lane, sm.box[w], sm.rowoff[w]);
     cp_async_commit();
     cp_async_wait<0>();
     __syncwarp();
-    r_tile_compute(k, g, lane, ccol, crow, sm.box[w][0], sm.rowoff[w][0]);
+    r_tile_compute(k, g, lane, ccol, crow, sm.box[w], sm.rowoff[w]);
   }
 }
 
@@ -808,11 +806,9 @@ ALB_D void a_tile_compute(const AImg& k, const ATile& g, int lane, const uint8_t
   }
 }
 
-struct AShared {       // dynamic shared memory of k_warp_affine3
-  uint8_t box[AWARP][1][AB * APITCH + 16];
-  int32_t rowoff[AWARP][1][AB];
-  AImg simg[AWARP][2];
-  ATile stile[AWARP][2];
+struct AShared {       // dynamic shared memory of k_warp_affine3: one staging box per warp
+  uint8_t box[AWARP][AB * APITCH + 16];   // +16: the last row's tap read past the staged bytes
+  int32_t rowoff[AWARP][AB];
 };
 
 __global__ void __launch_bounds__(32 * AWARP, 6) k_warp_affine3(Plan plan, ImgList in, ImgList out, PrmList prm) {
@@ -834,11 +830,11 @@ __global__ void __launch_bounds__(32 * AWARP, 6) k_warp_affine3(Plan plan, ImgLi
     ATile g;
     a_tile_geo(k, item, g);
     __syncwarp();
-    a_tile_stage(k, g, lane, sm.box[w][0], sm.rowoff[w][0]);
+    a_tile_stage(k, g, lane, sm.box[w], sm.rowoff[w]);
     cp_async_commit();
     cp_async_wait<0>();
     __syncwarp();
-    a_tile_compute(k, g, lane, sm.box[w][0], sm.rowoff[w][0]);
+    a_tile_compute(k, g, lane, sm.box[w], sm.rowoff[w]);
   }
 }
 
