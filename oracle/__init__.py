@@ -139,8 +139,8 @@ def _declare(L):
     L.orc_jitter_op.argtypes = [C.c_int, C.c_int]
     L.orc_jitter_op.restype = C.c_int
     dp = P(C.c_double)
-    L.orc_warp_photo_fwd.argtypes = [C.c_int] * 4 + [dp] * 10
-    L.orc_warp_photo_bwd.argtypes = [C.c_int] * 4 + [dp] * 11
+    L.orc_warp_photo_fwd.argtypes = [C.c_int] * 5 + [dp] * 10
+    L.orc_warp_photo_bwd.argtypes = [C.c_int] * 5 + [dp] * 13
 
 
 def _ptr(a: np.ndarray, ctype):
@@ -345,29 +345,43 @@ def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
-def warp_photo_fwd(x, angle, scale, tx, ty, alpha, beta, gamma, want_warped=False):
+def warp_photo_fwd(x, angle, scale, tx, ty, alpha, beta, gamma, want_warped=False, coords=64):
+    """Float warp + photometric forward.  coords=64: source coordinates in
+    float64 (the definition); coords=32: the float32 coordinate class (map
+    entries rounded to float32 once, coordinates by float32 fused
+    multiply-adds), everything else float64."""
+    if coords not in (32, 64):
+        raise ValueError("coords must be 32 or 64")
     x = _f64(x)
     B, Cc, H, W = x.shape
     args = [_f64(a) for a in (angle, scale, tx, ty, alpha, beta, gamma)]
     y = np.zeros_like(x)
     warped = np.zeros_like(x) if want_warped else None
     dp = C.POINTER(C.c_double)
-    lib().orc_warp_photo_fwd(B, Cc, H, W, _ptr(x, C.c_double), *[_ptr(a, C.c_double) for a in args],
+    lib().orc_warp_photo_fwd(B, Cc, H, W, coords, _ptr(x, C.c_double), *[_ptr(a, C.c_double) for a in args],
                              _ptr(warped, C.c_double) if warped is not None else C.cast(None, dp),
                              _ptr(y, C.c_double))
     return (y, warped) if want_warped else y
 
 
-def warp_photo_bwd(x, angle, scale, tx, ty, alpha, beta, gamma, gy):
+def warp_photo_bwd(x, angle, scale, tx, ty, alpha, beta, gamma, gy, coords=64, want_abs=False):
+    """Analytic adjoint: (dx, dparams[B][7]); with want_abs also the sums of
+    the absolute values of each entry's terms, (adx, adparams)."""
+    if coords not in (32, 64):
+        raise ValueError("coords must be 32 or 64")
     x = _f64(x)
     gy = _f64(gy)
     B, Cc, H, W = x.shape
     args = [_f64(a) for a in (angle, scale, tx, ty, alpha, beta, gamma)]
     dx = np.zeros_like(x)
     dparams = np.zeros((B, 7), dtype=np.float64)
-    lib().orc_warp_photo_bwd(B, Cc, H, W, _ptr(x, C.c_double), *[_ptr(a, C.c_double) for a in args],
-                             _ptr(gy, C.c_double), _ptr(dx, C.c_double), _ptr(dparams, C.c_double))
-    return dx, dparams
+    adx = np.zeros_like(x) if want_abs else None
+    adp = np.zeros((B, 7), dtype=np.float64) if want_abs else None
+    nul = C.cast(None, C.POINTER(C.c_double))
+    lib().orc_warp_photo_bwd(B, Cc, H, W, coords, _ptr(x, C.c_double), *[_ptr(a, C.c_double) for a in args],
+                             _ptr(gy, C.c_double), _ptr(dx, C.c_double), _ptr(dparams, C.c_double),
+                             _ptr(adx, C.c_double) if want_abs else nul, _ptr(adp, C.c_double) if want_abs else nul)
+    return (dx, dparams, adx, adp) if want_abs else (dx, dparams)
 
 
 # ---------------------------------------------------------------- chain targets

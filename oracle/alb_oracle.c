@@ -1027,12 +1027,27 @@ EXPORT int orc_chain_image(const orc_params* p, const double mean[3], const doub
 }
 
 /* ======================================================================
- * Differentiable float path, float64 throughout.
+ * Differentiable float path.
  * x: [B][C][H][W]; per image angle (deg), scale, tx, ty (fractions of W, H),
  * alpha, beta, gamma.  w = bilinear warp of x with zero border;
  * z = alpha w + beta; y = clamp(z, 0, 1)^gamma.
+ *
+ * Source coordinates come in two classes (`coords`):
+ *   64: the inverse map evaluated in float64 -- the definition of the warp;
+ *   32: the float32 coordinate class: the six inverse-map entries (computed
+ *       in float64) rounded to float32 once, then
+ *       sx = fma(a00, ox, fma(a01, oy, b0)) and sy = fma(a10, ox, fma(a11, oy, b1))
+ *       as correctly rounded float32 fused multiply-adds.  This is the
+ *       coordinate a float32 implementation of the warp samples at, so its
+ *       floor cells -- and with them the piecewise-bilinear pieces whose
+ *       boundaries gradients cannot cross smoothly -- are the same as the
+ *       implementation's.  Everything after the coordinate (weights, taps,
+ *       photometric step, gradients) stays float64 in both classes.
  * ====================================================================== */
-typedef struct { double a00, a01, a10, a11, b0, b1, cs, sn, s, cx, cy, W, H, txp, typ; } fwarp;
+typedef struct {
+  double a00, a01, a10, a11, b0, b1, cs, sn, s, cx, cy, W, H, txp, typ;
+  float f00, f01, f10, f11, fb0, fb1;   /* the float32 coordinate class */
+} fwarp;
 
 static void fwarp_setup(fwarp* g, double angle, double scale, double tx, double ty, int h, int w) {
   double rad = angle * (M_PI / 180.0);
@@ -1044,6 +1059,19 @@ static void fwarp_setup(fwarp* g, double angle, double scale, double tx, double 
   double ox = g->cx + g->txp, oy = g->cy + g->typ;
   g->b0 = g->cx - (g->a00 * ox + g->a01 * oy);
   g->b1 = g->cy - (g->a10 * ox + g->a11 * oy);
+  g->f00 = (float)g->a00; g->f01 = (float)g->a01; g->f10 = (float)g->a10; g->f11 = (float)g->a11;
+  g->fb0 = (float)g->b0; g->fb1 = (float)g->b1;
+}
+
+/* source coordinate (sx, sy) of output pixel (ox, oy) in coordinate class `coords` */
+static void fwarp_coord(const fwarp* g, int coords, int ox, int oy, double* sx, double* sy) {
+  if (coords == 32) {
+    *sx = (double)fmaf(g->f00, (float)ox, fmaf(g->f01, (float)oy, g->fb0));
+    *sy = (double)fmaf(g->f10, (float)ox, fmaf(g->f11, (float)oy, g->fb1));
+  } else {
+    *sx = g->a00 * ox + g->a01 * oy + g->b0;
+    *sy = g->a10 * ox + g->a11 * oy + g->b1;
+  }
 }
 
 static double tap(const double* img, int h, int w, int64_t x, int64_t y) {
@@ -1051,7 +1079,7 @@ static double tap(const double* img, int h, int w, int64_t x, int64_t y) {
   return img[y * w + x];
 }
 
-EXPORT void orc_warp_photo_fwd(int B, int C, int H, int W, const double* x,
+EXPORT void orc_warp_photo_fwd(int B, int C, int H, int W, int coords, const double* x,
                                const double* angle, const double* scale, const double* tx, const double* ty,
                                const double* alpha, const double* beta, const double* gamma,
                                double* warped, double* y) {
@@ -1061,8 +1089,8 @@ EXPORT void orc_warp_photo_fwd(int B, int C, int H, int W, const double* x,
       const double* img = x + ((size_t)b * C + c) * H * W;
       for (int oy = 0; oy < H; oy++)
         for (int ox = 0; ox < W; ox++) {
-          double sx = g.a00 * ox + g.a01 * oy + g.b0;
-          double sy = g.a10 * ox + g.a11 * oy + g.b1;
+          double sx, sy;
+          fwarp_coord(&g, coords, ox, oy, &sx, &sy);
           double fx0 = floor(sx), fy0 = floor(sy);
           double fx = sx - fx0, fy = sy - fy0;
           int64_t ix = (int64_t)fx0, iy = (int64_t)fy0;
@@ -1078,23 +1106,33 @@ EXPORT void orc_warp_photo_fwd(int B, int C, int H, int W, const double* x,
   }
 }
 
-/* Analytic adjoint of orc_warp_photo_fwd.  dparams: [B][7] =
- * (d angle [per degree], d scale, d tx, d ty, d alpha, d beta, d gamma). */
-EXPORT void orc_warp_photo_bwd(int B, int C, int H, int W, const double* x,
+/* Analytic adjoint of orc_warp_photo_fwd (same coordinate class).
+ * dparams: [B][7] = (d angle [per degree], d scale, d tx, d ty, d alpha,
+ * d beta, d gamma).  Optional (NULL = not wanted): adx [B][C][H][W] and
+ * adparams [B][7] receive the sums of the absolute values of the terms each
+ * gradient entry is a sum of -- for a parameter of the map, the terms are
+ * the products of the coordinate partials dL/dsx, dL/dsy with each part of
+ * the coordinate's derivative, taken apart as the map's rotation and
+ * translation parts -- the scale against which the rounding error of any
+ * finite-precision evaluation of the same sums is measured. */
+EXPORT void orc_warp_photo_bwd(int B, int C, int H, int W, int coords, const double* x,
                                const double* angle, const double* scale, const double* tx, const double* ty,
                                const double* alpha, const double* beta, const double* gamma,
-                               const double* gy, double* dx, double* dparams) {
+                               const double* gy, double* dx, double* dparams, double* adx, double* adparams) {
   memset(dx, 0, sizeof(double) * (size_t)B * C * H * W);
+  if (adx) memset(adx, 0, sizeof(double) * (size_t)B * C * H * W);
   for (int b = 0; b < B; b++) {
     fwarp g; fwarp_setup(&g, angle[b], scale[b], tx[b], ty[b], H, W);
     double dang = 0, dsc = 0, dtx = 0, dty = 0, dal = 0, dbe = 0, dga = 0;
+    double aang = 0, asc = 0, atx = 0, aty = 0, aal = 0, abe = 0, aga = 0;
     for (int c = 0; c < C; c++) {
       const double* img = x + ((size_t)b * C + c) * H * W;
       double* dimg = dx + ((size_t)b * C + c) * H * W;
+      double* aimg = adx ? adx + ((size_t)b * C + c) * H * W : NULL;
       for (int oy = 0; oy < H; oy++)
         for (int ox = 0; ox < W; ox++) {
-          double sx = g.a00 * ox + g.a01 * oy + g.b0;
-          double sy = g.a10 * ox + g.a11 * oy + g.b1;
+          double sx, sy;
+          fwarp_coord(&g, coords, ox, oy, &sx, &sy);
           double fx0 = floor(sx), fy0 = floor(sy);
           double fx = sx - fx0, fy = sy - fy0;
           int64_t ix = (int64_t)fx0, iy = (int64_t)fy0;
@@ -1110,12 +1148,18 @@ EXPORT void orc_warp_photo_bwd(int B, int C, int H, int W, const double* x,
           dga += g_out * zg * log(z);
           dal += gz * v;
           dbe += gz;
+          aga += fabs(g_out * zg * log(z));
+          aal += fabs(gz * v);
+          abe += fabs(gz);
           double gw = gz * alpha[b];
           /* image adjoint: scatter to the in-range taps */
-          if (ix >= 0 && ix < W && iy >= 0 && iy < H) dimg[iy * W + ix] += gw * (1 - fx) * (1 - fy);
-          if (ix + 1 >= 0 && ix + 1 < W && iy >= 0 && iy < H) dimg[iy * W + ix + 1] += gw * fx * (1 - fy);
-          if (ix >= 0 && ix < W && iy + 1 >= 0 && iy + 1 < H) dimg[(iy + 1) * W + ix] += gw * (1 - fx) * fy;
-          if (ix + 1 >= 0 && ix + 1 < W && iy + 1 >= 0 && iy + 1 < H) dimg[(iy + 1) * W + ix + 1] += gw * fx * fy;
+          double wk[4] = {(1 - fx) * (1 - fy), fx * (1 - fy), (1 - fx) * fy, fx * fy};
+          int64_t tx_[4] = {ix, ix + 1, ix, ix + 1}, ty_[4] = {iy, iy, iy + 1, iy + 1};
+          for (int k = 0; k < 4; k++)
+            if (tx_[k] >= 0 && tx_[k] < W && ty_[k] >= 0 && ty_[k] < H) {
+              dimg[ty_[k] * W + tx_[k]] += gw * wk[k];
+              if (aimg) aimg[ty_[k] * W + tx_[k]] += fabs(gw * wk[k]);
+            }
           /* coordinate partials */
           double dsx = gw * ((1 - fy) * (v10 - v00) + fy * (v11 - v01));
           double dsy = gw * ((1 - fx) * (v01 - v00) + fx * (v11 - v10));
@@ -1126,11 +1170,20 @@ EXPORT void orc_warp_photo_bwd(int B, int C, int H, int W, const double* x,
           dsc += dsx * (-(sx - g.cx) / g.s) + dsy * (-(sy - g.cy) / g.s);
           dtx += dsx * (-g.cs * g.W / g.s) + dsy * (-g.sn * g.W / g.s);
           dty += dsx * (g.sn * g.H / g.s) + dsy * (-g.cs * g.H / g.s);
+          aang += (fabs(dsx) * (fabs(g.sn * xp) + fabs(g.cs * yp)) + fabs(dsy) * (fabs(g.cs * xp) + fabs(g.sn * yp))) / g.s;
+          asc += (fabs(dsx) * fabs(sx - g.cx) + fabs(dsy) * fabs(sy - g.cy)) / g.s;
+          atx += (fabs(dsx) * fabs(g.cs) + fabs(dsy) * fabs(g.sn)) * g.W / g.s;
+          aty += (fabs(dsx) * fabs(g.sn) + fabs(dsy) * fabs(g.cs)) * g.H / g.s;
         }
     }
     double* dp = dparams + 7 * (size_t)b;
     dp[0] = dang * (M_PI / 180.0); dp[1] = dsc; dp[2] = dtx; dp[3] = dty;
     dp[4] = dal; dp[5] = dbe; dp[6] = dga;
+    if (adparams) {
+      double* ap = adparams + 7 * (size_t)b;
+      ap[0] = aang * (M_PI / 180.0); ap[1] = asc; ap[2] = atx; ap[3] = aty;
+      ap[4] = aal; ap[5] = abe; ap[6] = aga;
+    }
   }
 }
 

@@ -285,3 +285,100 @@ def test_float_gradients_match_finite_differences():
         xm[b, c, yy, xx] -= hstep
         fd = (loss(xp, p) - loss(xm, p)) / (2 * hstep)
         assert abs(fd - dx[b, c, yy, xx]) <= 1e-3 * max(1e-3, abs(fd))
+
+
+# ------------------------------------------------ float32 coordinate class
+def coord_bound(p, b, H, W):
+    """First-order bound on |s32 - s64| for every output pixel of image b: the
+    six map entries are rounded to float32 once (relative error <= u each)
+    and each of the two fused multiply-adds rounds once, so
+    |ds| <= u (|a00| (W-1) + |a01| (H-1) + |b0| + |a01 (H-1) + b0| + |s|)
+    <= 3 u (|a00| (W-1) + |a01| (H-1) + |b0|), u = 2^-24 (same for sy)."""
+    u = 2.0 ** -24
+    t = np.deg2rad(p["angle"][b])
+    s = p["scale"][b]
+    cx, cy = (W - 1) / 2, (H - 1) / 2
+    a00, a01 = np.cos(t) / s, -np.sin(t) / s
+    ox, oy = cx + p["tx"][b] * W, cy + p["ty"][b] * H
+    b0 = cx - (a00 * ox + a01 * oy)
+    b1 = cy - (-a01 * ox + a00 * oy)
+    m = abs(a00) * (W - 1) + abs(a01) * (H - 1)
+    return 3 * u * (m + max(abs(b0), abs(b1))) * 1.001
+
+
+def test_float32_coordinates_exact_where_representable():
+    # identity and integer shifts: every map entry and coordinate is exact in
+    # float32, so the two classes give identical outputs
+    B, C, H, W = 1, 2, 10, 12
+    x = np.random.default_rng(1).uniform(0.1, 0.9, (B, C, H, W))
+    for tx, ty in ((0.0, 0.0), (3 / W, -2 / H), (-5 / W, 4 / H)):
+        p = fparams(B, ident=True)
+        p["tx"], p["ty"] = np.array([tx]), np.array([ty])
+        assert np.array_equal(O.warp_photo_fwd(x, **p, coords=32), O.warp_photo_fwd(x, **p, coords=64))
+
+
+@pytest.mark.parametrize("H,W", [(512, 512), (333, 500), (37, 53)])
+def test_float32_coordinates_within_rounding_bound(H, W):
+    """The float32 class samples within the coordinate rounding bound of the
+    float64 map: with inputs in [0,1] the bilinear value moves by at most
+    |dsx| + |dsy| (slope <= 1 per pixel along each axis)."""
+    B, C = 2, 1
+    x = np.random.default_rng(4).uniform(0, 1, (B, C, H, W))
+    p = fparams(B, seed=9)
+    p.update(alpha=np.ones(B), beta=np.zeros(B), gamma=np.ones(B))
+    _, w32 = O.warp_photo_fwd(x, **p, coords=32, want_warped=True)
+    _, w64 = O.warp_photo_fwd(x, **p, coords=64, want_warped=True)
+    for b in range(B):
+        d = np.abs(w32[b] - w64[b]).max()
+        assert d <= 2 * coord_bound(p, b, H, W), (b, d, coord_bound(p, b, H, W))
+    assert np.abs(w32 - w64).max() > 0          # the classes do differ
+
+
+def test_float32_coordinates_adjoint_dot_product():
+    """The float32 class is linear in x for an affine photometric step with z
+    inside (0,1): <y - beta, g> == <x, dx> / alpha * alpha."""
+    B, C, H, W = 2, 2, 19, 23
+    rng = np.random.default_rng(5)
+    x = rng.uniform(0.0, 1.0, (B, C, H, W))
+    p = fparams(B, seed=8)
+    p.update(alpha=np.full(B, 0.5), beta=np.full(B, 0.25), gamma=np.ones(B))
+    g = rng.normal(0, 1, x.shape)
+    y = O.warp_photo_fwd(x, **p, coords=32)
+    dx, _ = O.warp_photo_bwd(x, **p, gy=g, coords=32)
+    lhs = float(((y - 0.25) * g).sum())
+    rhs = float((x * dx).sum())
+    assert abs(lhs - rhs) < 1e-10 * max(1.0, abs(lhs))
+
+
+def test_float32_coordinates_gradients_follow_the_float64_adjoint():
+    """On a 16x16 image no sample changes cell between the classes, so the
+    float32-class gradients equal the (finite-difference pinned) float64
+    ones up to the coordinate rounding."""
+    B, C, H, W = 2, 3, 16, 16
+    rng = np.random.default_rng(11)
+    x = rng.uniform(0.15, 0.85, (B, C, H, W))
+    p = fparams(B, seed=13)
+    g = rng.normal(0, 1, x.shape)
+    dx64, dp64 = O.warp_photo_bwd(x, **p, gy=g)
+    dx32, dp32 = O.warp_photo_bwd(x, **p, gy=g, coords=32)
+    assert np.abs(dx32 - dx64).max() <= 1e-5
+    assert np.all(np.abs(dp32 - dp64) <= 1e-5 * np.abs(dp64) + 1e-6), (dp32, dp64)
+
+
+def test_absolute_term_sums():
+    """The sums of absolute term values bound the gradients (triangle
+    inequality) and equal them where every term is non-negative: with g >= 0
+    and alpha > 0 the input adjoint, d alpha and d beta have only
+    non-negative terms."""
+    B, C, H, W = 2, 3, 21, 17
+    rng = np.random.default_rng(12)
+    x = rng.uniform(0.0, 1.0, (B, C, H, W))
+    p = fparams(B, seed=14)
+    g = rng.normal(0, 1, x.shape)
+    for coords in (32, 64):
+        dx, dp, adx, adp = O.warp_photo_bwd(x, **p, gy=g, coords=coords, want_abs=True)
+        assert np.all(adx >= np.abs(dx) - 1e-12) and np.all(adp >= np.abs(dp) - 1e-12)
+        assert np.all(adp[:, :4] > 0)
+        dx, dp, adx, adp = O.warp_photo_bwd(x, **p, gy=np.abs(g), coords=coords, want_abs=True)
+        assert np.allclose(adx, dx, rtol=1e-12, atol=0)
+        assert np.allclose(adp[:, 4:6], dp[:, 4:6], rtol=1e-12, atol=0)
