@@ -1,0 +1,198 @@
+"""GPU parity at the workloads' full sizes, in the launch configurations the
+benchmark times.
+
+* The per-transform suite: 2000 images, H, W ~ U[333, 500], parameters
+  sampled on the device, one ragged launch per transform over the whole
+  batch; a sample of images (the smallest, the largest and a spread) is
+  compared with the oracle one by one, for all 15 transforms.
+* The same 15 transforms on images of 512-1024 px (the size class of the
+  HBM target): 512 images in one launch, sampled outputs compared; and five
+  images of 512-1024 px with 20-class masks and 1-50 boxes each, every pixel
+  compared.
+* The detection workload: 256 images of 1024 x 1024 with 20-class masks and
+  1-50 boxes through ShiftScaleRotate -> Resize 512 -> HFlip (p = 0.5),
+  device-sampled, one ragged launch per step; four images' images, masks and
+  boxes compared after the whole chain.
+
+Images, masks and Q5 resampling are bit-exact; ShiftHSV within 1 LSB on at
+most 0.1 % of bytes; boxes within 1e-4 px with the same kept set."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from helpers import cfg_to_lib, same_params, suite_cfgs, to_lib
+
+from paper_1809_06839_gb300 import alb, synth
+from paper_1809_06839_gb300.ragged import DeviceBatch, mask_output_batch, output_batch
+
+pytestmark = pytest.mark.gpu
+SEED = 1809
+
+
+@pytest.fixture(scope="module")
+def dev():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    alb.load()
+    return torch.device("cuda")
+
+
+def hsv_ok(got, ref):
+    d = np.abs(got.astype(np.int32) - ref.astype(np.int32))
+    return d.max() <= 1 and (d > 0).mean() <= 1e-3
+
+
+def check_image(tid, got, ref, what):
+    assert got.shape == ref.shape, what
+    if tid == O.SHIFT_HSV:
+        assert hsv_ok(got, ref), what
+    else:
+        assert np.array_equal(got, ref), (what, int((got != ref).sum()))
+
+
+def sample_indices(sizes, k):
+    area = np.array([h * w for h, w in sizes])
+    idx = {int(area.argmin()), int(area.argmax()), 0, len(sizes) - 1}
+    idx.update(int(i) for i in np.linspace(0, len(sizes) - 1, k).round())
+    return sorted(idx)
+
+
+@pytest.fixture(scope="module")
+def suite_batch(dev):
+    sizes = synth.uniform_sizes(2000, 333, 500, seed=SEED)
+    return sizes, DeviceBatch(synth.ragged_noise(sizes, seed=SEED, device=dev))
+
+
+@pytest.fixture(scope="module")
+def large_batch(dev):
+    sizes = synth.uniform_sizes(512, 512, 1024, seed=SEED)
+    return sizes, DeviceBatch(synth.ragged_noise(sizes, seed=SEED, device=dev))
+
+
+def device_sampled_launch(dev, batch, name, oc, k):
+    """One suite transform as the benchmark runs it: device-sampled records,
+    one ragged launch over the whole batch; returns the sampled images."""
+    sizes, inp = batch
+    n = len(sizes)
+    cfg = cfg_to_lib(oc, alb)
+    pdev = torch.zeros(n * 232, dtype=torch.uint8, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    alb.alb_sample_params_batch(cfg, SEED, oc.tid, 0, n, inp.dev, pdev, status)
+    recs = alb.params_from_device(pdev)
+    out = output_batch(recs, inp.rb.shapes, dev)
+    ws = alb.workspace(alb.alb_workspace_size(oc.tid, n), dev)
+    alb.alb_apply_ragged(oc.tid, n, pdev, inp.dev, out.dev, ws=ws, dev_status=status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0, name
+    res = []
+    for i in sample_indices(sizes, k):
+        h, w = sizes[i]
+        op = O.sample_params(oc, SEED, oc.tid, i, h, w)
+        assert same_params(op, recs[i], rel_m=1e-12) is None, (name, i)
+        res.append((i, op, inp.rb.image(i).cpu().numpy(), out.rb.image(i).cpu().numpy()))
+    del out, ws
+    return res
+
+
+@pytest.mark.parametrize("name", sorted(suite_cfgs()))
+def test_suite_launch_full_size(dev, suite_batch, name):
+    oc = suite_cfgs()[name]
+    for i, op, img, got in device_sampled_launch(dev, suite_batch, name, oc, 10):
+        check_image(oc.tid, got, O.apply_image(op, img), (name, i))
+
+
+@pytest.mark.parametrize("name", sorted(suite_cfgs()))
+def test_large_suite_launch_full_size(dev, large_batch, name):
+    oc = suite_cfgs()[name]
+    for i, op, img, got in device_sampled_launch(dev, large_batch, name, oc, 5):
+        check_image(oc.tid, got, O.apply_image(op, img), (name, i))
+
+
+LARGE_SIZES = [(512, 512), (1024, 1024), (771, 613), (1000, 517), (600, 1024)]
+
+
+@pytest.mark.parametrize("name", sorted(suite_cfgs()))
+def test_large_images_with_masks_and_boxes(dev, name):
+    """Every pixel of five 512-1024 px images, their 20-class masks and their
+    1-50 boxes, oracle-sampled records."""
+    oc = suite_cfgs()[name]
+    sizes = LARGE_SIZES
+    n = len(sizes)
+    rb = synth.ragged_noise(sizes, seed=7, device=dev)
+    masks = synth.ragged_masks(sizes, seed=7, device=dev)
+    ops = [O.sample_params(oc, 7, oc.tid, i, h, w) for i, (h, w) in enumerate(sizes)]
+    lps = [to_lib(p, alb) for p in ops]
+    din, dmi = DeviceBatch(rb), DeviceBatch(masks)
+    dout, dmo = output_batch(lps, rb.shapes, dev), mask_output_batch(lps, masks.shapes, dev)
+    cap = 50
+    boxes = np.zeros((n, cap, 4), np.float32)
+    nb = np.zeros(n, np.int32)
+    for i, (h, w) in enumerate(sizes):
+        b = synth.random_boxes(h, w, i, 7)[:cap]
+        boxes[i, :len(b)] = b
+        nb[i] = len(b)
+    bd, nbd = torch.from_numpy(boxes).to(dev), torch.from_numpy(nb).to(dev)
+    bo, nbo = torch.zeros_like(bd), torch.zeros_like(nbd)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    alb.alb_apply_ragged(oc.tid, n, alb.params_to_device(lps, dev), din.dev, dout.dev, dmi.dev, dmo.dev, bd, nbd, cap,
+                         bo, nbo, alb.workspace(alb.alb_workspace_size(oc.tid, n), dev), status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    bo, nbo = bo.cpu().numpy(), nbo.cpu().numpy()
+    for i, (h, w) in enumerate(sizes):
+        check_image(oc.tid, dout.rb.image(i).cpu().numpy(), O.apply_image(ops[i], rb.image(i).cpu().numpy()),
+                    (name, i))
+        mref = O.apply_mask(ops[i], masks.image(i).cpu().numpy())
+        assert np.array_equal(dmo.rb.image(i).cpu().numpy(), mref), (name, "mask", i)
+        bref = O.apply_boxes(ops[i], h, w, boxes[i, :nb[i]])
+        assert nbo[i] == len(bref), (name, "boxes", i)
+        assert np.abs(bo[i, :nbo[i]] - bref).max(initial=0) <= 1e-4, (name, "boxes", i)
+
+
+def test_detection_workload_full_size(dev):
+    """256 x 1024^2 images + 20-class masks + 1-50 boxes, SSR -> Resize 512 ->
+    HFlip p=0.5, each step one device-sampled ragged launch over the batch."""
+    n, hw, cap = 256, 1024, 50
+    sizes = [(hw, hw)] * n
+    img = DeviceBatch(synth.ragged_noise(sizes, seed=SEED, device=dev))
+    msk = DeviceBatch(synth.ragged_masks(sizes, seed=SEED, device=dev))
+    boxes = np.zeros((n, cap, 4), np.float32)
+    nb = np.zeros(n, np.int32)
+    for i in range(n):
+        b = synth.random_boxes(hw, hw, i, SEED)
+        boxes[i, :len(b)] = b
+        nb[i] = len(b)
+    steps = [O.make_cfg(O.SHIFT_SCALE_ROTATE, lo=(-0.0625, 0.9, -45.0), hi=(0.0625, 1.1, 45.0)),
+             O.make_cfg(O.RESIZE, out_h=512, out_w=512), O.make_cfg(O.HFLIP, p=0.5)]
+    pick = [0, 1, 137, 255]
+    ref_img = {i: img.rb.image(i).cpu().numpy() for i in pick}
+    ref_msk = {i: msk.rb.image(i).cpu().numpy() for i in pick}
+    ref_box = {i: boxes[i, :nb[i]].copy() for i in pick}
+    cur, curm = img, msk
+    bcur, ncur = torch.from_numpy(boxes).to(dev), torch.from_numpy(nb).to(dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    for k, oc in enumerate(steps):
+        pdev = torch.zeros(n * 232, dtype=torch.uint8, device=dev)
+        alb.alb_sample_params_batch(cfg_to_lib(oc, alb), SEED, 300 + k, 0, n, cur.dev, pdev, status)
+        recs = alb.params_from_device(pdev)
+        nxt = output_batch(recs, cur.rb.shapes, dev)
+        nxtm = mask_output_batch(recs, curm.rb.shapes, dev)
+        bo, no = torch.zeros_like(bcur), torch.zeros_like(ncur)
+        alb.alb_apply_ragged(oc.tid, n, pdev, cur.dev, nxt.dev, curm.dev, nxtm.dev, bcur, ncur, cap, bo, no,
+                             alb.workspace(alb.alb_workspace_size(oc.tid, n), dev), status)
+        torch.cuda.synchronize()
+        assert int(status.item()) == 0, k
+        for i in pick:
+            h, w = ref_img[i].shape[:2]
+            op = O.sample_params(oc, SEED, 300 + k, i, h, w)
+            assert same_params(op, recs[i], rel_m=1e-12) is None, (k, i)
+            ref_box[i] = O.apply_boxes(op, h, w, ref_box[i])
+            ref_img[i] = O.apply_image(op, ref_img[i])
+            ref_msk[i] = O.apply_mask(op, ref_msk[i])
+        cur, curm, bcur, ncur = nxt, nxtm, bo, no
+    bo, no = bcur.cpu().numpy(), ncur.cpu().numpy()
+    for i in pick:
+        assert np.array_equal(cur.rb.image(i).cpu().numpy(), ref_img[i]), ("image", i)
+        assert np.array_equal(curm.rb.image(i).cpu().numpy(), ref_msk[i]), ("mask", i)
+        assert no[i] == len(ref_box[i]), ("boxes", i)
+        assert np.abs(bo[i, :no[i]] - ref_box[i]).max(initial=0) <= 1e-4, ("boxes", i)

@@ -11,6 +11,7 @@ import torch
 from scipy import ndimage
 
 import oracle as O
+from tolerances import coord_bound
 from paper_1809_06839_gb300 import synth
 
 
@@ -288,24 +289,6 @@ def test_float_gradients_match_finite_differences():
 
 
 # ------------------------------------------------ float32 coordinate class
-def coord_bound(p, b, H, W):
-    """First-order bound on |s32 - s64| for every output pixel of image b: the
-    six map entries are rounded to float32 once (relative error <= u each)
-    and each of the two fused multiply-adds rounds once, so
-    |ds| <= u (|a00| (W-1) + |a01| (H-1) + |b0| + |a01 (H-1) + b0| + |s|)
-    <= 3 u (|a00| (W-1) + |a01| (H-1) + |b0|), u = 2^-24 (same for sy)."""
-    u = 2.0 ** -24
-    t = np.deg2rad(p["angle"][b])
-    s = p["scale"][b]
-    cx, cy = (W - 1) / 2, (H - 1) / 2
-    a00, a01 = np.cos(t) / s, -np.sin(t) / s
-    ox, oy = cx + p["tx"][b] * W, cy + p["ty"][b] * H
-    b0 = cx - (a00 * ox + a01 * oy)
-    b1 = cy - (-a01 * ox + a00 * oy)
-    m = abs(a00) * (W - 1) + abs(a01) * (H - 1)
-    return 3 * u * (m + max(abs(b0), abs(b1))) * 1.001
-
-
 def test_float32_coordinates_exact_where_representable():
     # identity and integer shifts: every map entry and coordinate is exact in
     # float32, so the two classes give identical outputs
