@@ -231,7 +231,9 @@ ALB_API alb_status alb_apply_ragged(int32_t tid, int32_t n, const alb_params* pa
  * static 8 MiB device array inside the library (held by every GPU that loads
  * the library until exit); at most 2048 images per call, more returns
  * ALB_ECAPACITY.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) and should come before any stream capture.
+ * address (cudaGetSymbolAddress) and should come before any stream capture;
+ * the address is cached per CUDA context, so after cudaDeviceReset the next
+ * call looks it up again (and should also come before any capture).
  * All calls share the array: calls that overlap on the GPU race and must be
  * ordered by the caller.  Arguments as in alb_apply_ragged; allocates nothing. */
 ALB_API alb_status alb_apply_ragged_static(int32_t tid, int32_t n, const alb_params* params_dev,
@@ -310,6 +312,26 @@ ALB_API alb_status alb_autotune_batch(const alb_chain_cfg* cfg, int32_t n, const
                               const alb_image* in_dev, void* out_bf16, void* workspace,
                               size_t workspace_bytes, int32_t reps, alb_chain_cfg* best, void* stream);
 
+/* The schedule cache of alb_autotune_batch, read and persisted (no
+ * counterpart in the paper).  alb_autotune_lookup: the cached schedule of
+ * (current device, cfg->out_h, cfg->out_w, cfg->jitter, ceil(log2 n)) in
+ * *best (a copy of *cfg with tile_h, ctas_per_sm set) and *found = 1, or
+ * *found = 0 and *best = *cfg; host pointers.  alb_autotune_save: writes
+ * every cached entry to the JSON file `path` (written to path.tmp, then
+ * renamed), keyed by device name and SM count:
+ *   {"format": "alb-autotune-1", "entries": [{"device": "...", "sms": N,
+ *    "out_h": H, "out_w": W, "jitter": J, "bucket": K, "rows_per_item": R,
+ *    "ctas_per_sm": C}, ...]}
+ * alb_autotune_load: reads such a file, checks every entry (ALB_EINVAL, and
+ * nothing loaded, if the file is missing, malformed or out of range), then
+ * stores the entries whose device name and SM count match a device of this
+ * process, replacing entries of the same key; *n_loaded receives their
+ * number.  ALB_ECUDA when a device query fails.  None of them launches
+ * work or allocates device memory. */
+ALB_API alb_status alb_autotune_lookup(const alb_chain_cfg* cfg, int32_t n, alb_chain_cfg* best, int32_t* found);
+ALB_API alb_status alb_autotune_save(const char* path);
+ALB_API alb_status alb_autotune_load(const char* path, int32_t* n_loaded);
+
 /* ------------------------------------------------------------------ */
 /* Differentiable float32 path.  x: DEVICE float [B][C][H][W] (NCHW, values
  * nominally in [0,1]); prm: DEVICE float [B][4] = (angle in degrees, scale,
@@ -335,6 +357,23 @@ ALB_API alb_status alb_photometric_f32_fwd(int32_t B, int32_t C, int32_t H, int3
 ALB_API alb_status alb_photometric_f32_bwd(int32_t B, int32_t C, int32_t H, int32_t W, const float* x,
                                    const float* prm, const float* gy, float* gx, float* gprm,
                                    void* workspace, size_t workspace_bytes, void* stream);
+
+/* ------------------------------------------------------------------ */
+/* Diagnostic (no counterpart in the paper: part of the library's failure
+ * handling).  The bulk-copy kernels wait on their shared-memory barriers
+ * with an iteration limit; when a wait gives up they wait (bounded again)
+ * for the copies they had issued and not yet consumed, record ALB_ETIMEOUT
+ * in their status word and stop.  This call runs that path on purpose: one
+ * thread issues two 16-byte bulk loads from src_dev[0, 32) into two stages,
+ * announces a third copy that it never issues, waits for the third with at
+ * most `spins` tries (1 <= spins <= 2^22), drains the two real copies,
+ * records ALB_ETIMEOUT in *dev_status (device int32, set only if it is 0)
+ * and copies the two drained stages to out_dev[0, 32).  A caller sees a
+ * working timeout path as *dev_status == ALB_ETIMEOUT and out == src.
+ * src_dev must be 16-byte aligned (ALB_EALIGN otherwise); all pointers are
+ * device pointers owned by the caller.  Asynchronous on `stream`. */
+ALB_API alb_status alb_selftest_bounded_wait(int32_t spins, const void* src_dev, void* out_dev,
+                                             int32_t* dev_status, void* stream);
 
 /* ------------------------------------------------------------------ */
 /* Thread-local message for the last failing call on this thread. */

@@ -102,6 +102,14 @@ def _declare(L):
     L.alb_apply_ragged.restype = st
     L.alb_apply_ragged_static.argtypes = [C.c_int32, C.c_int32, vp, vp, vp, vp, vp]
     L.alb_apply_ragged_static.restype = st
+    L.alb_selftest_bounded_wait.argtypes = [C.c_int32, vp, vp, vp, vp]
+    L.alb_selftest_bounded_wait.restype = st
+    L.alb_autotune_lookup.argtypes = [P(ChainCfg), C.c_int32, P(ChainCfg), P(C.c_int32)]
+    L.alb_autotune_lookup.restype = st
+    L.alb_autotune_save.argtypes = [C.c_char_p]
+    L.alb_autotune_save.restype = st
+    L.alb_autotune_load.argtypes = [C.c_char_p, P(C.c_int32)]
+    L.alb_autotune_load.restype = st
     L.alb_batch_workspace_size.argtypes = [P(ChainCfg), C.c_int32, C.c_int32]
     L.alb_batch_workspace_size.restype = C.c_size_t
     L.alb_apply_batch.argtypes = [P(ChainCfg), C.c_int32, vp, vp, vp, C.c_int32, vp, C.c_size_t, vp, vp]
@@ -322,6 +330,29 @@ def alb_apply_ragged_static(tid: int, n: int, params_dev, in_dev, out_dev, dev_s
     device memory; scratch is a static array inside libalb (<= 2048 images)."""
     _check(load().alb_apply_ragged_static(tid, n, _ptr(params_dev), _ptr(in_dev), _ptr(out_dev), _ptr(dev_status),
                                           _stream(stream)))
+
+
+def alb_selftest_bounded_wait(spins: int, src_dev, out_dev, dev_status, stream=None):
+    """Runs the bulk-copy kernels' timeout path on purpose (see alb.h)."""
+    _check(load().alb_selftest_bounded_wait(spins, _ptr(src_dev), _ptr(out_dev), _ptr(dev_status), _stream(stream)))
+
+
+def alb_autotune_lookup(cfg: ChainCfg, n: int):
+    """The cached fused schedule for (current device, cfg, n), or None."""
+    best = ChainCfg()
+    found = C.c_int32(0)
+    _check(load().alb_autotune_lookup(C.byref(cfg), n, C.byref(best), C.byref(found)))
+    return best if found.value else None
+
+
+def alb_autotune_save(path: str):
+    _check(load().alb_autotune_save(os.fsencode(path)))
+
+
+def alb_autotune_load(path: str) -> int:
+    n = C.c_int32(0)
+    _check(load().alb_autotune_load(os.fsencode(path), C.byref(n)))
+    return n.value
 
 
 def alb_batch_workspace_size(cfg: ChainCfg, n: int, mode: int) -> int:

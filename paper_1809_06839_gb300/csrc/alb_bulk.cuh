@@ -44,9 +44,10 @@ ALB_D bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait for the phase with the given parity; false when it gave up.
-ALB_D bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (uint32_t i = 0; i < kMbarSpinLimit; i++) {
+// Bounded wait for the phase with the given parity (at most `limit` tries,
+// each followed by a short sleep); false when it gave up.
+ALB_D bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit = kMbarSpinLimit) {
+  for (uint32_t i = 0; i < limit; i++) {
     if (mbar_try_wait(bar, parity)) return true;
     __nanosleep(64);
   }

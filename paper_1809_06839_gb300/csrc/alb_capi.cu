@@ -7,6 +7,7 @@
 
 #include "alb_common.cuh"
 #include "alb_kernels.cuh"
+#include "alb_bulk.cuh"
 
 namespace alb {
 
@@ -228,4 +229,14 @@ extern "C" alb_status alb_apply_ragged(int32_t tid, int32_t n, const alb_params*
   return run_ragged(tid, n, prm, li, lo, mask_in_dev ? &mi : nullptr, mask_out_dev ? &mo : nullptr, boxes_dev,
                     n_boxes_dev, box_cap, 0, boxes_out_dev, n_boxes_out_dev, workspace, workspace_bytes, dev_status,
                     (cudaStream_t)stream);
+}
+
+extern "C" alb_status alb_selftest_bounded_wait(int32_t spins, const void* src_dev, void* out_dev,
+                                                int32_t* dev_status, void* stream) {
+  ALB_REQUIRE(spins >= 1 && (uint32_t)spins <= kMbarSpinLimit, ALB_EINVAL,
+              "alb_selftest_bounded_wait: spins %d outside [1, %u]", spins, kMbarSpinLimit);
+  ALB_REQUIRE(src_dev && out_dev && dev_status, ALB_EINVAL, "alb_selftest_bounded_wait: null argument");
+  ALB_REQUIRE(((uintptr_t)src_dev & 15) == 0, ALB_EALIGN, "alb_selftest_bounded_wait: src must be 16-byte aligned");
+  return launch_wait_selftest((uint32_t)spins, (const uint8_t*)src_dev, (uint8_t*)out_dev, dev_status,
+                              (cudaStream_t)stream);
 }

@@ -12,7 +12,9 @@
 // Both modes call the same __device__ step functions, so outputs are identical.
 #include <cuda_bf16.h>
 
+#include <cstdio>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "alb_common.cuh"
@@ -625,6 +627,121 @@ static void tune_store(int32_t dev, const alb_chain_cfg& cfg, int32_t n, int32_t
   g_tune.push_back(TuneEntry{dev, cfg.out_h, cfg.out_w, cfg.jitter, bk, band, per_sm});
 }
 
+// ---- persistence of the schedule cache (JSON), keyed by device name and SM
+// count instead of the process-local ordinal:
+//   {"format": "alb-autotune-1", "entries": [{"device": "...", "sms": 152,
+//    "out_h": 224, "out_w": 224, "jitter": 0, "bucket": 12,
+//    "rows_per_item": 32, "ctas_per_sm": 6}, ...]}
+struct TuneRecord {
+  std::string device;
+  int32_t sms = -1, oh = -1, ow = -1, jitter = -1, bucket = -1, band = -1, per_sm = -1;
+};
+
+static bool device_key(int dev, std::string& name, int32_t& sms) {
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return false;
+  name.clear();
+  for (const char* c = prop.name; *c && name.size() < 255; c++) name += (*c == '"' || *c == '\\') ? '_' : *c;
+  sms = prop.multiProcessorCount;
+  return true;
+}
+
+// A small reader for the format above: an object whose "entries" member is an
+// array of flat objects with string or integer members.  Returns false on
+// anything else.
+struct JsonReader {
+  const std::string& t;
+  size_t i = 0;
+  explicit JsonReader(const std::string& text) : t(text) {}
+  void ws() { while (i < t.size() && (t[i] == ' ' || t[i] == '\n' || t[i] == '\r' || t[i] == '\t')) i++; }
+  bool lit(char c) { ws(); if (i < t.size() && t[i] == c) { i++; return true; } return false; }
+  bool str(std::string& out) {
+    ws();
+    if (i >= t.size() || t[i] != '"') return false;
+    out.clear();
+    for (i++; i < t.size() && t[i] != '"'; i++) {
+      if (t[i] == '\\' || out.size() > 255) return false;
+      out += t[i];
+    }
+    if (i >= t.size()) return false;
+    i++;
+    return true;
+  }
+  bool integer(int64_t& v) {
+    ws();
+    size_t j = i;
+    bool neg = false;
+    if (j < t.size() && t[j] == '-') { neg = true; j++; }
+    if (j >= t.size() || t[j] < '0' || t[j] > '9') return false;
+    int64_t x = 0;
+    for (; j < t.size() && t[j] >= '0' && t[j] <= '9'; j++) {
+      x = 10 * x + (t[j] - '0');
+      if (x > (int64_t(1) << 40)) return false;
+    }
+    i = j;
+    v = neg ? -x : x;
+    return true;
+  }
+  bool record(TuneRecord& r) {
+    if (!lit('{')) return false;
+    if (lit('}')) return true;
+    do {
+      std::string key;
+      if (!str(key) || !lit(':')) return false;
+      if (key == "device") {
+        if (!str(r.device)) return false;
+        continue;
+      }
+      int64_t v = 0;
+      if (!integer(v)) return false;
+      const int32_t x = (int32_t)v;
+      if (key == "sms") r.sms = x;
+      else if (key == "out_h") r.oh = x;
+      else if (key == "out_w") r.ow = x;
+      else if (key == "jitter") r.jitter = x;
+      else if (key == "bucket") r.bucket = x;
+      else if (key == "rows_per_item") r.band = x;
+      else if (key == "ctas_per_sm") r.per_sm = x;
+      else return false;
+    } while (lit(','));
+    return lit('}');
+  }
+  bool document(std::vector<TuneRecord>& out, std::string& format) {
+    if (!lit('{')) return false;
+    bool have_entries = false;
+    if (!lit('}')) {
+      do {
+        std::string key;
+        if (!str(key) || !lit(':')) return false;
+        if (key == "format") {
+          if (!str(format)) return false;
+        } else if (key == "entries") {
+          if (!lit('[')) return false;
+          have_entries = true;
+          if (!lit(']')) {
+            do {
+              TuneRecord r;
+              if (!record(r)) return false;
+              out.push_back(r);
+            } while (lit(','));
+            if (!lit(']')) return false;
+          }
+        } else {
+          return false;
+        }
+      } while (lit(','));
+      if (!lit('}')) return false;
+    }
+    ws();
+    return have_entries && i == t.size();
+  }
+};
+
+static bool record_valid(const TuneRecord& r) {
+  return !r.device.empty() && r.sms > 0 && r.oh > 0 && r.ow > 0 && r.ow <= 1024 && (r.jitter == 0 || r.jitter == 1) &&
+         r.bucket >= 0 && r.bucket <= 31 && r.band >= 1 && r.band <= kBandMax && r.per_sm >= 1 && r.per_sm <= 64;
+}
+
 static int fused_max_per_sm(int jitter, bool masks = false) {
   int per_sm = 0;
   auto kern = jitter ? (masks ? k_chain_fused<1, true> : k_chain_fused<1, false>)
@@ -865,3 +982,92 @@ extern "C" alb_status alb_apply_batch_targets(const alb_chain_cfg* cfg, int32_t 
   return ALB_OK;
 }
 
+
+// ---- schedule cache: lookup and persistence
+extern "C" alb_status alb_autotune_lookup(const alb_chain_cfg* cfg, int32_t n, alb_chain_cfg* best,
+                                          int32_t* found) {
+  ALB_REQUIRE(cfg && best && found, ALB_EINVAL, "alb_autotune_lookup: null argument");
+  ALB_REQUIRE(n > 0, ALB_EINVAL, "alb_autotune_lookup: n must be > 0");
+  int dev = 0;
+  ALB_CUDA(cudaGetDevice(&dev));
+  int32_t band = 0, per_sm = 0;
+  *found = tune_lookup(dev, *cfg, n, band, per_sm) ? 1 : 0;
+  *best = *cfg;
+  if (*found) {
+    best->tile_h = band;
+    best->ctas_per_sm = per_sm;
+  }
+  return ALB_OK;
+}
+
+extern "C" alb_status alb_autotune_save(const char* path) {
+  ALB_REQUIRE(path && *path, ALB_EINVAL, "alb_autotune_save: empty path");
+  std::vector<TuneEntry> entries;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    entries = g_tune;
+  }
+  std::string out = "{\"format\": \"alb-autotune-1\", \"entries\": [";
+  for (size_t k = 0; k < entries.size(); k++) {
+    const TuneEntry& e = entries[k];
+    std::string name;
+    int32_t sms = 0;
+    if (!device_key(e.dev, name, sms)) return cuda_status(cudaGetLastError(), "alb_autotune_save: device query");
+    char buf[512];
+    snprintf(buf, sizeof(buf),
+             "%s\n  {\"device\": \"%s\", \"sms\": %d, \"out_h\": %d, \"out_w\": %d, \"jitter\": %d, \"bucket\": %d, "
+             "\"rows_per_item\": %d, \"ctas_per_sm\": %d}",
+             k ? "," : "", name.c_str(), sms, e.oh, e.ow, e.jitter, e.bucket, e.band, e.per_sm);
+    out += buf;
+  }
+  out += "\n]}\n";
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE* f = fopen(tmp.c_str(), "wb");
+  ALB_REQUIRE(f, ALB_EINVAL, "alb_autotune_save: cannot write %s", tmp.c_str());
+  const bool ok = fwrite(out.data(), 1, out.size(), f) == out.size();
+  const bool closed = fclose(f) == 0;
+  ALB_REQUIRE(ok && closed, ALB_EINVAL, "alb_autotune_save: write to %s failed", tmp.c_str());
+  ALB_REQUIRE(rename(tmp.c_str(), path) == 0, ALB_EINVAL, "alb_autotune_save: cannot rename to %s", path);
+  return ALB_OK;
+}
+
+extern "C" alb_status alb_autotune_load(const char* path, int32_t* n_loaded) {
+  ALB_REQUIRE(path && *path && n_loaded, ALB_EINVAL, "alb_autotune_load: null argument");
+  *n_loaded = 0;
+  FILE* f = fopen(path, "rb");
+  ALB_REQUIRE(f, ALB_EINVAL, "alb_autotune_load: cannot open %s", path);
+  std::string text;
+  char buf[4096];
+  size_t got;
+  while ((got = fread(buf, 1, sizeof(buf), f)) > 0 && text.size() < (1u << 22)) text.append(buf, got);
+  fclose(f);
+  ALB_REQUIRE(text.size() < (1u << 22), ALB_EINVAL, "alb_autotune_load: %s is larger than 4 MiB", path);
+  std::vector<TuneRecord> recs;
+  std::string format;
+  JsonReader rd(text);
+  ALB_REQUIRE(rd.document(recs, format), ALB_EINVAL, "alb_autotune_load: %s is not an autotune cache (offset %zu)",
+              path, rd.i);
+  ALB_REQUIRE(format == "alb-autotune-1", ALB_EINVAL, "alb_autotune_load: unknown format \"%s\"", format.c_str());
+  for (size_t k = 0; k < recs.size(); k++)
+    ALB_REQUIRE(record_valid(recs[k]), ALB_EINVAL, "alb_autotune_load: entry %zu of %s is out of range", k, path);
+  // nothing is loaded until the whole file has been read and checked
+  int count = 0;
+  ALB_CUDA(cudaGetDeviceCount(&count));
+  int32_t loaded = 0;
+  for (int dev = 0; dev < count; dev++) {
+    std::string name;
+    int32_t sms = 0;
+    if (!device_key(dev, name, sms)) return cuda_status(cudaGetLastError(), "alb_autotune_load: device query");
+    for (const TuneRecord& r : recs) {
+      if (r.device != name || r.sms != sms) continue;
+      alb_chain_cfg c{};
+      c.out_h = r.oh;
+      c.out_w = r.ow;
+      c.jitter = r.jitter;
+      tune_store(dev, c, int32_t(1) << (r.bucket > 30 ? 30 : r.bucket), r.band, r.per_sm);
+      loaded++;
+    }
+  }
+  *n_loaded = loaded;
+  return ALB_OK;
+}

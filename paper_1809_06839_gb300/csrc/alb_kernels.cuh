@@ -20,6 +20,8 @@ alb_status launch_stream_pixel(int32_t tid, const Plan& plan, const ImgList& in,
                                const PrmList& prm, int32_t* status, cudaStream_t st);
 alb_status launch_stream_hist(const Plan& plan, const ImgList& in, uint32_t* hist, int32_t* status,
                               cudaStream_t st);
+alb_status launch_wait_selftest(uint32_t spins, const uint8_t* src, uint8_t* out, int32_t* status,
+                                cudaStream_t st);
 
 // alb_resample.cu (tiled warps and resizes)
 alb_status launch_tile_geometric(int32_t tid, const Plan& plan, const ImgList& in, const ImgList& out,

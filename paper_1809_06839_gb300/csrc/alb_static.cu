@@ -14,12 +14,17 @@
 // every GPU that loads libalb.so holds it until the process exits.  Host code
 // must not use the array's name as a device address (on the host it names a
 // shadow object), so the first call on each device looks up the real device
-// address with cudaGetSymbolAddress, with that device current, and caches it.
-// That first call therefore does a runtime query and should happen before any
-// stream capture.  Every call shares the one array and leaves the last call's
-// contents in it; calls whose kernels overlap on the GPU (different streams
-// without ordering) race on it and must be serialised by the caller.
+// address with cudaGetSymbolAddress, with that device current, and caches it
+// together with the id of the CUDA context it belongs to; a later call in a
+// different context (after cudaDeviceReset) looks it up again.  A call that
+// looks the address up does a runtime query, so the first call on a device
+// (and the first after a reset) should happen before any stream capture.
+// Every call shares the one array and leaves the last call's contents in it;
+// calls whose kernels overlap on the GPU (different streams without
+// ordering) race on it and must be serialised by the caller.
 #include <mutex>
+
+#include <cuda.h>
 
 #include "alb_common.cuh"
 #include "alb_kernels.cuh"
@@ -33,21 +38,58 @@ constexpr int32_t kStaticItemBytes = 16384;        // output bytes per work item
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
 static std::mutex g_static_mu;
-static void* g_static_addr[64] = {nullptr};
+struct StaticAddr {
+  void* addr;                  // device address of g_static_scratch
+  unsigned long long ctx_id;   // the CUDA context it belongs to (0: unknown)
+};
+static StaticAddr g_static_addr[64] = {};
 
-// Device address of g_static_scratch on the current device (looked up once per device).
+// Unique id of the calling thread's current CUDA context, 0 when there is
+// none or the driver query is unavailable.  The driver functions are looked
+// up through the runtime, so the library does not link the driver library.
+static unsigned long long current_ctx_id() {
+  typedef CUresult (*GetCurrentFn)(CUcontext*);
+  typedef CUresult (*GetIdFn)(CUcontext, unsigned long long*);
+  static GetCurrentFn get_current = nullptr;
+  static GetIdFn get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = (GetCurrentFn)f;
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = (GetIdFn)f;
+    looked_up = true;
+  }
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+  if (get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+// Device address of g_static_scratch in the current device's context, looked
+// up once per context: a call after the context was destroyed and re-created
+// (cudaDeviceReset) looks it up again instead of reusing a stale address.
 static alb_status static_scratch(void** out) {
   int dev = -1;
   ALB_CUDA(cudaGetDevice(&dev));
   ALB_REQUIRE(dev >= 0 && dev < 64, ALB_EINVAL, "alb_apply_ragged_static: device ordinal %d out of range", dev);
   std::lock_guard<std::mutex> lock(g_static_mu);
-  if (!g_static_addr[dev]) {
+  const unsigned long long id = current_ctx_id();
+  StaticAddr& c = g_static_addr[dev];
+  if (!c.addr || id == 0 || id != c.ctx_id) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
     if (e != cudaSuccess || !p) return cuda_status(e, "cudaGetSymbolAddress(g_static_scratch)");
-    g_static_addr[dev] = p;
+    c.addr = p;
+    c.ctx_id = current_ctx_id();   // the lookup made the device's context current if it was not
   }
-  *out = g_static_addr[dev];
+  *out = c.addr;
   return ALB_OK;
 }
 

@@ -60,6 +60,20 @@ constexpr int kBulkChunk = 12288;   // bytes per stage: 768 vectors, a multiple 
 constexpr int kBulkStages = 3;
 static_assert(kBulkChunk % 48 == 0, "a stage starts on the same channel phase as the previous one");
 
+// After a bounded wait gave up: wait (bounded again) for the copies of chunks
+// [first, last) of the sequence -- exactly the chunks whose bulk loads were
+// issued and not yet consumed, so that no load into the CTA's shared memory
+// is still in flight when it stops -- and record ALB_ETIMEOUT.  A chunk whose
+// copy was never issued must not be in the range: its phase cannot complete.
+// Called by the thread that issued the loads.
+ALB_D void bulk_drain(uint64_t* full, uint32_t seq, int32_t first, int32_t last, int32_t* status) {
+  for (int32_t k = first; k < last; k++) {
+    const uint32_t q = seq + (uint32_t)k;
+    mbar_wait(&full[q % kBulkStages], (q / kBulkStages) & 1u);
+  }
+  dev_fail(status, ALB_ETIMEOUT);
+}
+
 // Streams bytes [0, total) of src (and, with dst, back to dst) through the
 // CTA's stages.  body(stage, bytes, offset) runs on every thread for each
 // chunk; with dst it may rewrite the stage in place, which is then stored.
@@ -108,14 +122,9 @@ ALB_D bool bulk_pipeline(uint8_t (*stage)[kBulkChunk], uint64_t* full, uint32_t&
     }
   }
   if (dead) {
-    if (tid == 0) {
-      const int32_t last = imin(nch, j + kBulkStages - 1);
-      for (int32_t k = j; k < last; k++) {
-        const uint32_t q = seq + (uint32_t)k;
-        mbar_wait(&full[q % kBulkStages], (q / kBulkStages) & 1u);
-      }
-      dev_fail(status, ALB_ETIMEOUT);
-    }
+    // chunks j .. j + stages - 2 had their copies issued (chunk j's wait is
+    // the one that gave up); none beyond
+    if (tid == 0) bulk_drain(full, seq, j, imin(nch, j + kBulkStages - 1), status);
     return false;
   }
   seq += (uint32_t)nch;
@@ -709,6 +718,40 @@ alb_status launch_stream_hist(const Plan& plan, const ImgList& in, uint32_t* his
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hist_bulk, 256, smem);
   k_hist_bulk<<<(per_sm < 1 ? 1 : per_sm) * sm_count(), 256, smem, st>>>(plan, in, hist, status);
+  ALB_CUDA(cudaGetLastError());
+  return ALB_OK;
+}
+
+// Self-test of the bounded wait and of the drain that follows it.  One CTA,
+// one thread: stages 1 and 2 get real 16-byte bulk loads from src; stage 0
+// gets the arrival announcing 16 bytes but no copy, so its phase can never
+// complete.  The wait on stage 0 (at most `spins` tries, the same routine as
+// the pipelines') gives up; bulk_drain then waits for the two copies that
+// were issued -- and only those -- and records ALB_ETIMEOUT.  The drained
+// stages are copied to out[0, 32) so the caller can see that they landed
+// before the CTA ended.
+__global__ void k_wait_selftest(uint32_t spins, const uint8_t* __restrict__ src, uint8_t* __restrict__ out,
+                                int32_t* status) {
+  __shared__ __align__(128) uint8_t stage[kBulkStages][kBulkChunk > 64 ? 64 : kBulkChunk];
+  __shared__ __align__(8) uint64_t full[kBulkStages];
+  if (threadIdx.x != 0) return;
+  for (int i = 0; i < kBulkStages; i++) mbar_init(&full[i], 1);
+  mbar_init_fence();
+  mbar_arrive_expect_tx(&full[0], 16);                 // announced, never issued
+  for (int k = 1; k < kBulkStages; k++) {
+    mbar_arrive_expect_tx(&full[k], 16);
+    bulk_load(stage[k], src + 16 * (k - 1), 16, &full[k]);
+  }
+  if (mbar_wait(&full[0], 0u, spins)) return;          // cannot happen: nothing completes stage 0
+  bulk_drain(full, 0u, 1, kBulkStages, status);
+  for (int k = 1; k < kBulkStages; k++)
+    for (int b = 0; b < 16; b++) out[16 * (k - 1) + b] = stage[k][b];
+}
+
+alb_status launch_wait_selftest(uint32_t spins, const uint8_t* src, uint8_t* out, int32_t* status,
+                                cudaStream_t st) {
+  static_assert(kBulkStages == 3, "the self-test issues copies into stages 1 and 2");
+  k_wait_selftest<<<1, 32, 0, st>>>(spins, src, out, status);
   ALB_CUDA(cudaGetLastError());
   return ALB_OK;
 }

@@ -185,3 +185,40 @@ def test_float_path_shape_limits_without_cuda(L):
     # an empty batch is a no-op
     assert fwd(0, 3, 8, 8, None, None, None, None) == alb.ALB_OK
     assert bwd(0, 3, 8, 8, None, None, None, None, None, None, 0, None) == alb.ALB_OK
+
+
+def test_selftest_bounded_wait_rejects_bad_arguments_before_any_launch(L):
+    # refused on the host: no CUDA call is made (no GPU here)
+    f = L.alb_selftest_bounded_wait
+    for spins in (0, -3, (1 << 22) + 1):
+        assert f(spins, C.c_void_p(16), C.c_void_p(64), C.c_void_p(128), None) == alb.ALB_EINVAL
+    assert f(8, C.c_void_p(24), C.c_void_p(64), C.c_void_p(128), None) == alb.ALB_EALIGN
+    assert f(8, None, C.c_void_p(64), C.c_void_p(128), None) == alb.ALB_EINVAL
+    assert f(8, C.c_void_p(16), C.c_void_p(64), None, None) == alb.ALB_EINVAL
+
+
+def test_autotune_load_rejects_bad_files_before_any_device_query(L, tmp_path):
+    """A missing, malformed or out-of-range cache file is refused (ALB_EINVAL)
+    after reading, before any CUDA call; a well-formed one reaches the
+    device query (no GPU here: ALB_ECUDA)."""
+    f = L.alb_autotune_load
+    n = C.c_int32(-1)
+    assert f(os.fsencode(str(tmp_path / "missing.json")), C.byref(n)) == alb.ALB_EINVAL
+    good = ('{"format": "alb-autotune-1", "entries": [{"device": "NVIDIA GB300", "sms": 152, "out_h": 224, '
+            '"out_w": 224, "jitter": 0, "bucket": 12, "rows_per_item": 32, "ctas_per_sm": 6}]}')
+    bad = [
+        "", "[]", '{"format": "alb-autotune-1"}', good.replace("alb-autotune-1", "other"),
+        good.replace('"rows_per_item": 32', '"rows_per_item": 33'), good.replace('"jitter": 0', '"jitter": 2'),
+        good.replace('"ctas_per_sm": 6', '"ctas_per_sm": 0'), good.replace('"sms": 152', '"sms": "x"'),
+        good.replace('"bucket": 12', '"bucket": 12, "extra": 1'), good[:-3], good + "x",
+    ]
+    for k, text in enumerate(bad):
+        p = tmp_path / f"bad{k}.json"
+        p.write_text(text)
+        assert f(os.fsencode(str(p)), C.byref(n)) == alb.ALB_EINVAL, text
+        assert n.value == 0
+    p = tmp_path / "good.json"
+    p.write_text(good)
+    assert f(os.fsencode(str(p)), C.byref(n)) == alb.ALB_ECUDA
+    p.write_text('{"format": "alb-autotune-1", "entries": []}')
+    assert f(os.fsencode(str(p)), C.byref(n)) in (alb.ALB_OK, alb.ALB_ECUDA)

@@ -94,6 +94,46 @@ def test_autotuned_schedule_and_every_candidate_agree(dev):
     assert np.array_equal(bits(cached), ref)
 
 
+def test_autotune_cache_persists_to_json(dev, tmp_path):
+    """The autotuner's pick is cached, written to JSON keyed by device name
+    and SM count, and read back: a schedule edited in the file becomes the
+    cached pick, and zero-field calls with it still write the oracle's bits."""
+    import json
+    sizes = [(300 + (i * 37) % 500, 280 + (i * 53) % 600) for i in range(24)]
+    rb = synth.ragged_noise(sizes, seed=13)
+    oc = O.make_cfg(O.CHAIN, **CHAIN_CFG)
+    ops = [O.sample_params(oc, 13, 20, i, h, w) for i, (h, w) in enumerate(sizes)]
+    lps = [to_lib(p, alb) for p in ops]
+    din = DeviceBatch(to_device(rb, dev))
+    n = len(lps)
+    pdev = alb.params_to_device(lps, dev)
+    out = torch.empty((n, 3, 224, 224), dtype=torch.bfloat16, device=dev)
+    best = alb.alb_autotune_batch(alb.chain_cfg(), n, pdev, din.dev, out, reps=1)
+    got = alb.alb_autotune_lookup(alb.chain_cfg(), n)
+    assert got is not None and (got.tile_h, got.ctas_per_sm) == (best.tile_h, best.ctas_per_sm)
+    assert alb.alb_autotune_lookup(alb.chain_cfg(out_h=17, out_w=19), n) is None
+    path = tmp_path / "tune.json"
+    alb.alb_autotune_save(str(path))
+    doc = json.loads(path.read_text())
+    assert doc["format"] == "alb-autotune-1"
+    mine = [e for e in doc["entries"] if e["out_h"] == 224 and e["jitter"] == 0 and e["bucket"] == 5]
+    assert len(mine) == 1 and mine[0]["rows_per_item"] == best.tile_h
+    assert mine[0]["device"] == torch.cuda.get_device_name(dev)
+    assert mine[0]["sms"] == torch.cuda.get_device_properties(dev).multi_processor_count
+    mine[0]["rows_per_item"] = 4 if best.tile_h != 4 else 16
+    mine[0]["ctas_per_sm"] = 1
+    path.write_text(json.dumps(doc))
+    assert alb.alb_autotune_load(str(path)) >= 1
+    got = alb.alb_autotune_lookup(alb.chain_cfg(), n)
+    assert (got.tile_h, got.ctas_per_sm) == (mine[0]["rows_per_item"], 1)
+    o = torch.empty_like(out)
+    alb.alb_apply_batch(alb.chain_cfg(), n, pdev, din.dev, o, alb.MODE_FUSED)
+    torch.cuda.synchronize()
+    ob = bits(o)
+    for i in range(n):
+        assert np.array_equal(ob[i], O.chain_image(ops[i], rb.image(i).numpy())), i
+
+
 def test_full_size_ragged_batch_sampled(dev):
     """4096 images, H, W ~ U[256, 1024], params from the device sampler; fused ==
     plain over the whole output; 24 sampled images against the oracle."""
