@@ -43,7 +43,7 @@ UNIT = "images/s"
 # traffic figure is this times the images of one launch.  Only kernels whose
 # code is unchanged since that capture are listed.
 NCU_DRAM_BYTES_PER_IMAGE = {"Rotate": 1138010.0, "ShiftScaleRotate": 1046432.0, "Resize512": 1166141.0,
-                            "ShiftHSV": 846090.0, "PadToSize512": 1172000.0, "Brightness": 848000.0}
+                            "ShiftHSV": 846090.0, "PadToSize512": 1172000.0}
 SUITE_N, SUITE_LO, SUITE_HI = 2000, 333, 500
 FUSED_N, FUSED_LO, FUSED_HI = 4096, 256, 1024
 DET_N, DET_HW = 256, 1024
@@ -276,6 +276,68 @@ def suite_e2e(suite, stream, steps, copy_streams=2):
     return dict(t=t, wall=wall, bi=bi, bo=bo)
 
 
+# ------------------------------------------------------------------ algorithmic bytes of the chain
+def _q5_taps(n_in, n_out):
+    """Source samples the half-pixel Q5 resize of n_in -> n_out reads with a
+    nonzero weight: ix, and ix + 1 where the fraction is nonzero."""
+    d = np.arange(n_out, dtype=np.int64)
+    num = 32 * ((2 * d + 1) * n_in - n_out) + n_out
+    xq = np.floor_divide(num, 2 * n_out)
+    xq = np.maximum(xq, 0)
+    xq = np.where((xq >> 5) >= n_in - 1, 32 * (n_in - 1), xq)
+    ix, fx = xq >> 5, xq & 31
+    return np.unique(np.concatenate([ix, (ix + 1)[fx > 0]]))
+
+
+def _nearest_taps(n_in, n_out):
+    d = np.arange(n_out, dtype=np.int64)
+    return np.unique(np.minimum(((2 * d + 1) * n_in) // (2 * n_out), n_in - 1))
+
+
+def _distinct_sectors(base, stride, rows, byte_cols):
+    """Distinct 32-byte sectors of the bytes base + r * stride + b, r in rows
+    (sorted), b in byte_cols (sorted): per row the sector set depends only on
+    the row start's phase within a sector; consecutive rows can share at most
+    their boundary sector (their spans are at most one row apart)."""
+    starts = base + rows * stride
+    phase = starts & 31
+    per_phase = {}
+    total = 0
+    lo = np.empty(len(rows), np.int64)
+    hi = np.empty(len(rows), np.int64)
+    for k, (s, ph) in enumerate(zip(starts.tolist(), phase.tolist())):
+        sec = per_phase.get(ph)
+        if sec is None:
+            sec = np.unique((ph + byte_cols) >> 5)
+            per_phase[ph] = sec
+        total += len(sec)
+        lo[k] = (s >> 5) + sec[0]
+        hi[k] = (s >> 5) + sec[-1]
+    if len(rows) > 1:
+        total -= int(np.maximum(hi[:-1] - lo[1:] + 1, 0).sum())
+    return total
+
+
+def chain_read_bytes(params, shapes, offsets, out_h=224, out_w=224, mask_planes=None, mask_offsets=None):
+    """Algorithmic read bytes of the chain over the batch: the distinct 32-byte
+    sectors holding the source bytes that the crop's bilinear taps (nonzero
+    weight) touch, per image (and, with masks, the sectors of the nearest
+    taps of every plane)."""
+    total = 0
+    for i, (p, (h, w, c)) in enumerate(zip(params, shapes)):
+        rows = p.y0 + _q5_taps(p.ch, out_h)
+        cols = p.x0 + _q5_taps(p.cw, out_w)
+        bcols = (3 * cols[:, None] + np.arange(3)[None, :]).ravel()
+        total += 32 * _distinct_sectors(int(offsets[i]), 3 * w, rows.astype(np.int64), bcols.astype(np.int64))
+        if mask_planes is not None:
+            npl = mask_planes[i]
+            mr = p.y0 + _nearest_taps(p.ch, out_h)
+            mc = p.x0 + _nearest_taps(p.cw, out_w)
+            mb = (npl * mc[:, None] + np.arange(npl)[None, :]).ravel()
+            total += 32 * _distinct_sectors(int(mask_offsets[i]), npl * w, mr.astype(np.int64), mb.astype(np.int64))
+    return total
+
+
 # ------------------------------------------------------------------ sub-workloads
 def fused_pipeline(dev, stream, steps=3, warmup=2, n=FUSED_N):
     from paper_1809_06839_gb300 import alb as A, synth
@@ -291,12 +353,11 @@ def fused_pipeline(dev, stream, steps=3, warmup=2, n=FUSED_N):
     wsp = A.workspace(A.alb_batch_workspace_size(ccfg, FUSED_N, A.MODE_PLAIN), dev)
     A.alb_sample_params_batch(cfg, SEED, 20, 0, FUSED_N, din.dev, pdev, stream=stream)
     params = A.params_from_device(pdev)
-    # algorithmic read bytes: distinct source rows x window width actually sampled
-    rd = 0
-    for p in params:
-        rows = min(p.ch, 2 * 224)
-        rd += rows * p.cw * 3
+    # algorithmic bytes: the distinct 32-byte sectors the crops' bilinear taps
+    # read, and the bf16 NCHW output written once
+    rd = chain_read_bytes(params, din.rb.shapes, din.rb.offsets)
     wr = FUSED_N * 3 * 224 * 224 * 2
+    hbm = peaks()[0]
 
     def run(mode, ws):
         A.alb_sample_params_batch(cfg, SEED, 20, 0, FUSED_N, din.dev, pdev, stream=stream)
@@ -306,6 +367,14 @@ def fused_pipeline(dev, stream, steps=3, warmup=2, n=FUSED_N):
     # timed region); ccfg keeps zero fields, so the fused runs use the cached pick
     best = A.alb_autotune_batch(ccfg, FUSED_N, pdev, din.dev, out, wsf, reps=3, stream=stream)
     res = {"schedule": {"rows_per_item": best.tile_h, "ctas_per_sm": best.ctas_per_sm, "by": "alb_autotune_batch"}}
+    # the schedule cache persisted to JSON and read back (the next process can
+    # start from it with alb_autotune_load)
+    cache = os.path.join(ROOT, "paper_1809_06839_gb300", "_build", "autotune.json")
+    try:
+        A.alb_autotune_save(cache)
+        res["autotune_cache"] = {"path": os.path.relpath(cache, ROOT), "entries_reloaded": A.alb_autotune_load(cache)}
+    except Exception as ex:  # persistence is reported, not required for the timing
+        res["autotune_cache"] = {"error": str(ex)[:160]}
     for name, mode, ws in (("fused", A.MODE_FUSED, wsf), ("plain", A.MODE_PLAIN, wsp)):
         for _ in range(warmup):
             run(mode, ws)
@@ -328,6 +397,10 @@ def fused_pipeline(dev, stream, steps=3, warmup=2, n=FUSED_N):
         res["fused_graph"] = dict(error=str(ex)[:160])
     tf = res["fused"]["ms"] / 1e3
     res["fused_gbs"] = (rd + wr) / tf / 1e9
+    res["roofline"] = {"bound": "hbm", "algorithmic_bytes": rd + wr, "read_bytes": rd, "write_bytes": wr,
+                       "achieved": round((rd + wr) / tf / 1e9, 1), "peak": hbm, "unit": "GB/s",
+                       "frac": round((rd + wr) / tf / 1e9 / hbm, 4),
+                       "read": "distinct 32-byte sectors of the crops' nonzero-weight bilinear taps (exact count)"}
     res["speedup_vs_plain"] = res["plain"]["ms"] / res["fused"]["ms"]
     # jitter mode 1: per-image random order and image-mean contrast pivot (a
     # per-image reduction before the write pass), fused vs plain
@@ -343,6 +416,10 @@ def fused_pipeline(dev, stream, steps=3, warmup=2, n=FUSED_N):
         t = ev_time(runj, stream, steps)
         jres[name] = dict(images_per_s=FUSED_N / t, ms=t * 1e3)
     jres["speedup_vs_plain"] = jres["plain"]["ms"] / jres["fused"]["ms"]
+    tj = jres["fused"]["ms"] / 1e3
+    # the pivot pass reads the sampled pixels once more; counted as traffic, not algorithmic bytes
+    jres["roofline"] = {"bound": "hbm", "algorithmic_bytes": rd + wr, "achieved": round((rd + wr) / tj / 1e9, 1),
+                        "peak": hbm, "unit": "GB/s", "frac": round((rd + wr) / tj / 1e9 / hbm, 4)}
     res["jitter_random_order_mean_pivot"] = jres
     res["workload"] = "4096 ragged u8 RGB images H,W~U[256,1024] -> RRC 224 + flip + jitter + Normalize bf16 NCHW"
     del din, out, wsf, wsp, wsj
@@ -386,9 +463,77 @@ def fused_detection(dev, stream, steps=3, warmup=2, n=FUSED_N):
         t = ev_time(run, stream, steps)
         res[name] = dict(images_per_s=n / t, ms=t * 1e3)
     res["speedup_vs_plain"] = res["plain"]["ms"] / res["fused"]["ms"]
+    params = A.params_from_device(pdev)
+    rd = chain_read_bytes(params, din.rb.shapes, din.rb.offsets, mask_planes=planes, mask_offsets=mi.rb.offsets)
+    rd += int(nb.sum()) * 16 + 4 * n
+    wr = n * 3 * 224 * 224 * 2 + sum(224 * 224 * c for c in planes) + int(nbo.cpu().sum()) * 16 + 4 * n
+    hbm = peaks()[0]
+    tf = res["fused"]["ms"] / 1e3
+    res["roofline"] = {"bound": "hbm", "algorithmic_bytes": rd + wr, "achieved": round((rd + wr) / tf / 1e9, 1),
+                       "peak": hbm, "unit": "GB/s", "frac": round((rd + wr) / tf / 1e9 / hbm, 4)}
     res["workload"] = (f"{n} ragged u8 RGB images H,W~U[{FUSED_LO},{FUSED_HI}] + 1-8 instance planes + 1-50 boxes: "
                        "box-safe crop -> 224 + flip + jitter + Normalize bf16 NCHW, masks nearest, boxes mapped")
     del din, mi, mo, out, ws
+    torch.cuda.empty_cache()
+    return res
+
+
+def small_plain(dev, stream, hbm, n=64, reps=20):
+    """The plain single-op path at small size: 64 images of 256 x 256 + their
+    20-class label masks; HFlip -> Brightness/Contrast LUT -> RandomCrop 224
+    (masks through the flip and the crop), each step a device-sampled ragged
+    launch.  Its 12.6 MB working set fits in L2, so it is timed both hot
+    (back to back) and with L2 flushed before every step (a 512 MB write that
+    is not timed)."""
+    from paper_1809_06839_gb300 import alb as A, synth
+    from paper_1809_06839_gb300.ragged import DeviceBatch, mask_output_batch, output_batch
+    sizes = [(256, 256)] * n
+    img = DeviceBatch(synth.ragged_noise(sizes, seed=SEED, device=dev))
+    msk = DeviceBatch(synth.ragged_masks(sizes, seed=SEED, device=dev))
+    steps_cfg = [(A.HFLIP, dict(p=1.0), True), (A.BRIGHTNESS_CONTRAST, dict(lo=(0.8, -20.0), hi=(1.2, 20.0)), False),
+                 (A.RANDOM_CROP, dict(out_h=224, out_w=224), True)]
+    stages, cur, curm, alg = [], img, msk, 0
+    for k, (tid, kw, with_mask) in enumerate(steps_cfg):
+        cfg = A.sample_cfg(tid, **kw)
+        pdev = torch.zeros(n * 232, dtype=torch.uint8, device=dev)
+        A.alb_sample_params_batch(cfg, SEED, 100 + k, 0, n, cur.dev, pdev)
+        params = A.params_from_device(pdev)
+        nxt = output_batch(params, cur.rb.shapes, dev)
+        nxtm = mask_output_batch(params, curm.rb.shapes, dev) if with_mask else curm
+        ws = A.workspace(A.alb_workspace_size(tid, n), dev)
+        stages.append((tid, cfg, pdev, cur, nxt, curm if with_mask else None, nxtm if with_mask else None, ws, k))
+        alg += cur.nbytes + nxt.nbytes + ((curm.nbytes + nxtm.nbytes) if with_mask else 0)
+        cur, curm = nxt, nxtm
+
+    def step():
+        for tid, cfg, pdev, a, b, ma, mb, ws, k in stages:
+            A.alb_sample_params_batch(cfg, SEED, 100 + k, 0, n, a.dev, pdev, stream=stream)
+            A.alb_apply_ragged(tid, n, pdev, a.dev, b.dev, ma.dev if ma else None, mb.dev if mb else None,
+                               ws=ws, stream=stream)
+
+    for _ in range(3):
+        step()
+    hot = ev_time(step, stream, reps)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    t = 0.0
+    for _ in range(reps):
+        flush.fill_(1)
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        step()
+        e.record(stream)
+        e.synchronize()
+        t += s.elapsed_time(e) / 1000.0
+    cold = t / reps
+    res = {}
+    for name, tt in (("l2_flushed", cold), ("hot", hot)):
+        res[name] = dict(images_per_s=round(n / tt, 1), ms=round(tt * 1e3, 4), gbs=round(alg / tt / 1e9, 1),
+                         frac=round(alg / tt / 1e9 / hbm, 4))
+    res["algorithmic_bytes"] = alg
+    res["launches"] = 6
+    res["workload"] = ("64 u8 RGB 256x256 + 20-class masks: HFlip -> Brightness/Contrast -> RandomCrop 224 "
+                       "(plain path, three ragged launches + their device samplers)")
+    del stages, img, msk, flush
     torch.cuda.empty_cache()
     return res
 
@@ -571,6 +716,40 @@ def oracle_suite_sample(n_images, seed=SEED, threads=None, imgs=None):
     return done * len(cfgs) / dt, threads, done, dt
 
 
+def summary(extra):
+    """Headline figures of the sub-workloads, last in the JSON line so that a
+    reader of the output's tail sees them."""
+    out = {}
+    fp = extra.get("fused_pipeline")
+    if fp:
+        out["fused_pipeline"] = {"fused_images_per_s": round(fp["fused"]["images_per_s"]),
+                                 "plain_images_per_s": round(fp["plain"]["images_per_s"]),
+                                 "speedup_vs_plain": round(fp["speedup_vs_plain"], 2),
+                                 "fused_frac": fp["roofline"]["frac"], "fused_gbs": fp["roofline"]["achieved"]}
+        j = fp.get("jitter_random_order_mean_pivot")
+        if j:
+            out["jitter_mode1"] = {"fused_images_per_s": round(j["fused"]["images_per_s"]),
+                                   "speedup_vs_plain": round(j["speedup_vs_plain"], 2),
+                                   "fused_frac": j["roofline"]["frac"]}
+    fd = extra.get("fused_detection")
+    if fd:
+        out["fused_detection"] = {"fused_images_per_s": round(fd["fused"]["images_per_s"]),
+                                  "speedup_vs_plain": round(fd["speedup_vs_plain"], 2),
+                                  "fused_frac": fd["roofline"]["frac"]}
+    if extra.get("detection"):
+        out["detection_images_per_s"] = round(extra["detection"]["images_per_s"])
+    d = extra.get("differentiable")
+    if d:
+        out["differentiable"] = {"fwd_ms": round(d["fwd_ms"], 3), "bwd_ms": round(d["bwd_ms"], 3)}
+    sp = extra.get("small_plain")
+    if sp:
+        out["small_plain"] = {k: sp[k]["images_per_s"] for k in ("l2_flushed", "hot")}
+    lg = extra.get("per_transform_large")
+    if lg:
+        out["large_frac"] = {k: v["frac"] for k, v in lg.items() if isinstance(v, dict)}
+    return out
+
+
 # ------------------------------------------------------------------ main
 def dist_setup(args):
     ws = int(os.environ.get("WORLD_SIZE", "1"))
@@ -620,10 +799,11 @@ def main():
     ap.add_argument("--ref-images", type=int, default=400)
     ap.add_argument("--skip-extra", action="store_true", help="headline suite only")
     ap.add_argument("--cpu-images", type=int, default=2000)
+    ap.add_argument("--cpu-images-1core", type=int, default=120)
     ap.add_argument("--only", default="", help="comma-separated suite transforms (profiling runs)")
     ap.add_argument("--n", type=int, default=SUITE_N, help="suite images (profiling runs)")
     ap.add_argument("--skip-e2e", action="store_true")
-    ap.add_argument("--extras", default="fused,detection,differentiable,large,distort,targets",
+    ap.add_argument("--extras", default="fused,detection,differentiable,large,distort,targets,small",
                     help="sub-workloads to run after the suite (comma-separated)")
     ap.add_argument("--fused-n", type=int, default=FUSED_N, help="images of the fused workload (profiling runs)")
     ap.add_argument("--diff-b", type=int, default=DIFF_B, help="batch of the differentiable workload (profiling runs)")
@@ -690,6 +870,8 @@ def main():
             extra["distortions"] = distortions(dev, stream, hbm)
         if "targets" in which:
             extra["fused_detection"] = fused_detection(dev, stream)
+        if "small" in which:
+            extra["small_plain"] = small_plain(dev, stream, hbm)
     cpu = None
     if rank == 0 and ws == 1 and args.cpu_images > 0:
         # the oracle on the same resident workload, copied to the host
@@ -697,6 +879,11 @@ def main():
         v, thr, done, dt = oracle_suite_sample(min(args.cpu_images, len(host)), imgs=host)
         cpu = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
                "sample": f"{done} images of the suite workload x 15 transforms ({dt:.1f} s)"}
+        n1 = min(args.cpu_images_1core, len(host))
+        if n1 > 0:
+            v1, _, done1, dt1 = oracle_suite_sample(n1, threads=1, imgs=host[:n1])
+            cpu["value_1core"] = v1
+            cpu["sample_1core"] = f"{done1} images of the suite workload x 15 transforms on one core ({dt1:.1f} s)"
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -716,6 +903,7 @@ def main():
                 "device_status": status,
                 "cpu_baseline": cpu, **extra}
         line["gpu_launches"] = launches
+        line["summary"] = summary(extra)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
