@@ -276,6 +276,26 @@ def suite_e2e(suite, stream, steps, copy_streams=2):
     return dict(t=t, wall=wall, bi=bi, bo=bo)
 
 
+def kernel_times(fn, reps=3):
+    """Average device time per launch of each kernel that `fn` launches, from
+    the profiler's CUDA activity trace (seconds, keyed by kernel name)."""
+    from torch.profiler import ProfilerActivity, profile
+    fn()
+    torch.cuda.synchronize()
+    with profile(activities=[ProfilerActivity.CUDA]) as prof:
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+    out = {}
+    for e in prof.key_averages():
+        tot = getattr(e, "device_time_total", None)
+        if tot is None:
+            tot = getattr(e, "cuda_time_total", 0.0)
+        if e.count and tot:
+            out[e.key] = tot / 1e6 / reps
+    return out
+
+
 # ------------------------------------------------------------------ algorithmic bytes of the chain
 def _q5_taps(n_in, n_out):
     """Source samples the half-pixel Q5 resize of n_in -> n_out reads with a
@@ -402,6 +422,30 @@ def fused_pipeline(dev, stream, steps=3, warmup=2, n=FUSED_N):
                        "frac": round((rd + wr) / tf / 1e9 / hbm, 4),
                        "read": "distinct 32-byte sectors of the crops' nonzero-weight bilinear taps (exact count)"}
     res["speedup_vs_plain"] = res["plain"]["ms"] / res["fused"]["ms"]
+    # the plain path's materialised bytes (each step reads and writes its
+    # intermediate: uint8 224^2 x 3 after the resize, the flip and the table,
+    # float32 after the saturation, bf16 out) and, per step, its kernel time
+    P3 = 3 * 224 * 224
+    plain_alg = rd + FUSED_N * (P3 + 2 * P3 + 2 * P3 + (P3 + 4 * P3) + (4 * P3 + 2 * P3))
+    tp = res["plain"]["ms"] / 1e3
+    res["plain_roofline"] = {"algorithmic_bytes": plain_alg, "achieved": round(plain_alg / tp / 1e9, 1),
+                             "frac": round(plain_alg / tp / 1e9 / hbm, 4)}
+    steps_bytes = {"k_resize_rows": rd + FUSED_N * P3, "k_pixmap3": FUSED_N * 2 * P3, "k_lut_bulk": FUSED_N * 2 * P3,
+                   "k_plain_saturate": FUSED_N * 5 * P3, "k_plain_normalize": FUSED_N * 6 * P3,
+                   "k_chain_fused": rd + wr}
+    try:
+        kt = kernel_times(lambda: run(A.MODE_PLAIN, wsp), reps=3)
+        kt.update({k: v for k, v in kernel_times(lambda: run(A.MODE_FUSED, wsf), reps=3).items() if "k_chain_fused" in k})
+        step_res = {}
+        for name, t in kt.items():
+            base = next((b for b in steps_bytes if b in name), None)
+            if base is None or t <= 0:
+                continue
+            step_res[base] = {"ms": round(t * 1e3, 4), "gbs": round(steps_bytes[base] / t / 1e9, 1),
+                           "frac": round(steps_bytes[base] / t / 1e9 / hbm, 4)}
+        res["steps"] = step_res
+    except Exception as ex:  # the per-kernel breakdown needs the profiler's CUDA activity trace
+        res["steps"] = {"error": str(ex)[:160]}
     # jitter mode 1: per-image random order and image-mean contrast pivot (a
     # per-image reduction before the write pass), fused vs plain
     jcfg = A.chain_cfg(jitter=1)

@@ -469,106 +469,285 @@ __global__ void k_chain_boxes(int32_t n, const alb_params* __restrict__ prm, Cha
 }
 
 // ---------------------------------------------------------------- plain path
-__global__ void k_plain_resize(int32_t n, const alb_params* __restrict__ prm, const alb_image* __restrict__ imgs,
-                               ChainK K, uint8_t* __restrict__ out) {
-  const int64_t total = (int64_t)n * K.oh * K.ow;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t b = (int32_t)(i / ((int64_t)K.oh * K.ow));
-    const int32_t r = (int32_t)(i - (int64_t)b * K.oh * K.ow);
-    const int32_t y = r / K.ow, x = r - y * K.ow;
+// The comparison path runs one step per launch through the library's own
+// per-transform machinery, every intermediate materialised:
+//   crop + resize  -> the ragged RandomResizedCrop launch (tile plan +
+//                     k_resize_rows) into uint8 224 x 224 images,
+//   h-flip         -> the ragged HorizontalFlip launch (k_pixmap3),
+//   colour table   -> the bulk-copy LUT kernel (k_lut_bulk) with the chain's
+//                     per-image tables,
+//   saturation     -> uint8 -> float32 (mode 0) or the jitter steps uint8 ->
+//                     uint8 (mode 1), 16-byte vectors,
+//   Normalize      -> float32 / uint8 HWC -> bf16 NCHW, 16-byte vectors.
+// The per-step kernels below take one image per grid row (blockIdx.y), so
+// per-image constants are loaded once and no pixel index is divided; images
+// whose plane is a multiple of 16 pixels take the vector path, others one
+// pixel per thread.  Same rounding points as the fused kernel, so the output
+// is identical.
+
+// per image: the step records of the per-transform launches and the
+// descriptors of the two uint8 intermediates
+__global__ void k_plain_records(int32_t n, const alb_params* __restrict__ prm, ChainK K, uint8_t* a, uint8_t* b,
+                                alb_params* __restrict__ rrc, alb_params* __restrict__ flip,
+                                alb_params* __restrict__ lut, alb_image* __restrict__ da,
+                                alb_image* __restrict__ db) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const alb_params p = prm[i];
+  alb_params r = p;
+  r.tid = ALB_RANDOM_RESIZED_CROP; r.apply = 1; r.out_h = K.oh; r.out_w = K.ow;
+  rrc[i] = r;
+  alb_params f = p;
+  f.tid = ALB_HFLIP; f.apply = p.flip != 0; f.in_h = f.out_h = K.oh; f.in_w = f.out_w = K.ow;
+  flip[i] = f;
+  alb_params l = p;
+  l.tid = ALB_BRIGHTNESS_CONTRAST; l.apply = 1; l.in_h = l.out_h = K.oh; l.in_w = l.out_w = K.ow;
+  lut[i] = l;
+  const int64_t plane = (int64_t)K.oh * K.ow * 3;
+  alb_image im;
+  im.h = K.oh; im.w = K.ow; im.c = 3; im.reserved = 0; im.row_stride = 3 * (int64_t)K.ow;
+  im.data = a + (int64_t)i * plane;
+  da[i] = im;
+  im.data = b + (int64_t)i * plane;
+  db[i] = im;
+}
+
+// the chain's colour table of each image, replicated for the three channels
+// (the layout of the LUT kernel's per-image tables)
+__global__ void k_plain_luts768(int32_t n, const uint8_t* __restrict__ luts256, uint8_t* __restrict__ luts768) {
+  const int b = blockIdx.x, v = threadIdx.x;
+  if (b >= n) return;
+  const uint8_t t = luts256[(int64_t)b * 256 + v];
+  uint8_t* o = luts768 + (int64_t)b * 768;
+  o[v] = t; o[256 + v] = t; o[512 + v] = t;
+}
+
+ALB_D void ld48(const uint8_t* p, uint8_t (&v)[48]) {
+  const uint4* q = reinterpret_cast<const uint4*>(p);
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    const uint4 t = q[k];
+    const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+    for (int j = 0; j < 16; j++) v[16 * k + j] = (uint8_t)(w[j >> 2] >> (8 * (j & 3)));
+  }
+}
+
+ALB_D void st48(uint8_t* p, const uint8_t (&v)[48]) {
+  uint4* q = reinterpret_cast<uint4*>(p);
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    uint32_t w[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int j = 0; j < 16; j++) w[j >> 2] |= (uint32_t)v[16 * k + j] << (8 * (j & 3));
+    q[k] = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+// mode 0 saturation: uint8 RGB -> float32 blend (clamped, not rounded)
+__global__ void __launch_bounds__(256) k_plain_saturate(int32_t n, const alb_params* __restrict__ prm, int64_t P,
+                                                        const uint8_t* __restrict__ in, float* __restrict__ out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int b = blockIdx.y; b < n; b += gridDim.y) {
+    const float s = (float)prm[b].sat;
+    const uint8_t* ib = in + (int64_t)b * P * 3;
+    float* ob = out + (int64_t)b * P * 3;
+    if ((P & 15) == 0) {
+      for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < P / 16; g += stride) {
+        uint8_t v[48];
+        ld48(ib + 48 * g, v);
+        float4* o4 = reinterpret_cast<float4*>(ob + 48 * g);
+#pragma unroll
+        for (int q = 0; q < 4; q++) {          // 4 pixels = 12 floats = 3 float4 per step
+          float f[12];
+#pragma unroll
+          for (int j = 0; j < 4; j++) {
+            const uint32_t rgb[3] = {v[12 * q + 3 * j], v[12 * q + 3 * j + 1], v[12 * q + 3 * j + 2]};
+            chain_saturate(rgb, s, f + 3 * j);
+          }
+          o4[3 * q] = make_float4(f[0], f[1], f[2], f[3]);
+          o4[3 * q + 1] = make_float4(f[4], f[5], f[6], f[7]);
+          o4[3 * q + 2] = make_float4(f[8], f[9], f[10], f[11]);
+        }
+      }
+    } else {
+      for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += stride) {
+        const uint32_t rgb[3] = {ib[3 * i], ib[3 * i + 1], ib[3 * i + 2]};
+        chain_saturate(rgb, s, ob + 3 * i);
+      }
+    }
+  }
+}
+
+// Normalize: float32 HWC -> bf16 NCHW
+__global__ void __launch_bounds__(256) k_plain_normalize(int32_t n, ChainK K, int64_t P, const float* __restrict__ in,
+                                                         __nv_bfloat16* __restrict__ out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int b = blockIdx.y; b < n; b += gridDim.y) {
+    const float* ib = in + (int64_t)b * P * 3;
+    __nv_bfloat16* ob = out + (int64_t)b * 3 * P;
+    if ((P & 7) == 0) {
+      for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < P / 8; g += stride) {
+        const float4* i4 = reinterpret_cast<const float4*>(ib + 24 * g);
+        float f[24];
+#pragma unroll
+        for (int q = 0; q < 6; q++) {
+          const float4 t = i4[q];
+          f[4 * q] = t.x; f[4 * q + 1] = t.y; f[4 * q + 2] = t.z; f[4 * q + 3] = t.w;
+        }
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          uint32_t w[4];
+#pragma unroll
+          for (int j = 0; j < 4; j++) {
+            const __nv_bfloat16 lo = chain_normalize(f[3 * (2 * j) + c], K.k[c], K.m[c]);
+            const __nv_bfloat16 hi = chain_normalize(f[3 * (2 * j + 1) + c], K.k[c], K.m[c]);
+            w[j] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+          }
+          *reinterpret_cast<uint4*>(ob + (int64_t)c * P + 8 * g) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+      }
+    } else {
+      for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += stride)
+        for (int c = 0; c < 3; c++) ob[(int64_t)c * P + i] = chain_normalize(ib[3 * i + c], K.k[c], K.m[c]);
+    }
+  }
+}
+
+// jitter mode 1: contrast-pivot sums (integer BT.601 grey) of the images
+// whose op at position `step` is C, one block reduction and one atomic per
+// block
+__global__ void __launch_bounds__(256) k_plain_pivot(int32_t n, const alb_params* __restrict__ prm, int64_t P,
+                                                     int32_t step, const uint8_t* __restrict__ in,
+                                                     unsigned long long* __restrict__ sums) {
+  __shared__ uint32_t red[8];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int b = blockIdx.y; b < n; b += gridDim.y) {
+    if (jitter_op(prm[b].k, step) != 1) continue;         // block-uniform
+    const uint8_t* ib = in + (int64_t)b * P * 3;
+    uint32_t acc = 0;
+    if ((P & 15) == 0) {
+      for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < P / 16; g += stride) {
+        uint8_t v[48];
+        ld48(ib + 48 * g, v);
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+          const uint32_t rgb[3] = {v[3 * j], v[3 * j + 1], v[3 * j + 2]};
+          acc += grey_bt601(rgb);
+        }
+      }
+    } else {
+      for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += stride) {
+        const uint32_t rgb[3] = {ib[3 * i], ib[3 * i + 1], ib[3 * i + 2]};
+        acc += grey_bt601(rgb);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long t = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += red[w];
+      if (t) atomicAdd(&sums[b], t);
+    }
+    __syncthreads();
+  }
+}
+
+// jitter mode 1: each image's op at position `step` (B or C through its
+// table, S as the rounded float32 blend), uint8 -> uint8
+__global__ void __launch_bounds__(256) k_plain_jitter_step(int32_t n, const alb_params* __restrict__ prm, int64_t P,
+                                                           int32_t step, const uint8_t* __restrict__ luts,
+                                                           const uint8_t* __restrict__ in, uint8_t* __restrict__ out) {
+  __shared__ uint8_t tab[256];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int b = blockIdx.y; b < n; b += gridDim.y) {
     const alb_params& p = prm[b];
-    const alb_image im = imgs[b];
-    const uint8_t* win = (const uint8_t*)im.data + (int64_t)p.y0 * im.row_stride + 3 * (int64_t)p.x0;
-    uint32_t rgb[3];
-    chain_bilinear(win, im.row_stride, p.ch, p.cw, chain_q5(x, p.cw, K.ow), chain_q5(y, p.ch, K.oh), rgb);
-    for (int c = 0; c < 3; c++) out[3 * i + c] = (uint8_t)rgb[c];
+    const int op = jitter_op(p.k, step);
+    const float s = (float)p.sat;
+    __syncthreads();
+    if (op != 2) tab[threadIdx.x] = luts[(int64_t)b * 512 + (op == 1 ? 256 : 0) + threadIdx.x];
+    __syncthreads();
+    const uint8_t* ib = in + (int64_t)b * P * 3;
+    uint8_t* ob = out + (int64_t)b * P * 3;
+    if ((P & 15) == 0) {
+      for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < P / 16; g += stride) {
+        uint8_t v[48];
+        ld48(ib + 48 * g, v);
+        if (op == 2) {
+#pragma unroll
+          for (int j = 0; j < 16; j++) {
+            uint32_t rgb[3] = {v[3 * j], v[3 * j + 1], v[3 * j + 2]};
+            jitter_saturate(rgb, s);
+            v[3 * j] = (uint8_t)rgb[0]; v[3 * j + 1] = (uint8_t)rgb[1]; v[3 * j + 2] = (uint8_t)rgb[2];
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 48; j++) v[j] = tab[v[j]];
+        }
+        st48(ob + 48 * g, v);
+      }
+    } else {
+      for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += stride) {
+        uint32_t rgb[3] = {ib[3 * i], ib[3 * i + 1], ib[3 * i + 2]};
+        if (op == 2) jitter_saturate(rgb, s);
+        else { rgb[0] = tab[rgb[0]]; rgb[1] = tab[rgb[1]]; rgb[2] = tab[rgb[2]]; }
+        for (int c = 0; c < 3; c++) ob[3 * i + c] = (uint8_t)rgb[c];
+      }
+    }
   }
 }
 
-__global__ void k_plain_flip(int32_t n, const alb_params* __restrict__ prm, ChainK K, const uint8_t* __restrict__ in,
-                             uint8_t* __restrict__ out) {
-  const int64_t total = (int64_t)n * K.oh * K.ow;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t b = (int32_t)(i / ((int64_t)K.oh * K.ow));
-    const int32_t x = (int32_t)(i % K.ow);
-    const int64_t src = prm[b].flip ? i - x + (K.ow - 1 - x) : i;
-    for (int c = 0; c < 3; c++) out[3 * i + c] = in[3 * src + c];
+// jitter mode 1 Normalize: uint8 HWC -> bf16 NCHW
+__global__ void __launch_bounds__(256) k_plain_normalize_u8(int32_t n, ChainK K, int64_t P,
+                                                            const uint8_t* __restrict__ in,
+                                                            __nv_bfloat16* __restrict__ out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int b = blockIdx.y; b < n; b += gridDim.y) {
+    const uint8_t* ib = in + (int64_t)b * P * 3;
+    __nv_bfloat16* ob = out + (int64_t)b * 3 * P;
+    if ((P & 15) == 0) {
+      for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < P / 16; g += stride) {
+        uint8_t v[48];
+        ld48(ib + 48 * g, v);
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          uint32_t w[8];
+#pragma unroll
+          for (int j = 0; j < 8; j++) {
+            const __nv_bfloat16 lo = chain_normalize((float)v[3 * (2 * j) + c], K.k[c], K.m[c]);
+            const __nv_bfloat16 hi = chain_normalize((float)v[3 * (2 * j + 1) + c], K.k[c], K.m[c]);
+            w[j] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+          }
+          uint4* o4 = reinterpret_cast<uint4*>(ob + (int64_t)c * P + 16 * g);
+          o4[0] = make_uint4(w[0], w[1], w[2], w[3]);
+          o4[1] = make_uint4(w[4], w[5], w[6], w[7]);
+        }
+      }
+    } else {
+      for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += stride)
+        for (int c = 0; c < 3; c++) ob[(int64_t)c * P + i] = chain_normalize((float)ib[3 * i + c], K.k[c], K.m[c]);
+    }
   }
 }
 
-__global__ void k_plain_lut(int32_t n, ChainK K, const uint8_t* __restrict__ luts, const uint8_t* __restrict__ in,
-                            uint8_t* __restrict__ out) {
-  const int64_t total = (int64_t)n * K.oh * K.ow * 3;
-  const int64_t per = (int64_t)K.oh * K.ow * 3;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = luts[(i / per) * 256 + in[i]];
+// grid of the per-image step kernels: enough blocks per image to give every
+// thread about one 16-pixel group, images on the grid's y axis
+static dim3 plain_grid(int32_t n, int64_t P) {
+  const int64_t groups = (P + 15) / 16;
+  const int64_t bx = (groups + 255) / 256;
+  return dim3((unsigned)(bx < 1 ? 1 : (bx > 1024 ? 1024 : bx)), (unsigned)(n < 65535 ? n : 65535));
 }
-
-__global__ void k_plain_saturate(int32_t n, const alb_params* __restrict__ prm, ChainK K,
-                                 const uint8_t* __restrict__ in, float* __restrict__ out) {
-  const int64_t total = (int64_t)n * K.oh * K.ow;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t b = (int32_t)(i / ((int64_t)K.oh * K.ow));
-    const uint32_t rgb[3] = {in[3 * i], in[3 * i + 1], in[3 * i + 2]};
-    float v[3];
-    chain_saturate(rgb, (float)prm[b].sat, v);
-    for (int c = 0; c < 3; c++) out[3 * i + c] = v[c];
-  }
-}
-
-__global__ void k_plain_normalize(int32_t n, ChainK K, const float* __restrict__ in, __nv_bfloat16* __restrict__ out) {
-  const int64_t plane = (int64_t)K.oh * K.ow;
-  const int64_t total = (int64_t)n * plane;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t b = i / plane, r = i - b * plane;
-    for (int c = 0; c < 3; c++) out[(b * 3 + c) * plane + r] = chain_normalize(in[3 * i + c], K.k[c], K.m[c]);
-  }
-}
-
-// plain path, jitter mode 1: contrast pivot sums of the images whose op at
-// position `step` is C, from the materialised uint8 image
-__global__ void k_plain_pivot(int32_t n, const alb_params* __restrict__ prm, ChainK K, int32_t step,
-                              const uint8_t* __restrict__ in, unsigned long long* __restrict__ sums) {
-  const int64_t plane = (int64_t)K.oh * K.ow;
-  const int64_t total = (int64_t)n * plane;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t b = (int32_t)(i / plane);
-    if (jitter_op(prm[b].k, step) != 1) continue;
-    const uint32_t rgb[3] = {in[3 * i], in[3 * i + 1], in[3 * i + 2]};
-    atomicAdd(&sums[b], (unsigned long long)grey_bt601(rgb));
-  }
-}
-
-// plain path, jitter mode 1: each image's op at position `step`
-__global__ void k_plain_jitter_step(int32_t n, const alb_params* __restrict__ prm, ChainK K, int32_t step,
-                                    const uint8_t* __restrict__ luts, const uint8_t* __restrict__ in,
-                                    uint8_t* __restrict__ out) {
-  const int64_t plane = (int64_t)K.oh * K.ow;
-  const int64_t total = (int64_t)n * plane;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t b = (int32_t)(i / plane);
-    const alb_params& p = prm[b];
-    uint32_t rgb[3] = {in[3 * i], in[3 * i + 1], in[3 * i + 2]};
-    const uint8_t* L = luts + (int64_t)b * 512;
-    jitter_ops(rgb, p.k, step, step + 1, L, L + 256, (float)p.sat);
-    for (int c = 0; c < 3; c++) out[3 * i + c] = (uint8_t)rgb[c];
-  }
-}
-
-__global__ void k_plain_normalize_u8(int32_t n, ChainK K, const uint8_t* __restrict__ in, __nv_bfloat16* __restrict__ out) {
-  const int64_t plane = (int64_t)K.oh * K.ow;
-  const int64_t total = (int64_t)n * plane;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t b = i / plane, r = i - b * plane;
-    for (int c = 0; c < 3; c++) out[(b * 3 + c) * plane + r] = chain_normalize((float)in[3 * i + c], K.k[c], K.m[c]);
-  }
-}
-
 // ---------------------------------------------------------------- launcher
+constexpr int32_t kPlainItemBytes = 16384;   // output bytes per work item of the plain path's ragged launches
+
 size_t chain_workspace(const alb_chain_cfg& cfg, int32_t n, int32_t mode) {
   size_t px = (size_t)n * cfg.out_h * cfg.out_w;
   size_t b = 4096 + (size_t)n * 512 + (size_t)n * 8 + 512;   // queue, tables, pivot sums
-  if (mode == ALB_MODE_PLAIN) b += 2 * px * 3 + px * 3 * 4 + 1024;
+  if (mode == ALB_MODE_PLAIN)   // intermediates, step records, descriptors, plan, 3-channel tables
+    b += 2 * px * 3 + px * 3 * 4 + (size_t)n * 3 * sizeof(alb_params) + (size_t)n * 2 * sizeof(alb_image) +
+         (size_t)(2 * n + 1) * 4 + (size_t)n * 768 + 8 * 256;
   return b;
 }
 
@@ -797,46 +976,74 @@ alb_status launch_chain(const alb_chain_cfg& cfg, int32_t n, const alb_params* p
     ALB_CUDA(cudaGetLastError());
     return ALB_OK;
   }
-  const size_t px = (size_t)n * cfg.out_h * cfg.out_w;
+  // plain path: one step per launch, intermediates materialised
+  const int64_t P = (int64_t)cfg.out_h * cfg.out_w;
+  const size_t px = (size_t)n * P;
   uint8_t* a = ws.take<uint8_t>(px * 3);
   uint8_t* b = ws.take<uint8_t>(px * 3);
   float* f = jit ? nullptr : ws.take<float>(px * 3);
-  ALB_REQUIRE(a && b && (jit || f), ALB_EWORKSPACE, "alb_apply_batch: workspace too small for plain mode");
-  const int grid = 8 * sm_count();
-  k_plain_resize<<<grid, 256, 0, st>>>(n, params, in, K, a);
+  alb_params* rec = ws.take<alb_params>((size_t)n * 3);
+  alb_image* desc = ws.take<alb_image>((size_t)n * 2);
+  int32_t* prefix = ws.take<int32_t>((size_t)n + 1);
+  int32_t* rpi = ws.take<int32_t>((size_t)n);
+  uint8_t* luts768 = jit ? nullptr : ws.take<uint8_t>((size_t)n * 768);
+  ALB_REQUIRE(a && b && (jit || (f && luts768)) && rec && desc && prefix && rpi, ALB_EWORKSPACE,
+              "alb_apply_batch: workspace too small for plain mode");
+  alb_params *rrc = rec, *fl = rec + n, *lr = rec + 2 * n;
+  alb_image *da = desc, *db = desc + n;
+  k_plain_records<<<(n + 127) / 128, 128, 0, st>>>(n, params, K, a, b, rrc, fl, lr, da, db);
   ALB_CUDA(cudaGetLastError());
-  k_plain_flip<<<grid, 256, 0, st>>>(n, params, K, a, b);
-  ALB_CUDA(cudaGetLastError());
+  const ImgList lin{in, {}}, la{da, {}}, lb{db, {}};
+  const Plan plan{prefix, rpi, n};
+  // crop + resize: the ragged RandomResizedCrop launch
+  {
+    const PrmList pr{rrc, {}};
+    const PlanCheck chk{ALB_RANDOM_RESIZED_CROP, 3, true, lin, pr, status, 0};
+    alb_status rc = launch_plan(la, n, kPlainItemBytes, prefix, rpi, chk, st);
+    if (rc == ALB_OK) rc = launch_geometric(ALB_RANDOM_RESIZED_CROP, plan, lin, la, pr, 3, false, status, st);
+    if (rc != ALB_OK) return rc;
+  }
+  // h-flip: the ragged HorizontalFlip launch
+  {
+    const PrmList pr{fl, {}};
+    const PlanCheck chk{ALB_HFLIP, 3, true, la, pr, status, 0};
+    alb_status rc = launch_plan(lb, n, kPlainItemBytes, prefix, rpi, chk, st);
+    if (rc == ALB_OK) rc = launch_geometric(ALB_HFLIP, plan, la, lb, pr, 3, false, status, st);
+    if (rc != ALB_OK) return rc;
+  }
+  const dim3 grid = plain_grid(n, P);
   if (jit) {
     // one launch per position of the order; before each, the pivots of the
     // images whose contrast runs at that position, and their C tables
     uint8_t* cur = b;
     uint8_t* nxt = a;
     for (int step = 0; step < 3; step++) {
-      k_plain_pivot<<<grid, 256, 0, st>>>(n, params, K, step, cur, sums);
+      k_plain_pivot<<<grid, 256, 0, st>>>(n, params, P, step, cur, sums);
       ALB_CUDA(cudaGetLastError());
       k_jitter_luts<<<n, 256, 0, st>>>(n, params, sums, npx, 1, luts);
       ALB_CUDA(cudaGetLastError());
-      k_plain_jitter_step<<<grid, 256, 0, st>>>(n, params, K, step, luts, cur, nxt);
+      k_plain_jitter_step<<<grid, 256, 0, st>>>(n, params, P, step, luts, cur, nxt);
       ALB_CUDA(cudaGetLastError());
       uint8_t* t = cur; cur = nxt; nxt = t;
     }
-    k_plain_normalize_u8<<<grid, 256, 0, st>>>(n, K, cur, o);
+    k_plain_normalize_u8<<<grid, 256, 0, st>>>(n, K, P, cur, o);
     ALB_CUDA(cudaGetLastError());
-    if (mask_in) {
-      k_chain_masks<<<grid, 256, 0, st>>>(n, params, in, K, mask_in, mask_out, status);
-      ALB_CUDA(cudaGetLastError());
-    }
-    return ALB_OK;
+  } else {
+    // brightness / contrast table: the bulk-copy LUT kernel with the chain's tables
+    k_plain_luts768<<<n, 256, 0, st>>>(n, luts, luts768);
+    ALB_CUDA(cudaGetLastError());
+    const PrmList pr{lr, {}};
+    const PlanCheck chk{ALB_BRIGHTNESS_CONTRAST, 3, false, lb, pr, status, 0};
+    alb_status rc = launch_plan(la, n, kPlainItemBytes, prefix, rpi, chk, st);
+    if (rc == ALB_OK) rc = launch_stream_lut(plan, lb, la, luts768, status, st);
+    if (rc != ALB_OK) return rc;
+    k_plain_saturate<<<grid, 256, 0, st>>>(n, params, P, a, f);
+    ALB_CUDA(cudaGetLastError());
+    k_plain_normalize<<<grid, 256, 0, st>>>(n, K, P, f, o);
+    ALB_CUDA(cudaGetLastError());
   }
-  k_plain_lut<<<grid, 256, 0, st>>>(n, K, luts, b, a);
-  ALB_CUDA(cudaGetLastError());
-  k_plain_saturate<<<grid, 256, 0, st>>>(n, params, K, a, f);
-  ALB_CUDA(cudaGetLastError());
-  k_plain_normalize<<<grid, 256, 0, st>>>(n, K, f, o);
-  ALB_CUDA(cudaGetLastError());
   if (mask_in) {
-    k_chain_masks<<<grid, 256, 0, st>>>(n, params, in, K, mask_in, mask_out, status);
+    k_chain_masks<<<8 * sm_count(), 256, 0, st>>>(n, params, in, K, mask_in, mask_out, status);
     ALB_CUDA(cudaGetLastError());
   }
   return ALB_OK;

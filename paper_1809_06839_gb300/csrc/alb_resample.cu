@@ -116,6 +116,17 @@ ALB_D void taps_row(const uint8_t* base, int o, uint32_t& lo, uint32_t& hi) {
   hi = __funnelshift_r(w1, w2, s);
 }
 
+// the 6 bytes at p (pixels ix, ix + 1 of a row) as lo = bytes 0..3, hi = 4..5;
+// aligned word loads, the third only when it holds a needed byte
+ALB_D void ldg_pair(const uint8_t* p, uint32_t& lo, uint32_t& hi) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+  const uint32_t* w = reinterpret_cast<const uint32_t*>(a & ~uintptr_t(3));
+  const int s = (int)(a & 3);
+  const uint32_t w0 = __ldg(w), w1 = __ldg(w + 1), w2 = s == 3 ? __ldg(w + 2) : 0u;
+  lo = __funnelshift_r(w0, w1, 8 * s);
+  hi = __funnelshift_r(w1, w2, 8 * s);
+}
+
 // Q5 bilinear of one RGB pixel from the two tap rows (lo = bytes 0..3, hi =
 // bytes 4..5 of the 6-byte pair (ix, ix + 1) of each row), exactly
 // (sum w_ij p_ij + 512) >> 10 with w_ij = wx_i * wy_j, evaluated as
@@ -580,13 +591,21 @@ ALB_D void r_tile_compute(const RImg& k, const RTile& g, int lane, int32_t vcol,
       }
     }
   } else {
-    // footprint larger than the box: taps straight from the source window
+    // footprint larger than the box: taps straight from the source window,
+    // the pair (sx0, sx0 + 1) as aligned words (every word read holds a byte
+    // of the pair); at the clamped last column (sx1 == sx0, weight fx = 0)
+    // byte by byte
     const int32_t sx0 = k.wx0 + (vcol >> 5), sx1 = k.wx0 + imin((vcol >> 5) + 1, k.cw - 1);
     auto hrow = [&](int32_t sy, uint32_t (&h)[3]) {
       const uint8_t* row = k.src + (int64_t)sy * k.sstride;
-      const uint32_t lo = (uint32_t)row[3 * sx0] | ((uint32_t)row[3 * sx0 + 1] << 8) |
-                          ((uint32_t)row[3 * sx0 + 2] << 16) | ((uint32_t)row[3 * sx1] << 24);
-      const uint32_t hi = (uint32_t)row[3 * sx1 + 1] | ((uint32_t)row[3 * sx1 + 2] << 8);
+      uint32_t lo, hi;
+      if (sx1 == sx0 + 1) {
+        ldg_pair(row + 3 * sx0, lo, hi);
+      } else {
+        lo = (uint32_t)row[3 * sx0] | ((uint32_t)row[3 * sx0 + 1] << 8) | ((uint32_t)row[3 * sx0 + 2] << 16) |
+             ((uint32_t)row[3 * sx1] << 24);
+        hi = (uint32_t)row[3 * sx1 + 1] | ((uint32_t)row[3 * sx1 + 2] << 8);
+      }
       r_hrow(lo, hi, wx, h);
     };
     for (int r = 0; r < g.th; r++, od += k.dstride) {
@@ -847,17 +866,6 @@ __global__ void __launch_bounds__(32 * AWARP, 6) k_warp_affine3(Plan plan, ImgLi
 // field is smooth, neighbouring lanes read neighbouring bytes), reflected
 // per tap at the image border.
 constexpr int ET_W = 32, ET_H = 16, EWARP = 4, ELAT = 64;
-
-// the 6 bytes at p (pixels ix, ix + 1 of a row) as lo = bytes 0..3, hi = 4..5;
-// aligned word loads, the third only when it holds a needed byte
-ALB_D void ldg_pair(const uint8_t* p, uint32_t& lo, uint32_t& hi) {
-  const uintptr_t a = reinterpret_cast<uintptr_t>(p);
-  const uint32_t* w = reinterpret_cast<const uint32_t*>(a & ~uintptr_t(3));
-  const int s = (int)(a & 3);
-  const uint32_t w0 = __ldg(w), w1 = __ldg(w + 1), w2 = s == 3 ? __ldg(w + 2) : 0u;
-  lo = __funnelshift_r(w0, w1, 8 * s);
-  hi = __funnelshift_r(w1, w2, 8 * s);
-}
 
 // the same pair format from two arbitrary (reflected) pixels
 ALB_D void gather_pair(const uint8_t* row, int32_t xa, int32_t xb, uint32_t& lo, uint32_t& hi) {
