@@ -42,8 +42,7 @@ UNIT = "images/s"
 # suite workload (same H, W distribution), scaled per image; the roofline's
 # traffic figure is this times the images of one launch.  Only kernels whose
 # code is unchanged since that capture are listed.
-NCU_DRAM_BYTES_PER_IMAGE = {"Rotate": 1138010.0, "ShiftScaleRotate": 1046432.0, "Resize512": 1166141.0,
-                            "ShiftHSV": 846090.0, "PadToSize512": 1172000.0}
+NCU_DRAM_BYTES_PER_IMAGE = {"ShiftHSV": 846090.0, "PadToSize512": 1172000.0}
 SUITE_N, SUITE_LO, SUITE_HI = 2000, 333, 500
 FUSED_N, FUSED_LO, FUSED_HI = 4096, 256, 1024
 DET_N, DET_HW = 256, 1024
@@ -276,12 +275,21 @@ def suite_e2e(suite, stream, steps, copy_streams=2):
     return dict(t=t, wall=wall, bi=bi, bo=bo)
 
 
+_PROFILER_READY = False
+
+
 def kernel_times(fn, reps=3):
     """Average device time per launch of each kernel that `fn` launches, from
     the profiler's CUDA activity trace (seconds, keyed by kernel name)."""
     from torch.profiler import ProfilerActivity, profile
     fn()
     torch.cuda.synchronize()
+    global _PROFILER_READY
+    if not _PROFILER_READY:          # the first session of a process records no kernels
+        with profile(activities=[ProfilerActivity.CUDA]):
+            fn()
+            torch.cuda.synchronize()
+        _PROFILER_READY = True
     with profile(activities=[ProfilerActivity.CUDA]) as prof:
         for _ in range(reps):
             fn()

@@ -739,9 +739,40 @@ ALB_D void a_tile_geo(const AImg& k, int32_t item, ATile& g) {
 
 // Lane r (and r + 32) stages box row r (reflected source row): raw aligned
 // chunks; rowoff[r] = r * pitch + the row's byte phase.
+// x-extent [lo, hi] of the parallelogram V0 V1 V2 V3 (in order) inside the
+// horizontal band [yl, yh]; lo > hi when they do not meet
+ALB_D void band_extent(const float (&vx)[4], const float (&vy)[4], float yl, float yh, float& lo, float& hi) {
+  lo = 3e38f; hi = -3e38f;
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    const float x0 = vx[i], y0 = vy[i], x1 = vx[(i + 1) & 3], y1 = vy[(i + 1) & 3];
+    if (y0 >= yl && y0 <= yh) { lo = fminf(lo, x0); hi = fmaxf(hi, x0); }
+    const float dy = y1 - y0;
+    if (dy != 0.0f) {
+      const float rdx = (x1 - x0) / dy;
+      const float ta = yl - y0, tb = yh - y0;
+      if ((ta > 0.0f) == (ta < dy) && ta != 0.0f) { const float x = fmaf(ta, rdx, x0); lo = fminf(lo, x); hi = fmaxf(hi, x); }
+      if ((tb > 0.0f) == (tb < dy) && tb != 0.0f) { const float x = fmaf(tb, rdx, x0); lo = fminf(lo, x); hi = fmaxf(hi, x); }
+    }
+  }
+}
+
 ALB_D void a_tile_stage(const AImg& k, const ATile& g, int lane, uint8_t* box, int32_t* rowoff) {
   if (g.mode == 2) return;
   const int span = 3 * (g.rb - g.ra + 1);
+  // inside tiles stage, per box row, only the columns that the tile's taps
+  // can read: the mapped tile (a parallelogram, box-relative pixel units with
+  // the Q16 -> Q5 rounding bias) meets row r's band [r - 1, r + 1) of tap
+  // rows; columns floor(x) and floor(x) + 1 of that extent, with a margin
+  float vx[4], vy[4];
+  if (g.mode == 0) {
+    const float s = 1.0f / 65536.0f;
+    const float x0 = (float)(g.X00 + 1024 - 65536 * (int64_t)g.bx0) * s, y0 = (float)(g.Y00 + 1024 - 65536 * (int64_t)g.by0) * s;
+    const float ux = (float)(k.q[0] * (g.tw - 1)) * s, uy = (float)(k.q[3] * (g.tw - 1)) * s;
+    const float wx = (float)(k.q[1] * (g.th - 1)) * s, wy = (float)(k.q[4] * (g.th - 1)) * s;
+    vx[0] = x0; vy[0] = y0; vx[1] = x0 + ux; vy[1] = y0 + uy;
+    vx[2] = x0 + ux + wx; vy[2] = y0 + uy + wy; vx[3] = x0 + wx; vy[3] = y0 + wy;
+  }
   for (int r = lane; r < g.bh; r += 32) {
     const int ry = reflect101(g.by0 + r, k.H);
     const uintptr_t first = reinterpret_cast<uintptr_t>(k.src) + (uintptr_t)((int64_t)ry * k.sstride) +
@@ -749,9 +780,18 @@ ALB_D void a_tile_stage(const AImg& k, const ATile& g, int lane, uint8_t* box, i
     const uintptr_t c0 = first & ~uintptr_t(15);
     const int ph = (int)(first - c0);
     rowoff[r] = r * APITCH + ph;
-    const int nch = (ph + span + 15) >> 4;
+    int j0 = 0, j1 = ((ph + span + 15) >> 4) - 1;
+    if (g.mode == 0) {
+      float lo, hi;
+      band_extent(vx, vy, (float)r - 1.05f, (float)r + 1.05f, lo, hi);
+      if (lo > hi) continue;                                   // no tap reads this row
+      const int cl = imax((int)floorf(lo - 0.05f), 0), chh = imin((int)floorf(hi + 0.05f) + 1, g.bw - 1);
+      if (cl > chh) continue;
+      j0 = (ph + 3 * cl) >> 4;
+      j1 = imin(j1, (ph + 3 * chh + 2) >> 4);
+    }
     uint8_t* d = box + r * APITCH;
-    for (int j = 0; j < nch; j++) cp_async16(d + 16 * j, reinterpret_cast<const void*>(c0 + 16 * j));
+    for (int j = j0; j <= j1; j++) cp_async16(d + 16 * j, reinterpret_cast<const void*>(c0 + 16 * j));
   }
 }
 
@@ -777,10 +817,13 @@ ALB_D void a_tile_compute(const AImg& k, const ATile& g, int lane, const uint8_t
         uint32_t tl, th2, bl, bh2;
         taps_row(box, rowoff[iy] + o, tl, th2);
         taps_row(box, rowoff[iy + 1] + o, bl, bh2);
-        const uint32_t wx = (uint32_t)(32 + 255 * fx), wy = (uint32_t)(32 + 255 * fy);   // (32 - f) | f << 8
-        const uint32_t hr = __dp4a(__byte_perm(tl, th2, 0x0030), wx, 0u), br = __dp4a(__byte_perm(bl, bh2, 0x0030), wx, 0u);
-        const uint32_t hg = __dp4a(__byte_perm(tl, th2, 0x0041), wx, 0u), bg = __dp4a(__byte_perm(bl, bh2, 0x0041), wx, 0u);
-        const uint32_t hb = __dp4a(__byte_perm(tl, th2, 0x0052), wx, 0u), bb = __dp4a(__byte_perm(bl, bh2, 0x0052), wx, 0u);
+        // horizontal pairs: red is bytes 0 and 3 of the tap word itself, green
+        // and blue the same bytes of the word shifted by one and two bytes,
+        // with the weights (32 - fx) on byte 0 and fx on byte 3
+        const uint32_t wx = (uint32_t)fx * 16777215u + 32u, wy = (uint32_t)(32 + 255 * fy);
+        const uint32_t hr = __dp4a(tl, wx, 0u), br = __dp4a(bl, wx, 0u);
+        const uint32_t hg = __dp4a(__funnelshift_r(tl, th2, 8), wx, 0u), bg = __dp4a(__funnelshift_r(bl, bh2, 8), wx, 0u);
+        const uint32_t hb = __dp4a(__funnelshift_r(tl, th2, 16), wx, 0u), bb = __dp4a(__funnelshift_r(bl, bh2, 16), wx, 0u);
         const uint32_t vr = __dp2a_lo(__byte_perm(hr, br, 0x5410), wy, 512u) >> 10;
         const uint32_t vg = __dp2a_lo(__byte_perm(hg, bg, 0x5410), wy, 512u) >> 10;
         const uint32_t vb = __dp2a_lo(__byte_perm(hb, bb, 0x5410), wy, 512u) >> 10;
