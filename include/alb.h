@@ -375,6 +375,18 @@ ALB_API alb_status alb_photometric_f32_bwd(int32_t B, int32_t C, int32_t H, int3
 ALB_API alb_status alb_selftest_bounded_wait(int32_t spins, const void* src_dev, void* out_dev,
                                              int32_t* dev_status, void* stream);
 
+/* Diagnostic (no counterpart in the paper).  In the bounds-checked build of
+ * the library (compiled with ALB_CHECK_BOUNDS) every instrumented gather,
+ * staging copy and store of the resampling, chain, index-map and float warp
+ * kernels tests its index or address against the region it must stay in; a
+ * failing check skips the access and is counted on the device.  This call
+ * adds up the counts of every kernel file into *count (host), puts the source
+ * line of the first failing check into *first_line (0 if none), clears the
+ * counters when reset != 0, and sets *checked to 1 in the checked build, 0 in
+ * the normal build (whose counts are always 0).  Synchronous (it reads device
+ * memory); ALB_ECUDA when that fails. */
+ALB_API alb_status alb_bounds_violations(uint32_t* count, uint32_t* first_line, int32_t reset, int32_t* checked);
+
 /* ------------------------------------------------------------------ */
 /* Thread-local message for the last failing call on this thread. */
 ALB_API const char* alb_last_error(void);

@@ -110,6 +110,8 @@ def _declare(L):
     L.alb_autotune_save.restype = st
     L.alb_autotune_load.argtypes = [C.c_char_p, P(C.c_int32)]
     L.alb_autotune_load.restype = st
+    L.alb_bounds_violations.argtypes = [P(C.c_uint32), P(C.c_uint32), C.c_int32, P(C.c_int32)]
+    L.alb_bounds_violations.restype = st
     L.alb_batch_workspace_size.argtypes = [P(ChainCfg), C.c_int32, C.c_int32]
     L.alb_batch_workspace_size.restype = C.c_size_t
     L.alb_apply_batch.argtypes = [P(ChainCfg), C.c_int32, vp, vp, vp, C.c_int32, vp, C.c_size_t, vp, vp]
@@ -137,8 +139,13 @@ def _declare(L):
         f.restype = st
 
 
+def bounds_checked() -> bool:
+    """ALB_BOUNDS_CHECK=1 in the environment selects the bounds-checked build."""
+    return os.environ.get("ALB_BOUNDS_CHECK", "") == "1"
+
+
 def lib_path() -> str:
-    return _build.LIB
+    return _build.CHECK_LIB if bounds_checked() else _build.LIB
 
 
 def load(build_if_missing: bool = True):
@@ -146,8 +153,10 @@ def load(build_if_missing: bool = True):
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.LIB
-            if not os.path.exists(path):
+            path = lib_path()
+            if bounds_checked():
+                _build.build(check_bounds=True)
+            elif not os.path.exists(path):
                 if not build_if_missing:
                     raise RuntimeError(f"libalb.so not found at {path}; run paper_1809_06839_gb300.build.build()")
                 _build.build()
@@ -353,6 +362,13 @@ def alb_autotune_load(path: str) -> int:
     n = C.c_int32(0)
     _check(load().alb_autotune_load(os.fsencode(path), C.byref(n)))
     return n.value
+
+
+def alb_bounds_violations(reset: bool = False):
+    """(checked build?, violations counted, first failing source line)."""
+    cnt, line, chk = C.c_uint32(0), C.c_uint32(0), C.c_int32(0)
+    _check(load().alb_bounds_violations(C.byref(cnt), C.byref(line), int(reset), C.byref(chk)))
+    return bool(chk.value), cnt.value, line.value
 
 
 def alb_batch_workspace_size(cfg: ChainCfg, n: int, mode: int) -> int:

@@ -240,3 +240,20 @@ extern "C" alb_status alb_selftest_bounded_wait(int32_t spins, const void* src_d
   return launch_wait_selftest((uint32_t)spins, (const uint8_t*)src_dev, (uint8_t*)out_dev, dev_status,
                               (cudaStream_t)stream);
 }
+
+extern "C" alb_status alb_bounds_violations(uint32_t* count, uint32_t* first_line, int32_t reset, int32_t* checked) {
+  ALB_REQUIRE(count && first_line && checked, ALB_EINVAL, "alb_bounds_violations: null argument");
+#ifdef ALB_CHECK_BOUNDS
+  *checked = 1;
+#else
+  *checked = 0;
+#endif
+  unsigned int c = 0, line = 0;
+  alb_status rc = oob_resample(&c, &line, reset != 0);
+  if (rc == ALB_OK) rc = oob_fused(&c, &line, reset != 0);
+  if (rc == ALB_OK) rc = oob_geom(&c, &line, reset != 0);
+  if (rc == ALB_OK) rc = oob_diff(&c, &line, reset != 0);
+  *count = c;
+  *first_line = line;
+  return rc;
+}

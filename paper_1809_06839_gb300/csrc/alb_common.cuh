@@ -36,6 +36,51 @@ ALB_D void dev_fail(int32_t* status, int code) {
   if (status) atomicCAS(status, 0, code);
 }
 
+// ------------------------------------------------------------------ bounds-checked build
+// Compiled with -DALB_CHECK_BOUNDS (build.build(check_bounds=True)), ALB_IN(cond)
+// tests an index or address against the region it must stay in: when it
+// fails, the source line of the first failing check and a count go to this
+// translation unit's device counters and the guarded access is skipped (no
+// trap, no fault); alb_bounds_violations reads the counters of every unit.
+// In the normal build ALB_IN(cond) is `true` and costs nothing.
+#ifdef ALB_CHECK_BOUNDS
+static __device__ unsigned int g_alb_oob[2];   // count, first failing line
+ALB_D bool alb_in_check(bool ok, int line) {
+  if (!ok) {
+    if (atomicAdd(&g_alb_oob[0], 1u) == 0u) g_alb_oob[1] = (unsigned)line;
+  }
+  return ok;
+}
+#define ALB_IN(cond) (::alb::alb_in_check((cond), __LINE__))
+// per translation unit: read (and optionally clear) its counters
+#define ALB_OOB_ACCESSOR(fname)                                                   \
+  alb_status fname(unsigned int* count, unsigned int* line, bool reset) {         \
+    unsigned int h[2] = {0u, 0u};                                                 \
+    ALB_CUDA(cudaMemcpyFromSymbol(h, g_alb_oob, sizeof(h)));                     \
+    if (reset) {                                                                  \
+      const unsigned int z[2] = {0u, 0u};                                         \
+      ALB_CUDA(cudaMemcpyToSymbol(g_alb_oob, z, sizeof(z)));                     \
+    }                                                                             \
+    *count += h[0];                                                               \
+    if (!*line && h[1]) *line = h[1];                                             \
+    return ALB_OK;                                                                \
+  }
+#else
+#define ALB_IN(cond) (true)
+#define ALB_OOB_ACCESSOR(fname) \
+  alb_status fname(unsigned int*, unsigned int*, bool) { return ALB_OK; }
+#endif
+
+// a byte range [p, p + len) inside [base - slack, base + bytes + slack)
+ALB_D bool bytes_within(const void* p, int64_t len, const void* base, int64_t bytes, int64_t slack = 0) {
+  const intptr_t a = reinterpret_cast<intptr_t>(p), b = reinterpret_cast<intptr_t>(base);
+  return a >= b - slack && a + len <= b + bytes + slack;
+}
+// the byte extent of an image: its first byte to its last pixel's last byte
+ALB_D int64_t image_bytes(const alb_image& im) {
+  return im.h > 0 && im.w > 0 ? (int64_t)(im.h - 1) * im.row_stride + (int64_t)im.w * im.c : 0;
+}
+
 // ------------------------------------------------------------------ integer helpers
 ALB_HD int64_t floor_div(int64_t a, int64_t b) {  // b > 0
   int64_t q = a / b, r = a % b;

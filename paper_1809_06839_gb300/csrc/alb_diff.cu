@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(kWT_THREADS) k_warp_f32_fwd(int B, int C, int 
         const int s0 = ly * bp + lx;
 #pragma unroll
         for (int k = 0; k < kWT_CG; k++) {
-          if (k < cn) {
+          if (k < cn && ALB_IN(k * bpl + s0 + bp + 1 < kWT_BUF && s0 >= 0)) {
             const float* s = buf + k * bpl + s0;
             dstp[k * plane + o] = w00 * s[0] + w10 * s[1] + w01 * s[bp] + w11 * s[bp + 1];
           }
@@ -803,3 +803,7 @@ extern "C" alb_status alb_photometric_f32_bwd(int32_t B, int32_t C, int32_t H, i
   ALB_CUDA(cudaGetLastError());
   return ALB_OK;
 }
+
+namespace alb {
+ALB_OOB_ACCESSOR(oob_diff)
+}  // namespace alb

@@ -71,6 +71,10 @@ ALB_D void chain_bilinear(const uint8_t* __restrict__ win, int64_t stride, int32
   int32_t ix = xq >> 5;
   const int32_t fx = xq & 31, iy = yq >> 5, fy = yq & 31;
   const int32_t iyb = imin(iy + 1, ch - 1);
+  if (!ALB_IN(iy >= 0 && iy < ch && ix >= 0 && ix < cw)) {
+    rgb[0] = rgb[1] = rgb[2] = 0u;
+    return;
+  }
   const uint8_t* ra = win + (int64_t)iy * stride;
   const uint8_t* rb = win + (int64_t)iyb * stride;
   uint32_t wx = (uint32_t)(32 - fx) | ((uint32_t)fx << 8);
@@ -360,6 +364,7 @@ __global__ void __launch_bounds__(256) k_chain_fused(int32_t n, const alb_params
           for (int q = 0; q < 3; q++) { va[q] = (float)a[q]; vc[q] = (float)c[q]; }
         }
         const int64_t o = (int64_t)y * K.ow + x;
+        if (!ALB_IN(y < K.oh && x + 1 < K.ow)) continue;
 #pragma unroll
         for (int q = 0; q < 3; q++) {
           __nv_bfloat162 v2;
@@ -385,7 +390,8 @@ __global__ void __launch_bounds__(256) k_chain_fused(int32_t n, const alb_params
           for (int q = 0; q < 3; q++) v[q] = (float)rgb[q];
         }
 #pragma unroll
-        for (int q = 0; q < 3; q++) ob[q * plane + (int64_t)y * K.ow + x] = chain_normalize(v[q], K.k[q], K.m[q]);
+        if (ALB_IN(y < K.oh && x < K.ow))
+          for (int q = 0; q < 3; q++) ob[q * plane + (int64_t)y * K.ow + x] = chain_normalize(v[q], K.k[q], K.m[q]);
       }
     }
     if (MASKS) {
@@ -544,7 +550,9 @@ ALB_D void st48(uint8_t* p, const uint8_t (&v)[48]) {
   }
 }
 
-// mode 0 saturation: uint8 RGB -> float32 blend (clamped, not rounded)
+// mode 0 saturation: uint8 RGB -> float32 blend (clamped, not rounded); four
+// pixels a thread (three input words, three float4 outputs), consecutive
+// threads on consecutive pixels so that a warp's stores cover 1.5 KB
 __global__ void __launch_bounds__(256) k_plain_saturate(int32_t n, const alb_params* __restrict__ prm, int64_t P,
                                                         const uint8_t* __restrict__ in, float* __restrict__ out) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -553,22 +561,22 @@ __global__ void __launch_bounds__(256) k_plain_saturate(int32_t n, const alb_par
     const uint8_t* ib = in + (int64_t)b * P * 3;
     float* ob = out + (int64_t)b * P * 3;
     if ((P & 15) == 0) {
-      for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < P / 16; g += stride) {
-        uint8_t v[48];
-        ld48(ib + 48 * g, v);
-        float4* o4 = reinterpret_cast<float4*>(ob + 48 * g);
+      const uint32_t* iw = reinterpret_cast<const uint32_t*>(ib);
+      float4* o4 = reinterpret_cast<float4*>(ob);
+      for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < P / 4; g += stride) {
+        const uint32_t w0 = __ldg(iw + 3 * g), w1 = __ldg(iw + 3 * g + 1), w2 = __ldg(iw + 3 * g + 2);
+        const uint32_t w[3] = {w0, w1, w2};
+        float f[12];
 #pragma unroll
-        for (int q = 0; q < 4; q++) {          // 4 pixels = 12 floats = 3 float4 per step
-          float f[12];
-#pragma unroll
-          for (int j = 0; j < 4; j++) {
-            const uint32_t rgb[3] = {v[12 * q + 3 * j], v[12 * q + 3 * j + 1], v[12 * q + 3 * j + 2]};
-            chain_saturate(rgb, s, f + 3 * j);
-          }
-          o4[3 * q] = make_float4(f[0], f[1], f[2], f[3]);
-          o4[3 * q + 1] = make_float4(f[4], f[5], f[6], f[7]);
-          o4[3 * q + 2] = make_float4(f[8], f[9], f[10], f[11]);
+        for (int j = 0; j < 4; j++) {
+          const uint32_t rgb[3] = {(w[(3 * j) >> 2] >> (8 * ((3 * j) & 3))) & 0xFFu,
+                                   (w[(3 * j + 1) >> 2] >> (8 * ((3 * j + 1) & 3))) & 0xFFu,
+                                   (w[(3 * j + 2) >> 2] >> (8 * ((3 * j + 2) & 3))) & 0xFFu};
+          chain_saturate(rgb, s, f + 3 * j);
         }
+        o4[3 * g] = make_float4(f[0], f[1], f[2], f[3]);
+        o4[3 * g + 1] = make_float4(f[4], f[5], f[6], f[7]);
+        o4[3 * g + 2] = make_float4(f[8], f[9], f[10], f[11]);
       }
     } else {
       for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += stride) {
@@ -734,8 +742,8 @@ __global__ void __launch_bounds__(256) k_plain_normalize_u8(int32_t n, ChainK K,
 
 // grid of the per-image step kernels: enough blocks per image to give every
 // thread about one 16-pixel group, images on the grid's y axis
-static dim3 plain_grid(int32_t n, int64_t P) {
-  const int64_t groups = (P + 15) / 16;
+static dim3 plain_grid(int32_t n, int64_t P, int32_t px_per_thread = 16) {
+  const int64_t groups = (P + px_per_thread - 1) / px_per_thread;
   const int64_t bx = (groups + 255) / 256;
   return dim3((unsigned)(bx < 1 ? 1 : (bx > 1024 ? 1024 : bx)), (unsigned)(n < 65535 ? n : 65535));
 }
@@ -1037,7 +1045,7 @@ alb_status launch_chain(const alb_chain_cfg& cfg, int32_t n, const alb_params* p
     alb_status rc = launch_plan(la, n, kPlainItemBytes, prefix, rpi, chk, st);
     if (rc == ALB_OK) rc = launch_stream_lut(plan, lb, la, luts768, status, st);
     if (rc != ALB_OK) return rc;
-    k_plain_saturate<<<grid, 256, 0, st>>>(n, params, P, a, f);
+    k_plain_saturate<<<plain_grid(n, P, 4), 256, 0, st>>>(n, params, P, a, f);
     ALB_CUDA(cudaGetLastError());
     k_plain_normalize<<<grid, 256, 0, st>>>(n, K, P, f, o);
     ALB_CUDA(cudaGetLastError());
@@ -1278,3 +1286,7 @@ extern "C" alb_status alb_autotune_load(const char* path, int32_t* n_loaded) {
   *n_loaded = loaded;
   return ALB_OK;
 }
+
+namespace alb {
+ALB_OOB_ACCESSOR(oob_fused)
+}  // namespace alb

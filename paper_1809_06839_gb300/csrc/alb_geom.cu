@@ -140,6 +140,7 @@ __global__ void __launch_bounds__(256) k_index_map(Plan plan, ImgList in, ImgLis
           if (ob < 0 || ob >= L) continue;
           const int32_t x = (int32_t)(ob / C), c = (int32_t)(ob - (int64_t)x * C);
           const int32_t sx = m.src_x(y, x);
+          if (!ALB_IN(sx >= 0 && sx < si.w && m.src_y(y, x) >= 0 && m.src_y(y, x) < si.h)) continue;
           const uint8_t* sp = sep ? srow : src + (int64_t)m.src_y(y, x) * si.row_stride;
           word |= (uint32_t)__ldg(sp + (int64_t)sx * C + c) << (8 * t);
           nvalid++;
@@ -439,10 +440,13 @@ __global__ void __launch_bounds__(256) k_grid_u8(Plan plan, ImgList in, ImgList 
       const int32_t xq = table ? colq[x] : (act ? grid_q5(p.q, p.k, 0, x, W) : 32 * x);
       const int32_t yq = act ? grid_q5(p.q, p.k, 1, y, H) : 32 * y;
       if (NEAREST) {
+        if (!ALB_IN(((yq + 16) >> 5) >= 0 && ((yq + 16) >> 5) < H && ((xq + 16) >> 5) >= 0 && ((xq + 16) >> 5) < W))
+          continue;
         const uint8_t* sp = src + (int64_t)((yq + 16) >> 5) * si.row_stride + (int64_t)((xq + 16) >> 5) * C;
         for (int c = 0; c < C; c++) op[c] = __ldg(sp + c);
       } else {
         const int32_t ix = xq >> 5, iy = yq >> 5;
+        if (!ALB_IN(ix >= 0 && ix < W && iy >= 0 && iy < H)) continue;
         q5_taps_store<CT>(src, si.row_stride, C, ix, imin(ix + 1, W - 1), iy, imin(iy + 1, H - 1), xq & 31, yq & 31,
                           op);
       }
@@ -582,4 +586,8 @@ alb_status launch_boxes(int32_t n, const PrmList& prm, const ImgList& in, const 
   return ALB_OK;
 }
 
+}  // namespace alb
+
+namespace alb {
+ALB_OOB_ACCESSOR(oob_geom)
 }  // namespace alb

@@ -39,6 +39,13 @@ alb_status launch_chain(const alb_chain_cfg& cfg, int32_t n, const alb_params* p
                         const alb_image* mask_in = nullptr, const alb_image* mask_out = nullptr);
 size_t chain_workspace(const alb_chain_cfg& cfg, int32_t n, int32_t mode);
 
+// per translation unit: the bounds-checked build's violation counters (count
+// added to *count, first failing source line into *line when it is 0)
+alb_status oob_resample(unsigned int* count, unsigned int* line, bool reset);
+alb_status oob_fused(unsigned int* count, unsigned int* line, bool reset);
+alb_status oob_geom(unsigned int* count, unsigned int* line, bool reset);
+alb_status oob_diff(unsigned int* count, unsigned int* line, bool reset);
+
 inline bool is_geometric(int32_t tid) {
   switch (tid) {
     case ALB_HFLIP: case ALB_VFLIP: case ALB_RANDOM_CROP: case ALB_PAD_TO_SIZE: case ALB_ROTATE:

@@ -260,7 +260,11 @@ ALB_D void tile_stage(const WImg& k, const WTile& g, int lane, uint8_t* box, int
     phase[r] = (int16_t)ph;
     const int nch = (ph + span + 15) >> 4;
     uint8_t* d = box + r * WPitch<C>::SROW;
-    for (int j = 0; j < nch; j++) cp_async16(d + 16 * j, reinterpret_cast<const void*>(c0 + 16 * j));
+    const int64_t ib = (int64_t)(k.H - 1) * k.sstride + (int64_t)C * k.W;
+    for (int j = 0; j < nch; j++)
+      if (ALB_IN(bytes_within(reinterpret_cast<const void*>(c0 + 16 * j), 16, k.src, ib, 15) && r < WBOX &&
+                 16 * j + 16 <= WPitch<C>::SROW))
+        cp_async16(d + 16 * j, reinterpret_cast<const void*>(c0 + 16 * j));
   }
 }
 
@@ -288,6 +292,7 @@ ALB_D void tile_compute(const WImg& ks, const WTile& g, int lane, const uint8_t*
     int32_t rq = 0;
     if (MAP == MAP_RESIZE) rq = __shfl_sync(0xffffffffu, g.v, 16 + py);
     if (px >= g.tw || py >= g.th) continue;
+    if (!ALB_IN(g.oy0 + py < k.OH && g.ox0 + px < k.OW)) continue;
     uint8_t* __restrict__ od = k.dst + (int64_t)(g.oy0 + py) * k.dstride + (int64_t)C * (g.ox0 + px);
     if (g.mode != 2) {
       int ix, iy, fx = 0, fy = 0;
@@ -304,9 +309,12 @@ ALB_D void tile_compute(const WImg& ks, const WTile& g, int lane, const uint8_t*
           ix = xq >> 5; fx = xq & 31; iy = yq >> 5; fy = yq & 31;
         }
       }
+      if (!ALB_IN(iy >= 0 && iy < g.bh && ix >= 0 && ix < g.bw && (NEAREST || g.mode != 1 || iy + 1 < g.bh)))
+        continue;
       const int o0 = iy * SROW + ph[iy];
       if (NEAREST) {
         const int rx = g.mode == 1 ? reflect101(g.bx0 + ix, W) - g.ra : ix;
+        if (!ALB_IN(rx >= 0 && rx <= g.rb - g.ra)) continue;
 #pragma unroll
         for (int c = 0; c < C; c++) od[c] = bx[o0 + C * rx + c];
       } else if (g.mode == 0) {
@@ -352,6 +360,9 @@ ALB_D void tile_compute(const WImg& ks, const WTile& g, int lane, const uint8_t*
           sy0 = k.wy0 + (rq >> 5); sy1 = k.wy0 + imin((rq >> 5) + 1, k.ch - 1);
         }
       }
+      if (!ALB_IN(sx0 >= 0 && sx0 < W && sy0 >= 0 && sy0 < H && (NEAREST || (sx1 >= 0 && sx1 < W && sy1 >= 0 &&
+                                                                       sy1 < H))))
+        continue;
       if (NEAREST) {
         const uint8_t* s0 = k.src + (int64_t)sy0 * k.sstride + (int64_t)C * sx0;
 #pragma unroll
@@ -516,7 +527,11 @@ ALB_D void r_tile_stage(const RImg& k, const RTile& g, int lane, uint8_t* box, i
     rowoff[r] = r * RPITCH + ph;
     const int nch = (ph + span + 15) >> 4;
     uint8_t* d = box + r * RPITCH;
-    for (int j = 0; j < nch; j++) cp_async16(d + 16 * j, reinterpret_cast<const void*>(c0 + 16 * j));
+    const int64_t ib = (int64_t)(k.ch - 1 + k.wy0) * k.sstride + 3 * (int64_t)(k.cw + k.wx0);
+    for (int j = 0; j < nch; j++)
+      if (ALB_IN(bytes_within(reinterpret_cast<const void*>(c0 + 16 * j), 16, k.src, ib, 15) && r < RB_Y &&
+                 16 * j + 16 <= RPITCH))
+        cp_async16(d + 16 * j, reinterpret_cast<const void*>(c0 + 16 * j));
   }
 }
 
@@ -546,8 +561,8 @@ ALB_D void r_tile_compute(const RImg& k, const RTile& g, int lane, int32_t vcol,
   if (!g.big) {
     const int32_t ocol = 3 * ((vcol >> 5) - g.bx0);
     auto hrow = [&](int32_t i, uint32_t (&h)[3]) {
-      uint32_t lo, hi;
-      taps_row(box, rowoff[i] + ocol, lo, hi);
+      uint32_t lo = 0u, hi = 0u;
+      if (ALB_IN(i >= 0 && i < g.bh && ocol >= 0 && ocol < 3 * g.bw)) taps_row(box, rowoff[i] + ocol, lo, hi);
       r_hrow(lo, hi, wx, h);
     };
     // at a clamped bottom edge the row below the last tap row is not staged
@@ -572,7 +587,7 @@ ALB_D void r_tile_compute(const RImg& k, const RTile& g, int lane, int32_t vcol,
         ha[0] = adv ? hb[0] : ha[0]; ha[1] = adv ? hb[1] : ha[1]; ha[2] = adv ? hb[2] : ha[2];
         hb[0] = hn[0]; hb[1] = hn[1]; hb[2] = hn[2];
         ia = iy;
-        r_vert_store(ha, hb, (uint32_t)(32 + 255 * fy), store, od);
+        r_vert_store(ha, hb, (uint32_t)(32 + 255 * fy), store && ALB_IN(g.oy0 + r < k.OH && g.ox0 + lane < k.OW), od);
       }
     } else {
       for (int r = 0; r < g.th; r++, od += k.dstride) {
@@ -587,7 +602,7 @@ ALB_D void r_tile_compute(const RImg& k, const RTile& g, int lane, int32_t vcol,
           hrow(imin(iy + 1, last), hb);
           ia = iy;
         }
-        r_vert_store(ha, hb, (uint32_t)(32 + 255 * fy), store, od);
+        r_vert_store(ha, hb, (uint32_t)(32 + 255 * fy), store && ALB_IN(g.oy0 + r < k.OH && g.ox0 + lane < k.OW), od);
       }
     }
   } else {
@@ -598,8 +613,9 @@ ALB_D void r_tile_compute(const RImg& k, const RTile& g, int lane, int32_t vcol,
     const int32_t sx0 = k.wx0 + (vcol >> 5), sx1 = k.wx0 + imin((vcol >> 5) + 1, k.cw - 1);
     auto hrow = [&](int32_t sy, uint32_t (&h)[3]) {
       const uint8_t* row = k.src + (int64_t)sy * k.sstride;
-      uint32_t lo, hi;
-      if (sx1 == sx0 + 1) {
+      uint32_t lo = 0u, hi = 0u;
+      if (!ALB_IN(sy >= k.wy0 && sy < k.wy0 + k.ch && sx0 >= k.wx0 && sx1 < k.wx0 + k.cw && sx1 >= sx0)) {
+      } else if (sx1 == sx0 + 1) {
         ldg_pair(row + 3 * sx0, lo, hi);
       } else {
         lo = (uint32_t)row[3 * sx0] | ((uint32_t)row[3 * sx0 + 1] << 8) | ((uint32_t)row[3 * sx0 + 2] << 16) |
@@ -616,7 +632,7 @@ ALB_D void r_tile_compute(const RImg& k, const RTile& g, int lane, int32_t vcol,
         hrow(k.wy0 + imin(iy + 1, k.ch - 1), hb);
         ia = iy;
       }
-      r_vert_store(ha, hb, (uint32_t)(32 + 255 * fy), store, od);
+      r_vert_store(ha, hb, (uint32_t)(32 + 255 * fy), store && ALB_IN(g.oy0 + r < k.OH && g.ox0 + lane < k.OW), od);
     }
   }
 }
@@ -791,7 +807,11 @@ ALB_D void a_tile_stage(const AImg& k, const ATile& g, int lane, uint8_t* box, i
       j1 = imin(j1, (ph + 3 * chh + 2) >> 4);
     }
     uint8_t* d = box + r * APITCH;
-    for (int j = j0; j <= j1; j++) cp_async16(d + 16 * j, reinterpret_cast<const void*>(c0 + 16 * j));
+    const int64_t ib = (int64_t)(k.H - 1) * k.sstride + 3 * (int64_t)k.W;
+    for (int j = j0; j <= j1; j++)
+      if (ALB_IN(bytes_within(reinterpret_cast<const void*>(c0 + 16 * j), 16, k.src, ib, 15) && r < AB && j >= 0 &&
+                 16 * j + 16 <= APITCH))
+        cp_async16(d + 16 * j, reinterpret_cast<const void*>(c0 + 16 * j));
   }
 }
 
@@ -814,9 +834,11 @@ ALB_D void a_tile_compute(const AImg& k, const ATile& g, int lane, const uint8_t
       for (int r = 0; r < g.th; r++, X += q1, Y += q4, od += k.dstride) {
         const int32_t ix = X >> 16, fx = (X >> 11) & 31, iy = Y >> 16, fy = (Y >> 11) & 31;
         const int o = 3 * ix;
-        uint32_t tl, th2, bl, bh2;
-        taps_row(box, rowoff[iy] + o, tl, th2);
-        taps_row(box, rowoff[iy + 1] + o, bl, bh2);
+        uint32_t tl = 0u, th2 = 0u, bl = 0u, bh2 = 0u;
+        if (ALB_IN(ix >= 0 && ix + 1 < g.bw && iy >= 0 && iy + 1 < g.bh)) {
+          taps_row(box, rowoff[iy] + o, tl, th2);
+          taps_row(box, rowoff[iy + 1] + o, bl, bh2);
+        }
         // horizontal pairs: red is bytes 0 and 3 of the tap word itself, green
         // and blue the same bytes of the word shifted by one and two bytes,
         // with the weights (32 - fx) on byte 0 and fx on byte 3
@@ -827,14 +849,16 @@ ALB_D void a_tile_compute(const AImg& k, const ATile& g, int lane, const uint8_t
         const uint32_t vr = __dp2a_lo(__byte_perm(hr, br, 0x5410), wy, 512u) >> 10;
         const uint32_t vg = __dp2a_lo(__byte_perm(hg, bg, 0x5410), wy, 512u) >> 10;
         const uint32_t vb = __dp2a_lo(__byte_perm(hb, bb, 0x5410), wy, 512u) >> 10;
-        if (store) a_store3(od, vr, vg, vb);
+        if (store && ALB_IN(g.oy0 + r < k.OH && g.ox0 + lane < k.OW)) a_store3(od, vr, vg, vb);
       }
     } else {
       const int32_t W = k.W;
       for (int r = 0; r < g.th; r++, X += q1, Y += q4, od += k.dstride) {
         const int32_t ix = X >> 16, fx = (X >> 11) & 31, iy = Y >> 16, fy = (Y >> 11) & 31;
-        const int o0 = rowoff[iy], o1 = rowoff[iy + 1];
         const int xa = 3 * (reflect101(g.bx0 + ix, W) - g.ra), xb = 3 * (reflect101(g.bx0 + ix + 1, W) - g.ra);
+        if (!ALB_IN(iy >= 0 && iy + 1 < g.bh && xa >= 0 && xb >= 0 && xa <= 3 * (g.rb - g.ra) && xb <= 3 * (g.rb - g.ra)))
+          continue;
+        const int o0 = rowoff[iy], o1 = rowoff[iy + 1];
         const int w11 = fx * fy, w01 = 32 * fx - w11, w10 = 32 * fy - w11, w00 = 1024 - 32 * fx - 32 * fy + w11;
         uint32_t v[3];
 #pragma unroll
@@ -842,7 +866,7 @@ ALB_D void a_tile_compute(const AImg& k, const ATile& g, int lane, const uint8_t
           const int acc = w00 * box[o0 + xa + c] + w01 * box[o0 + xb + c] + w10 * box[o1 + xa + c] + w11 * box[o1 + xb + c];
           v[c] = (uint32_t)((acc + 512) >> 10);
         }
-        if (store) a_store3(od, v[0], v[1], v[2]);
+        if (store && ALB_IN(g.oy0 + r < k.OH && g.ox0 + lane < k.OW)) a_store3(od, v[0], v[1], v[2]);
       }
     }
   } else {
@@ -854,6 +878,7 @@ ALB_D void a_tile_compute(const AImg& k, const ATile& g, int lane, const uint8_t
       const int fx = (int)(xq & 31), fy = (int)(yq & 31);
       const int sx0 = reflect101(xq >> 5, W), sx1 = reflect101((xq >> 5) + 1, W);
       const int sy0 = reflect101(yq >> 5, H), sy1 = reflect101((yq >> 5) + 1, H);
+      if (!ALB_IN(sx0 >= 0 && sx0 < W && sx1 >= 0 && sx1 < W && sy0 >= 0 && sy0 < H && sy1 >= 0 && sy1 < H)) continue;
       const int w11 = fx * fy, w01 = 32 * fx - w11, w10 = 32 * fy - w11, w00 = 1024 - 32 * fx - 32 * fy + w11;
       const uint8_t* ra = k.src + (int64_t)sy0 * k.sstride;
       const uint8_t* rbp = k.src + (int64_t)sy1 * k.sstride;
@@ -863,7 +888,7 @@ ALB_D void a_tile_compute(const AImg& k, const ATile& g, int lane, const uint8_t
         const int acc = w00 * ra[3 * sx0 + c] + w01 * ra[3 * sx1 + c] + w10 * rbp[3 * sx0 + c] + w11 * rbp[3 * sx1 + c];
         v[c] = (uint32_t)((acc + 512) >> 10);
       }
-      if (store) a_store3(od, v[0], v[1], v[2]);
+      if (store && ALB_IN(g.oy0 + r < k.OH && g.ox0 + lane < k.OW)) a_store3(od, v[0], v[1], v[2]);
     }
   }
 }
@@ -970,7 +995,7 @@ __global__ void __launch_bounds__(32 * EWARP) k_elastic3(Plan plan, ImgList in, 
       int32_t X = 32 * x, Y = 32 * y;
       if (act) {
         const int32_t ci = (y >> sh) - ci0, fy = y & (S - 1);
-        if (ci != crow) {
+        if (ci != crow && ALB_IN(ci >= 0 && cj >= 0 && cj + 1 < ncols && (ci + 1) * ncols + cj + 1 < ELAT)) {
           const int2 a = lat[w][ci * ncols + cj], bq = lat[w][ci * ncols + cj + 1];
           const int2 c = lat[w][(ci + 1) * ncols + cj], d = lat[w][(ci + 1) * ncols + cj + 1];
           hax = (int64_t)(S - fx) * a.x + (int64_t)fx * bq.x;
@@ -1000,7 +1025,9 @@ __global__ void __launch_bounds__(32 * EWARP) k_elastic3(Plan plan, ImgList in, 
         gather_pair(src + (int64_t)reflect101(iy + 1, H) * ss, xa, xb, bl, bh2);
       }
       const uint32_t v = bilerp3(tl, th2, bl, bh2, fxq, fyq);
-      if (store) { od[0] = (uint8_t)v; od[1] = (uint8_t)(v >> 8); od[2] = (uint8_t)(v >> 16); }
+      if (store && ALB_IN(oy0 + r < so.h && ox0 + lane < so.w)) {
+        od[0] = (uint8_t)v; od[1] = (uint8_t)(v >> 8); od[2] = (uint8_t)(v >> 16);
+      }
     }
   }
 }
@@ -1064,4 +1091,8 @@ alb_status launch_tile_geometric(int32_t tid, const Plan& plan, const ImgList& i
   return launch_k(k_resample_warp<MAP_RESIZE, true, 1>, st, plan, in, out, prm);
 }
 
+}  // namespace alb
+
+namespace alb {
+ALB_OOB_ACCESSOR(oob_resample)
 }  // namespace alb

@@ -27,11 +27,16 @@ def bits(t):
 
 
 def run_chain(din, lps, dev, mode, oh=224, ow=224, tile_h=0, jitter=0):
+    """The chain into an output with a guard image before and after it (a
+    sentinel bit pattern that must survive the launch)."""
     n = len(lps)
     cfg = alb.chain_cfg(oh, ow, tile_h=tile_h, jitter=jitter)
-    out = torch.empty((n, 3, oh, ow), dtype=torch.bfloat16, device=dev)
+    full = torch.full((n + 2, 3, oh, ow), -1, dtype=torch.int16, device=dev).view(torch.bfloat16)
+    out = full[1:n + 1]
     alb.alb_apply_batch(cfg, n, alb.params_to_device(lps, dev), din.dev, out, mode)
     torch.cuda.synchronize()
+    g = full.view(torch.int16)
+    assert bool((g[0] == -1).all()) and bool((g[n + 1] == -1).all()), "chain wrote outside its output"
     return out
 
 

@@ -21,6 +21,7 @@ import pytest
 import torch
 
 import oracle as O
+from guards import assert_guards, guarded_output_batch
 from helpers import cfg_to_lib, same_params, suite_cfgs, to_lib
 
 from paper_1809_06839_gb300 import alb, synth
@@ -123,7 +124,8 @@ def test_large_images_with_masks_and_boxes(dev, name):
     ops = [O.sample_params(oc, 7, oc.tid, i, h, w) for i, (h, w) in enumerate(sizes)]
     lps = [to_lib(p, alb) for p in ops]
     din, dmi = DeviceBatch(rb), DeviceBatch(masks)
-    dout, dmo = output_batch(lps, rb.shapes, dev), mask_output_batch(lps, masks.shapes, dev)
+    dout = guarded_output_batch(lps, rb.shapes, dev)
+    dmo = guarded_output_batch(lps, masks.shapes, dev, mask=True)
     cap = 50
     boxes = np.zeros((n, cap, 4), np.float32)
     nb = np.zeros(n, np.int32)
@@ -138,6 +140,8 @@ def test_large_images_with_masks_and_boxes(dev, name):
                          bo, nbo, alb.workspace(alb.alb_workspace_size(oc.tid, n), dev), status)
     torch.cuda.synchronize()
     assert int(status.item()) == 0
+    assert_guards(dout, name)
+    assert_guards(dmo, (name, "mask"))
     bo, nbo = bo.cpu().numpy(), nbo.cpu().numpy()
     for i, (h, w) in enumerate(sizes):
         check_image(oc.tid, dout.rb.image(i).cpu().numpy(), O.apply_image(ops[i], rb.image(i).cpu().numpy()),

@@ -8,6 +8,7 @@ import pytest
 import torch
 
 import oracle as O
+from guards import assert_guards, guarded_output_batch
 from helpers import EXTRA_CFGS, cfg_to_lib, same_params, suite_cfgs, to_lib
 
 from paper_1809_06839_gb300 import alb, synth
@@ -44,13 +45,13 @@ def run_ragged(name, sizes, seed, dev, with_mask=True, with_boxes=True):
     ops = [O.sample_params(oc, seed, oc.tid, i, h, w) for i, (h, w) in enumerate(sizes)]
     lps = [to_lib(p, alb) for p in ops]
     din = DeviceBatch(to_device(rb, dev))
-    dout = output_batch(lps, rb.shapes, dev)
+    dout = guarded_output_batch(lps, rb.shapes, dev)
     prm = alb.params_to_device(lps, dev)
     n = len(sizes)
     dmi = dmo = None
     if with_mask:
         dmi = DeviceBatch(to_device(masks, dev))
-        dmo = mask_output_batch(lps, masks.shapes, dev)
+        dmo = guarded_output_batch(lps, masks.shapes, dev, mask=True)
     cap = 50
     boxes = np.zeros((n, cap, 4), np.float32)
     nb = np.zeros(n, np.int32)
@@ -69,6 +70,9 @@ def run_ragged(name, sizes, seed, dev, with_mask=True, with_boxes=True):
                          bo if with_boxes else None, nbo if with_boxes else None, ws, status)
     torch.cuda.synchronize()
     assert int(status.item()) == 0
+    assert_guards(dout, (name, "image"))
+    if dmo is not None:
+        assert_guards(dmo, (name, "mask"))
     return rb, masks, ops, dout, dmo, boxes, nb, bo.cpu().numpy(), nbo.cpu().numpy()
 
 
@@ -212,12 +216,14 @@ def test_resample_extremes(dev, kind, arg):
     lps = [to_lib(p, alb) for p in ops]
     din = DeviceBatch(to_device(rb, dev))
     dmi = DeviceBatch(to_device(masks, dev))
-    dout = output_batch(lps, rb.shapes, dev)
-    dmo = mask_output_batch(lps, masks.shapes, dev)
+    dout = guarded_output_batch(lps, rb.shapes, dev)
+    dmo = guarded_output_batch(lps, masks.shapes, dev, mask=True)
     ws = alb.workspace(alb.alb_workspace_size(ops[0].tid, len(sizes)), dev)
     alb.alb_apply_ragged(ops[0].tid, len(sizes), alb.params_to_device(lps, dev), din.dev, dout.dev, dmi.dev, dmo.dev,
                          ws=ws)
     torch.cuda.synchronize()
+    assert_guards(dout, kind)
+    assert_guards(dmo, (kind, "mask"))
     for i in range(len(sizes)):
         assert np.array_equal(dout.rb.image(i).cpu().numpy(), O.apply_image(ops[i], rb.image(i).numpy())), (kind, i)
         assert np.array_equal(dmo.rb.image(i).cpu().numpy(), O.apply_mask(ops[i], masks.image(i).numpy())), (kind, i)
@@ -330,13 +336,15 @@ def test_distortion_extremes(dev, name, cfg):
     ops = [O.sample_params(cfg, 4, cfg.tid, i, h, w) for i, (h, w) in enumerate(sizes)]
     lps = [to_lib(p, alb) for p in ops]
     din, dmi = DeviceBatch(to_device(rb, dev)), DeviceBatch(to_device(masks, dev))
-    dout, dmo = output_batch(lps, rb.shapes, dev), mask_output_batch(lps, masks.shapes, dev)
+    dout, dmo = guarded_output_batch(lps, rb.shapes, dev), guarded_output_batch(lps, masks.shapes, dev, mask=True)
     status = torch.zeros(1, dtype=torch.int32, device=dev)
     n = len(sizes)
     alb.alb_apply_ragged(cfg.tid, n, alb.params_to_device(lps, dev), din.dev, dout.dev, dmi.dev, dmo.dev,
                          ws=alb.workspace(alb.alb_workspace_size(cfg.tid, n), dev), dev_status=status)
     torch.cuda.synchronize()
     assert int(status.item()) == 0
+    assert_guards(dout, name)
+    assert_guards(dmo, (name, "mask"))
     for i in range(n):
         assert np.array_equal(dout.rb.image(i).cpu().numpy(), O.apply_image(ops[i], rb.image(i).numpy())), (name, i)
         assert np.array_equal(dmo.rb.image(i).cpu().numpy(), O.apply_mask(ops[i], masks.image(i).numpy())), (name, i)
