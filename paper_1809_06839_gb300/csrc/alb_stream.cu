@@ -18,11 +18,6 @@
 
 namespace alb {
 
-ALB_D uint8_t sat_rne_f(float v) {
-  const float r = fminf(fmaxf(rintf(v), 0.0f), 255.0f);
-  return (uint8_t)r;
-}
-
 // ================================================================== LUT ops
 // Tables in shared memory, 32 copies interleaved so that lane l always reads
 // bank l: byte v of channel c for lane l lives at c*8192 + (v & ~3)*32 + 4l + (v & 3).
@@ -298,15 +293,16 @@ ALB_D void gray_px(uint32_t& r, uint32_t& g, uint32_t& b) {
 }
 
 // ShiftHSV, float32 (Smith's hexcone; hue shift 2*dh degrees; sat and val by
-// /255).  Branch-free: the hue numerator/offset are selected, and the inverse
-// hexcone uses the per-channel form f(n) = V - V S clamp(min(k, 4 - k), 0, 1),
-// k = (n + H/60) mod 6 with n = 5, 3, 1 for R, G, B (identical to the sector
-// table of the definition).
-ALB_D uint32_t hsv_channel(float hp, float n, float V255, float C255) {
-  float k = hp + n;
-  k = k >= 6.0f ? k - 6.0f : k;
-  const float t = __saturatef(fminf(k, 4.0f - k));
-  return sat_rne_f(fmaf(-C255, t, V255));
+// /255), with the hue kept in sextants (H/60, in [0, 6)).  Branch-free: the
+// hue numerator/offset are selected, and the inverse hexcone uses the
+// per-channel form f(n) = V - V S t(k), t(k) = clamp(min(k, 4 - k), 0, 1) for
+// k = (n + H/60) mod 6, n = 5, 3, 1 for R, G, B (identical to the sector table
+// of the definition).  k = H/60 + n lies in [1, 11), where t is the sum of the
+// two clamped bumps 2 - |k - 2| and 2 - |k - 8|, so no wrap is needed.  The
+// result lies in [V - VS, V] within [0, 255], so only the rounding remains.
+ALB_D uint32_t hsv_channel(float h, float n, float V255, float C255) {
+  const float t = __saturatef(2.0f - fabsf(h + (n - 2.0f))) + __saturatef(2.0f - fabsf(h + (n - 8.0f)));
+  return __float2uint_rn(fmaf(-C255, t, V255));
 }
 
 ALB_D void hsv_px(float dh2, float ds, float dv, uint32_t& R, uint32_t& G, uint32_t& B) {
@@ -316,16 +312,15 @@ ALB_D void hsv_px(float dh2, float ds, float dv, uint32_t& R, uint32_t& G, uint3
   const bool isr = mx == r, isg = !isr && mx == g;
   const float num = isr ? g - b : (isg ? b - r : r - g);
   const float off = isr ? 0.0f : (isg ? 120.0f : 240.0f);
-  float hue = chroma > 0.0f ? fmaf(num, __fdividef(60.0f, chroma), off) : 0.0f;
-  hue = hue < 0.0f ? hue + 360.0f : hue;
+  float hue = chroma > 0.0f ? fmaf(num, __fdividef(1.0f, chroma), off * (1.0f / 60.0f)) : 0.0f;
+  hue = hue < 0.0f ? hue + 6.0f : hue;
   const float sat = mx > 0.0f ? __fdividef(chroma, mx) : 0.0f;
-  float h2 = hue + dh2;
-  h2 = h2 >= 360.0f ? h2 - 360.0f : h2;
-  h2 = h2 < 0.0f ? h2 + 360.0f : h2;
+  float hp = hue + dh2 * (1.0f / 60.0f);
+  hp = hp >= 6.0f ? hp - 6.0f : hp;
+  hp = hp < 0.0f ? hp + 6.0f : hp;
   const float s2 = __saturatef(sat + ds);
   const float v2 = __saturatef(fmaf(mx, 1.0f / 255.0f, dv));
   const float V255 = 255.0f * v2, C255 = V255 * s2;
-  const float hp = h2 * (1.0f / 60.0f);
   R = hsv_channel(hp, 5.0f, V255, C255);
   G = hsv_channel(hp, 3.0f, V255, C255);
   B = hsv_channel(hp, 1.0f, V255, C255);
