@@ -293,69 +293,120 @@ ALB_D void gray_px(uint32_t& r, uint32_t& g, uint32_t& b) {
 }
 
 // ShiftHSV, float32 (Smith's hexcone; hue shift 2*dh degrees; sat and val by
-// /255), with the hue kept in sextants (H/60, in [0, 6)).  Branch-free: the
-// hue numerator/offset are selected, and the inverse hexcone uses the
-// per-channel form f(n) = V - V S t(k), t(k) = clamp(min(k, 4 - k), 0, 1) for
-// k = (n + H/60) mod 6, n = 5, 3, 1 for R, G, B (identical to the sector table
-// of the definition).  k = H/60 + n lies in [1, 11), where t is the sum of the
-// two clamped bumps 2 - |k - 2| and 2 - |k - 8|, so no wrap is needed.  The
-// result lies in [V - VS, V] within [0, 255], so only the rounding remains.
-ALB_D uint32_t hsv_channel(float h, float n, float V255, float C255) {
-  const float t = __saturatef(2.0f - fabsf(h + (n - 2.0f))) + __saturatef(2.0f - fabsf(h + (n - 8.0f)));
-  return __float2uint_rn(fmaf(-C255, t, V255));
+// /255), with the hue kept in sextants (H/60, in [0, 6)).  Every value is a
+// BIASED float 2^23 + v: the bit pattern of a byte v is 0x4B000000 | v, so a
+// channel is unpacked with one byte permute, differences of two channels are
+// exact, the integer chroma and max are differences of bit patterns, and
+// adding 2^23 to a result in [0, 255] rounds it to the nearest integer (ties
+// to even) into the low byte of its bit pattern, ready to be packed.  The two
+// reciprocals (1 / chroma, 1 / max) come from a 256-entry table of correctly
+// rounded 1 / c (entry 0 = 0: a grey pixel has hue 0 and saturation 0).
+// Branch-free: the hue numerator/offset are selected, and the inverse hexcone
+// uses the per-channel form f(n) = V - V S t(k), t(k) = clamp(min(k, 4 - k),
+// 0, 1) for k = (n + H/60) mod 6, n = 5, 3, 1 for R, G, B (identical to the
+// sector table of the definition).  k = H/60 + n lies in [1, 11), where t is
+// 2 - (the distance to the nearer of 2 and 8), clamped, so no wrap is needed.
+// The result lies in [V - VS, V] within [0, 255], so only the rounding remains.
+constexpr float kBias = 8388608.0f;   // 2^23
+
+ALB_D float hsv_channel_b(float hp, float n, float V255, float C255) {
+  const float d = fminf(fabsf(hp + (n - 2.0f)), fabsf(hp + (n - 8.0f)));
+  return fmaf(-C255, __saturatef(2.0f - d), V255) + kBias;
 }
 
-ALB_D void hsv_px(float dh2, float ds, float dv, uint32_t& R, uint32_t& G, uint32_t& B) {
-  const float r = (float)R, g = (float)G, b = (float)B;
+ALB_D void hsv_px_b(const float* __restrict__ rcp, float dh6, float ds, float dv, float& R, float& G, float& B) {
+  const float r = R, g = G, b = B;
   const float mx = fmaxf(r, fmaxf(g, b)), mn = fminf(r, fminf(g, b));
-  const float chroma = mx - mn;
+  const uint32_t ic = __float_as_uint(mx) - __float_as_uint(mn), im = __float_as_uint(mx) & 0xFFu;
+  const float chroma = mx - mn, mxv = mx - kBias;
   const bool isr = mx == r, isg = !isr && mx == g;
   const float num = isr ? g - b : (isg ? b - r : r - g);
-  const float off = isr ? 0.0f : (isg ? 120.0f : 240.0f);
-  float hue = chroma > 0.0f ? fmaf(num, __fdividef(1.0f, chroma), off * (1.0f / 60.0f)) : 0.0f;
+  const float off = isr ? 0.0f : (isg ? 2.0f : 4.0f);
+  float hue = fmaf(num, rcp[ic], off);
   hue = hue < 0.0f ? hue + 6.0f : hue;
-  const float sat = mx > 0.0f ? __fdividef(chroma, mx) : 0.0f;
-  float hp = hue + dh2 * (1.0f / 60.0f);
+  const float sat = chroma * rcp[im];
+  float hp = hue + dh6;
   hp = hp >= 6.0f ? hp - 6.0f : hp;
   hp = hp < 0.0f ? hp + 6.0f : hp;
   const float s2 = __saturatef(sat + ds);
-  const float v2 = __saturatef(fmaf(mx, 1.0f / 255.0f, dv));
+  const float v2 = __saturatef(fmaf(mxv, 1.0f / 255.0f, dv));
   const float V255 = 255.0f * v2, C255 = V255 * s2;
-  R = hsv_channel(hp, 5.0f, V255, C255);
-  G = hsv_channel(hp, 3.0f, V255, C255);
-  B = hsv_channel(hp, 1.0f, V255, C255);
+  R = hsv_channel_b(hp, 5.0f, V255, C255);
+  G = hsv_channel_b(hp, 3.0f, V255, C255);
+  B = hsv_channel_b(hp, 1.0f, V255, C255);
 }
 
+// byte i (compile-time after unrolling) of the words as a biased float
+template <int NW>
+ALB_D float biased_byte(const uint32_t (&w)[NW], int i) {
+  return __uint_as_float(__byte_perm(w[i >> 2], 0x4B000000u, 0x7440u | (uint32_t)(i & 3)));
+}
+ALB_D float biased(uint32_t v) { return __uint_as_float(0x4B000000u | v); }
+ALB_D uint8_t unbias(float f) { return (uint8_t)__float_as_uint(f); }
+
+struct PixArgs {
+  const float* rcp;
+  float dh6, ds, dv;
+};
+
 template <int OP>  // 0 = Grayscale, 1 = ShiftHSV
-ALB_D void pixel_op(uint32_t& r, uint32_t& g, uint32_t& b, float dh2, float ds, float dv) {
-  if (OP == 0) gray_px(r, g, b);
-  else hsv_px(dh2, ds, dv, r, g, b);
+ALB_D void pixel_op(uint32_t& r, uint32_t& g, uint32_t& b, const PixArgs& a) {
+  if (OP == 0) {
+    gray_px(r, g, b);
+  } else {
+    float R = biased(r), G = biased(g), B = biased(b);
+    hsv_px_b(a.rcp, a.dh6, a.ds, a.dv, R, G, B);
+    r = unbias(R); g = unbias(G); b = unbias(B);
+  }
 }
 
 template <int OP>
-ALB_D void pixel_unit(const U48& u, uint32_t (&o)[12], float dh2, float ds, float dv) {
+ALB_D void pixel_unit(const U48& u, uint32_t (&o)[12], const PixArgs& a) {
   uint32_t w[12];
   words48(u, w);
+  if (OP == 0) {
 #pragma unroll
-  for (int m = 0; m < 12; m++) o[m] = 0;
+    for (int m = 0; m < 12; m++) o[m] = 0;
 #pragma unroll
-  for (int px = 0; px < 16; px++) {
-    uint32_t R = byte_of(w, 3 * px), G = byte_of(w, 3 * px + 1), B = byte_of(w, 3 * px + 2);
-    pixel_op<OP>(R, G, B, dh2, ds, dv);
-    o[(3 * px) >> 2] |= R << (8 * ((3 * px) & 3));
-    o[(3 * px + 1) >> 2] |= G << (8 * ((3 * px + 1) & 3));
-    o[(3 * px + 2) >> 2] |= B << (8 * ((3 * px + 2) & 3));
+    for (int px = 0; px < 16; px++) {
+      uint32_t R = byte_of(w, 3 * px), G = byte_of(w, 3 * px + 1), B = byte_of(w, 3 * px + 2);
+      gray_px(R, G, B);
+      o[(3 * px) >> 2] |= R << (8 * ((3 * px) & 3));
+      o[(3 * px + 1) >> 2] |= G << (8 * ((3 * px + 1) & 3));
+      o[(3 * px + 2) >> 2] |= B << (8 * ((3 * px + 2) & 3));
+    }
+  } else {
+    // 48 results as biased floats; each output word packs the low bytes of four
+    float f[48];
+#pragma unroll
+    for (int px = 0; px < 16; px++) {
+      float R = biased_byte(w, 3 * px), G = biased_byte(w, 3 * px + 1), B = biased_byte(w, 3 * px + 2);
+      hsv_px_b(a.rcp, a.dh6, a.ds, a.dv, R, G, B);
+      f[3 * px] = R; f[3 * px + 1] = G; f[3 * px + 2] = B;
+    }
+#pragma unroll
+    for (int m = 0; m < 12; m++) {
+      const uint32_t lo = __byte_perm(__float_as_uint(f[4 * m]), __float_as_uint(f[4 * m + 1]), 0x0040u);
+      const uint32_t hi = __byte_perm(__float_as_uint(f[4 * m + 2]), __float_as_uint(f[4 * m + 3]), 0x0040u);
+      o[m] = __byte_perm(lo, hi, 0x5410u);
+    }
   }
 }
 
 template <int OP>
 __global__ void __launch_bounds__(256) k_pixel_stream(Plan plan, ImgList in, ImgList out, PrmList prm) {
+  __shared__ float s_rcp[256];
+  if (OP == 1) {
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) s_rcp[i] = i ? 1.0f / (float)i : 0.0f;
+    __syncthreads();
+  }
   for_each_run(plan, [&](int32_t b, int32_t r0, int32_t r1) {
     const alb_image si = in.get(b), so = out.get(b);
     const alb_params& p = prm.get(b);
     r1 = imin(r1, so.h);
     const bool act = p.apply != 0;
-    const float dh2 = (float)(2.0 * p.shift[0]), ds = (float)(p.shift[1] / 255.0), dv = (float)(p.shift[2] / 255.0);
+    const PixArgs pa{s_rcp, (float)(2.0 * p.shift[0]) * (1.0f / 60.0f), (float)(p.shift[1] / 255.0),
+                     (float)(p.shift[2] / 255.0)};
     const uint8_t* __restrict__ ip = (const uint8_t*)si.data;
     uint8_t* __restrict__ op = (uint8_t*)so.data;
     if (flat_aligned(si) && flat_aligned(so)) {
@@ -369,7 +420,7 @@ __global__ void __launch_bounds__(256) k_pixel_stream(Plan plan, ImgList in, Img
         if (u + blockDim.x < u1) ld48(ip + 48 * (u + blockDim.x), nx);
         uint32_t o[12];
         if (act) {
-          pixel_unit<OP>(cur, o, dh2, ds, dv);
+          pixel_unit<OP>(cur, o, pa);
         } else {
           words48(cur, o);
         }
@@ -379,7 +430,7 @@ __global__ void __launch_bounds__(256) k_pixel_stream(Plan plan, ImgList in, Img
       for (int64_t q = a + threadIdx.x; q < e; q += blockDim.x) {
         if (q >= h1 && q < u1 * 16) continue;
         uint32_t R = ip[3 * q], G = ip[3 * q + 1], B = ip[3 * q + 2];
-        if (act) pixel_op<OP>(R, G, B, dh2, ds, dv);
+        if (act) pixel_op<OP>(R, G, B, pa);
         op[3 * q] = (uint8_t)R; op[3 * q + 1] = (uint8_t)G; op[3 * q + 2] = (uint8_t)B;
       }
     } else {
@@ -389,7 +440,7 @@ __global__ void __launch_bounds__(256) k_pixel_stream(Plan plan, ImgList in, Img
         const uint8_t* s = ip + (int64_t)y * si.row_stride + 3 * (int64_t)x;
         uint8_t* d = op + (int64_t)y * so.row_stride + 3 * (int64_t)x;
         uint32_t R = s[0], G = s[1], B = s[2];
-        if (act) pixel_op<OP>(R, G, B, dh2, ds, dv);
+        if (act) pixel_op<OP>(R, G, B, pa);
         d[0] = (uint8_t)R; d[1] = (uint8_t)G; d[2] = (uint8_t)B;
       }
     }
