@@ -403,6 +403,139 @@ __global__ void __launch_bounds__(256) k_chain_fused(int32_t n, const alb_params
   }
 }
 
+// Jitter mode 1 with the image held on chip: one CTA per image (pulled from a
+// counter, one CTA per SM), the whole resized output image kept in shared
+// memory between the two halves of the chain.  Pass 1: per output pixel the
+// Q5 bilinear value with the ops ordered before contrast applied (uint8,
+// stored unflipped), its integer BT.601 grey summed over the image; the
+// image's C table from that pivot (the float64 rule of k_jitter_luts); pass 2:
+// the remaining ops, the flip, Normalize and bf16 NCHW stores, from shared
+// memory.  The source crop is read once and nothing is recomputed; the
+// results are those of k_chain_pivot + k_jitter_luts + k_chain_fused<1>.
+// Instance-mask stacks are copied in the same pass.
+constexpr int kJitImgMax = 3 * 256 * 256;    // shared-memory image bytes, at most
+
+template <bool MASKS>
+__global__ void __launch_bounds__(1024, 1) k_chain_jitter_img(int32_t n, const alb_params* __restrict__ prm,
+                                                              const alb_image* __restrict__ imgs,
+                                                              const uint8_t* __restrict__ luts, ChainK K,
+                                                              int32_t* __restrict__ queue,
+                                                              __nv_bfloat16* __restrict__ out,
+                                                              const alb_image* __restrict__ mask_in,
+                                                              const alb_image* __restrict__ mask_out,
+                                                              int32_t* status) {
+  extern __shared__ __align__(16) uint8_t s_img[];
+  __shared__ int32_t s_item;
+  __shared__ uint8_t s_tb[256], s_tc[256];
+  __shared__ int32_t s_col[1024], s_row[1024];
+  __shared__ int32_t s_cnn[MASKS ? 1024 : 1], s_rnn[MASKS ? 1024 : 1];
+  __shared__ unsigned long long s_part[32];
+  const int tid = threadIdx.x, bs = blockDim.x;
+  const int32_t OW = K.ow, OH = K.oh;
+  const int64_t plane = (int64_t)OH * OW;
+  const int32_t hw = (OW + 1) >> 1;                   // pixel pairs per row (the last may be single)
+  const bool pairs = (OW & 1) == 0;                    // bf16x2 stores stay 4-byte aligned
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(queue, 1);
+    __syncthreads();
+    const int32_t b = s_item;
+    if (b >= n) break;
+    const alb_params& p = prm[b];
+    for (int i = tid; i < 256; i += bs) s_tb[i] = luts[(int64_t)b * 512 + i];
+    for (int x = tid; x < OW; x += bs) {
+      s_col[x] = chain_q5(x, p.cw, OW);
+      if (MASKS) s_cnn[x] = chain_nn(p.flip ? OW - 1 - x : x, p.cw, OW);
+    }
+    for (int y = tid; y < OH; y += bs) {
+      s_row[y] = chain_q5(y, p.ch, OH);
+      if (MASKS) s_rnn[y] = chain_nn(y, p.ch, OH);
+    }
+    __syncthreads();
+    const alb_image im = imgs[b];
+    const uint8_t* win = (const uint8_t*)im.data + (int64_t)p.y0 * im.row_stride + 3 * (int64_t)p.x0;
+    const int pos_c = jitter_pos_c(p.k);
+    const float s = (float)p.sat;
+    // ---- pass 1: ops before contrast, grey sum
+    uint32_t acc = 0;        // at most 32 pairs of 2 * 255 per thread for images <= 256 x 256
+    const int32_t npair = OH * hw;
+    for (int32_t i = tid; i < npair; i += bs) {
+      const int32_t y = i / hw, x = 2 * (i - y * hw);
+      const int32_t yq = s_row[y];
+      uint8_t* d = s_img + 3 * ((int64_t)y * OW + x);
+      uint32_t a[3];
+      chain_bilinear(win, im.row_stride, p.ch, p.cw, s_col[x], yq, a);
+      jitter_ops(a, p.k, 0, pos_c, s_tb, s_tb, s);
+      acc += grey_bt601(a);
+      d[0] = (uint8_t)a[0]; d[1] = (uint8_t)a[1]; d[2] = (uint8_t)a[2];
+      if (x + 1 < OW) {
+        uint32_t c[3];
+        chain_bilinear(win, im.row_stride, p.ch, p.cw, s_col[x + 1], yq, c);
+        jitter_ops(c, p.k, 0, pos_c, s_tb, s_tb, s);
+        acc += grey_bt601(c);
+        d[3] = (uint8_t)c[0]; d[4] = (uint8_t)c[1]; d[5] = (uint8_t)c[2];
+      }
+    }
+    unsigned long long acc64 = acc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc64 += __shfl_down_sync(0xffffffffu, acc64, o);
+    if ((tid & 31) == 0) s_part[tid >> 5] = acc64;
+    __syncthreads();
+    // ---- the image's C table from its pivot
+    if (tid < 256) {
+      unsigned long long sum = 0;
+      for (int w = 0; w < (bs >> 5); w++) sum += s_part[w];
+      const uint64_t np = (uint64_t)plane;
+      uint64_t q = sum / np;
+      const uint64_t r = sum - q * np;
+      if (2 * r > np || (2 * r == np && (q & 1))) q++;
+      const double m = (double)q;
+      s_tc[tid] = sat_rne_d(m + p.alpha * ((double)tid - m));
+    }
+    __syncthreads();
+    // ---- pass 2: the remaining ops, flip, Normalize, bf16 NCHW
+    __nv_bfloat16* ob = out + (int64_t)b * 3 * plane;
+    for (int32_t i = tid; i < npair; i += bs) {
+      const int32_t y = i / hw, x = 2 * (i - y * hw);
+      const bool two = x + 1 < OW;
+      const int32_t xa = p.flip ? OW - 1 - x : x, xb = p.flip ? OW - 2 - x : x + 1;   // resized columns shown
+      const uint8_t* sa = s_img + 3 * ((int64_t)y * OW + xa);
+      uint32_t a[3] = {sa[0], sa[1], sa[2]};
+      jitter_ops(a, p.k, pos_c, 3, s_tb, s_tc, s);
+      const int64_t o = (int64_t)y * OW + x;
+      if (!ALB_IN(y < OH && x < OW)) continue;
+      if (two) {
+        const uint8_t* sb = s_img + 3 * ((int64_t)y * OW + xb);
+        uint32_t c[3] = {sb[0], sb[1], sb[2]};
+        jitter_ops(c, p.k, pos_c, 3, s_tb, s_tc, s);
+        if (pairs) {
+#pragma unroll
+          for (int q = 0; q < 3; q++) {
+            __nv_bfloat162 v2;
+            v2.x = chain_normalize((float)a[q], K.k[q], K.m[q]);
+            v2.y = chain_normalize((float)c[q], K.k[q], K.m[q]);
+            *reinterpret_cast<__nv_bfloat162*>(ob + q * plane + o) = v2;
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < 3; q++) {
+            ob[q * plane + o] = chain_normalize((float)a[q], K.k[q], K.m[q]);
+            ob[q * plane + o + 1] = chain_normalize((float)c[q], K.k[q], K.m[q]);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 3; q++) ob[q * plane + o] = chain_normalize((float)a[q], K.k[q], K.m[q]);
+      }
+    }
+    if (MASKS) {
+      const alb_image mi = mask_in[b], mo = mask_out[b];
+      if (chain_mask_ok(im, mi, mo, K)) chain_mask_rows(p, mi, mo, s_cnn, s_rnn, 0, OH, OW);
+      else if (tid == 0) dev_fail(status, ALB_ESHAPE);
+    }
+    __syncthreads();
+  }
+}
+
 // Masks of the chain on their own (the plain path): item = (image, band of 32 rows), grid-stride.
 __global__ void __launch_bounds__(256) k_chain_masks(int32_t n, const alb_params* __restrict__ prm,
                                                      const alb_image* __restrict__ imgs, ChainK K,
@@ -968,6 +1101,19 @@ alb_status launch_chain(const alb_chain_cfg& cfg, int32_t n, const alb_params* p
     }
     const int max_per_sm = fused_max_per_sm(jit, mask_in != nullptr);
     if (per_sm <= 0 || per_sm > max_per_sm) per_sm = max_per_sm;
+    if (jit && 3 * npx <= kJitImgMax && cfg.out_h <= 1024) {
+      // the whole chain per image on chip (one CTA per SM, the image in shared memory)
+      const int smem = (int)(3 * npx);
+      auto kj = mask_in ? k_chain_jitter_img<true> : k_chain_jitter_img<false>;
+      ALB_CUDA(cudaFuncSetAttribute(kj, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+      int pj = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pj, kj, 1024, smem);
+      ALB_CUDA(cudaMemsetAsync(queue, 0, sizeof(int32_t), st));
+      kj<<<(pj < 1 ? 1 : pj) * sm_count(), 1024, smem, st>>>(n, params, in, luts, K, queue, o, mask_in, mask_out,
+                                                              status);
+      ALB_CUDA(cudaGetLastError());
+      return ALB_OK;
+    }
     if (jit) {
       // the contrast pivots first (a reduction over each image), then the C tables
       int pv = 0;
