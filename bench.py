@@ -455,11 +455,12 @@ def fused_pipeline(dev, stream, steps=3, warmup=2, n=FUSED_N):
     except Exception as ex:  # the per-kernel breakdown needs the profiler's CUDA activity trace
         res["steps"] = {"error": str(ex)[:160]}
     # jitter mode 1: per-image random order and image-mean contrast pivot (a
-    # per-image reduction before the write pass), fused vs plain
+    # per-image reduction between the ops before contrast and the rest), fused
+    # vs plain; the fused path runs one CTA per image with the resized image in
+    # shared memory, so the band schedule does not apply
     jcfg = A.chain_cfg(jitter=1)
     wsj = A.workspace(A.alb_batch_workspace_size(jcfg, FUSED_N, A.MODE_PLAIN), dev)
-    jb = A.alb_autotune_batch(jcfg, FUSED_N, pdev, din.dev, out, wsj, reps=2, stream=stream)
-    jres = {"schedule": {"rows_per_item": jb.tile_h, "ctas_per_sm": jb.ctas_per_sm}}
+    jres = {"kernel": "k_chain_jitter_img: one CTA per image, the 224x224 image held in shared memory"}
     for name, mode in (("fused", A.MODE_FUSED), ("plain", A.MODE_PLAIN)):
         def runj(mode=mode):
             A.alb_sample_params_batch(cfg, SEED, 20, 0, FUSED_N, din.dev, pdev, stream=stream)
@@ -469,7 +470,7 @@ def fused_pipeline(dev, stream, steps=3, warmup=2, n=FUSED_N):
         jres[name] = dict(images_per_s=FUSED_N / t, ms=t * 1e3)
     jres["speedup_vs_plain"] = jres["plain"]["ms"] / jres["fused"]["ms"]
     tj = jres["fused"]["ms"] / 1e3
-    # the pivot pass reads the sampled pixels once more; counted as traffic, not algorithmic bytes
+    # every sampled source sector is read once, the output written once
     jres["roofline"] = {"bound": "hbm", "algorithmic_bytes": rd + wr, "achieved": round((rd + wr) / tj / 1e9, 1),
                         "peak": hbm, "unit": "GB/s", "frac": round((rd + wr) / tj / 1e9 / hbm, 4)}
     res["jitter_random_order_mean_pivot"] = jres
