@@ -839,16 +839,16 @@ ALB_D void a_tile_compute(const AImg& k, const ATile& g, int lane, const uint8_t
           taps_row(box, rowoff[iy] + o, tl, th2);
           taps_row(box, rowoff[iy + 1] + o, bl, bh2);
         }
-        // horizontal pairs: red is bytes 0 and 3 of the tap word itself, green
-        // and blue the same bytes of the word shifted by one and two bytes,
-        // with the weights (32 - fx) on byte 0 and fx on byte 3
-        const uint32_t wx = (uint32_t)fx * 16777215u + 32u, wy = (uint32_t)(32 + 255 * fy);
-        const uint32_t hr = __dp4a(tl, wx, 0u), br = __dp4a(bl, wx, 0u);
-        const uint32_t hg = __dp4a(__funnelshift_r(tl, th2, 8), wx, 0u), bg = __dp4a(__funnelshift_r(bl, bh2, 8), wx, 0u);
-        const uint32_t hb = __dp4a(__funnelshift_r(tl, th2, 16), wx, 0u), bb = __dp4a(__funnelshift_r(bl, bh2, 16), wx, 0u);
-        const uint32_t vr = __dp2a_lo(__byte_perm(hr, br, 0x5410), wy, 512u) >> 10;
-        const uint32_t vg = __dp2a_lo(__byte_perm(hg, bg, 0x5410), wy, 512u) >> 10;
-        const uint32_t vb = __dp2a_lo(__byte_perm(hb, bb, 0x5410), wy, 512u) >> 10;
+        // the tap pairs as {R0, R1, G0, G1} and {B0, B1} per row, against the
+        // 16-bit weight pairs ((32 - fx) wy, fx wy) of the top (wy = 32 - fy) and
+        // bottom (wy = fy) row: two dp2a per channel give sum w_ij p_ij + 512
+        const uint32_t wxp = 32u + 65535u * (uint32_t)fx;                  // {32 - fx, fx}
+        const uint32_t wt = wxp * (uint32_t)(32 - fy), wb = wxp * (uint32_t)fy;
+        const uint32_t pt = __byte_perm(tl, th2, 0x4130), qt = __byte_perm(tl, th2, 0x0052);
+        const uint32_t pb = __byte_perm(bl, bh2, 0x4130), qb = __byte_perm(bl, bh2, 0x0052);
+        const uint32_t vr = __dp2a_lo(wt, pt, __dp2a_lo(wb, pb, 512u)) >> 10;
+        const uint32_t vg = __dp2a_hi(wt, pt, __dp2a_hi(wb, pb, 512u)) >> 10;
+        const uint32_t vb = __dp2a_lo(wt, qt, __dp2a_lo(wb, qb, 512u)) >> 10;
         if (store && ALB_IN(g.oy0 + r < k.OH && g.ox0 + lane < k.OW)) a_store3(od, vr, vg, vb);
       }
     } else {
