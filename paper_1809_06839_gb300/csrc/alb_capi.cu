@@ -88,7 +88,9 @@ static alb_status run_ragged(int32_t tid, int32_t n, const PrmList& prm, const I
     const PlanCheck chk{tid, img_c, geo, in, prm, status, 0};
     alb_status rc = launch_plan(out, n, kItemBytes, prefix, rpi, chk, st);
     if (rc != ALB_OK) return rc;
-    Plan plan{prefix, rpi, n};
+    // the mask plan's arrays serve as the image launch's second tile plan;
+    // the mask plan is written after the image kernels (stream order)
+    Plan plan{prefix, rpi, n, mprefix, mrpi};
     rc = geo ? launch_geometric(tid, plan, in, out, prm, img_c, false, status, st)
              : launch_photometric(tid, n, plan, in, out, prm, luts, hist, status, st);
     if (rc != ALB_OK) return rc;

@@ -124,6 +124,10 @@ struct Plan {
   const int32_t* prefix;        // n + 1
   const int32_t* rows_per_item; // n
   int32_t n;
+  // optional second tile plan ([n + 1], [n]), free for the image launch: the
+  // resizes route their reductions through it (see launch_tile_geometric)
+  int32_t* prefix2 = nullptr;
+  int32_t* rows2 = nullptr;
 };
 
 // Blocked distribution of the plan's items over the grid: CTA j takes a
@@ -233,6 +237,7 @@ struct PlanCheck {
   PrmList prm;
   int32_t* status;
   int32_t filter_c;   // 0: all images; k > 0: only images with c == k; k < 0: only c != -k (others: no items, no error)
+  int32_t reduce = 0; // resizes: 0 all images; 1 only reductions (window over 17/16 of the output on an axis); -1 the others
 };
 
 ALB_D bool plan_filtered_out(const PlanCheck& chk, const alb_image& im) {

@@ -55,6 +55,11 @@ __global__ void k_plan_tiles(ImgList out, int32_t n, int32_t tile_w, int32_t til
       tiles_x[i] = tx > 0 ? tx : 1;
       if (check_image_pair(chk.tid, chk.prm.get(i), chk.in.get(i), im, chk.want_c, chk.geometric)) cnt = 0;
       if (plan_filtered_out(chk, im)) cnt = 0;
+      if (chk.reduce != 0 && cnt) {
+        const alb_params& pr = chk.prm.get(i);
+        const bool red = 16 * (int64_t)pr.cw > 17 * (int64_t)im.w || 16 * (int64_t)pr.ch > 17 * (int64_t)im.h;
+        if (red != (chk.reduce > 0)) cnt = 0;
+      }
     }
     int32_t v = cnt;
 #pragma unroll
@@ -445,20 +450,26 @@ __global__ void __launch_bounds__(32 * NWARP, 5) k_resample_warp(Plan plan, ImgL
 // lane j = output column j; it walks the tile's rows top to bottom keeping the
 // two current tap rows' h in registers (for an enlargement most output rows
 // reuse both, or shift by one source row).  The tile's source box (up to
-// RB_X x RB_Y pixels: enlargements and reductions to ~0.95) is staged per warp
-// in shared memory by cp.async, one buffer per warp (the per-tile image and
-// geometry stay in registers).  Measured trade-off: a taller
+// BX x BY pixels of its shape) is staged per warp in shared memory by
+// cp.async, one buffer per warp (the per-tile image and geometry stay in
+// registers).  Measured trade-off: a taller
 // tile amortises the per-tile geometry, a larger box costs warps per SM (the
 // row chain is latency-bound); 32 x 32 with a 36 x 36 box beat 32 x 16 with
 // 36 x 20 and 32 x 32 with 36 x 28.  Larger footprints read global memory.
-constexpr int RT_W = 32, RT_H = 32;   // output tile (columns x rows)
-constexpr int RB_X = 36, RB_Y = 36;   // staged box (source pixels x rows)
-constexpr int RPITCH = 144;           // staged row pitch in bytes
+// Two tile shapes: S = 0, 32 x 32 output tiles with a 36 x 36 box
+// (enlargements and reductions to ~0.95); S = 1, 32 x 16 tiles with a 68 x 36
+// box (reductions by up to ~2, routed there per image).
+template <int S>
+struct RShape {
+  static constexpr int TW = 32, TH = S ? 16 : 32;         // output tile (columns x rows)
+  static constexpr int BX = S ? 68 : 36, BY = 36;         // staged box (source pixels x rows)
+  static constexpr int PITCH = S ? 240 : 144;             // staged row pitch in bytes
+  static_assert(PITCH % 16 == 0, "cp.async destinations must be 16-byte aligned");
+  static_assert(PITCH >= 15 + 3 * (BX - 1) + 12, "a tap read (3 words from the pair's word) stays in its row");
+  static_assert(BY >= TH + 1 && BX >= TW + 2, "the box holds an unscaled tile");
+  static_assert(TH <= 32 && (TH & (TH - 1)) == 0, "lane r holds the coordinate of tile row r");
+};
 constexpr int RWARP = 4;              // warps per CTA
-static_assert(RPITCH % 16 == 0, "cp.async destinations must be 16-byte aligned");
-static_assert(RPITCH >= 15 + 3 * (RB_X - 1) + 12, "a tap read (3 words from the pair's word) stays in its row");
-static_assert(RB_Y >= RT_H + 1 && RB_X >= RT_W + 2, "the box holds an unscaled tile");
-static_assert(RT_H <= 32 && (RT_H & (RT_H - 1)) == 0, "lane r holds the coordinate of tile row r");
 
 struct RImg {          // per-image values of a warp's current image (warp-uniform)
   int32_t b, prefix, ntiles, tiles_x;
@@ -489,14 +500,15 @@ ALB_D void r_load_img(const Plan& plan, const ImgList& in, const ImgList& out, c
 }
 
 // Tile geometry; per lane: vcol = Q5 coordinate of tile column `lane`,
-// vrow = that of tile row `lane` (lanes < RT_H), both clamped to the tile.
-template <int MAP>
+// vrow = that of tile row `lane` (lanes < TH), both clamped to the tile.
+template <int MAP, int S>
 ALB_D void r_tile_geo(const RImg& k, const PrmList& prm, int32_t item, int lane, RTile& g, int32_t& vcol,
                       int32_t& vrow) {
+  using SH = RShape<S>;
   const int32_t t = item - k.prefix, ty = t / k.tiles_x, tx = t - ty * k.tiles_x;
-  g.ox0 = tx * RT_W; g.oy0 = ty * RT_H;
-  g.tw = imin(RT_W, k.OW - g.ox0); g.th = imin(RT_H, k.OH - g.oy0);
-  const int32_t cx = g.ox0 + imin(lane, g.tw - 1), ry = g.oy0 + imin(lane & (RT_H - 1), g.th - 1);
+  g.ox0 = tx * SH::TW; g.oy0 = ty * SH::TH;
+  g.tw = imin(SH::TW, k.OW - g.ox0); g.th = imin(SH::TH, k.OH - g.oy0);
+  const int32_t cx = g.ox0 + imin(lane, g.tw - 1), ry = g.oy0 + imin(lane & (SH::TH - 1), g.th - 1);
   if (MAP == MAP_GRID) {
     const alb_params& p = prm.get(k.b);            // the cell factors stay in the record
     vcol = p.apply ? grid_q5(p.q, p.k, 0, cx, k.cw) : 32 * cx;
@@ -510,12 +522,14 @@ ALB_D void r_tile_geo(const RImg& k, const PrmList& prm, int32_t item, int lane,
   g.bx0 = c0 >> 5; g.by0 = r0 >> 5;
   g.bw = imin((c1 >> 5) + 1, k.cw - 1) - g.bx0 + 1;
   g.bh = imin((r1 >> 5) + 1, k.ch - 1) - g.by0 + 1;
-  g.big = g.bw > RB_X || g.bh > RB_Y;
+  g.big = g.bw > SH::BX || g.bh > SH::BY;
 }
 
 // Lane r (and r + 32) stages box row r: raw aligned 16-byte chunks;
 // rowoff[r] = r * pitch + the row's byte phase.
+template <int S>
 ALB_D void r_tile_stage(const RImg& k, const RTile& g, int lane, uint8_t* box, int32_t* rowoff) {
+  using SH = RShape<S>;
   if (g.big) return;
   const int span = 3 * g.bw;
   for (int r = lane; r < g.bh; r += 32) {
@@ -524,13 +538,13 @@ ALB_D void r_tile_stage(const RImg& k, const RTile& g, int lane, uint8_t* box, i
                             (uintptr_t)(3 * (k.wx0 + g.bx0));
     const uintptr_t c0 = first & ~uintptr_t(15);
     const int ph = (int)(first - c0);
-    rowoff[r] = r * RPITCH + ph;
+    rowoff[r] = r * SH::PITCH + ph;
     const int nch = (ph + span + 15) >> 4;
-    uint8_t* d = box + r * RPITCH;
+    uint8_t* d = box + r * SH::PITCH;
     const int64_t ib = (int64_t)(k.ch - 1 + k.wy0) * k.sstride + 3 * (int64_t)(k.cw + k.wx0);
     for (int j = 0; j < nch; j++)
-      if (ALB_IN(bytes_within(reinterpret_cast<const void*>(c0 + 16 * j), 16, k.src, ib, 15) && r < RB_Y &&
-                 16 * j + 16 <= RPITCH))
+      if (ALB_IN(bytes_within(reinterpret_cast<const void*>(c0 + 16 * j), 16, k.src, ib, 15) && r < SH::BY &&
+                 16 * j + 16 <= SH::PITCH))
         cp_async16(d + 16 * j, reinterpret_cast<const void*>(c0 + 16 * j));
   }
 }
@@ -637,15 +651,16 @@ ALB_D void r_tile_compute(const RImg& k, const RTile& g, int lane, int32_t vcol,
   }
 }
 
+template <int S>
 struct RShared {       // dynamic shared memory of k_resize_rows: one staging box per warp
-  uint8_t box[RWARP][RB_Y * RPITCH + 16];   // +16: the last row's tap read past the staged bytes
-  int32_t rowoff[RWARP][RB_Y];
+  uint8_t box[RWARP][RShape<S>::BY * RShape<S>::PITCH + 16];   // +16: the last row's tap read past the staged bytes
+  int32_t rowoff[RWARP][RShape<S>::BY];
 };
 
-template <int MAP>
+template <int MAP, int S>
 __global__ void __launch_bounds__(32 * RWARP) k_resize_rows(Plan plan, ImgList in, ImgList out, PrmList prm) {
   extern __shared__ __align__(16) uint8_t rs_dyn[];
-  RShared& sm = *reinterpret_cast<RShared*>(rs_dyn);
+  RShared<S>& sm = *reinterpret_cast<RShared<S>*>(rs_dyn);
   int32_t it0, it1;
   item_range(plan, it0, it1);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -661,9 +676,9 @@ __global__ void __launch_bounds__(32 * RWARP) k_resize_rows(Plan plan, ImgList i
     }
     RTile g;
     int32_t ccol, crow;
-    r_tile_geo<MAP>(k, prm, item, lane, g, ccol, crow);
+    r_tile_geo<MAP, S>(k, prm, item, lane, g, ccol, crow);
     __syncwarp();
-    r_tile_stage(k, g, lane, sm.box[w], sm.rowoff[w]);
+    r_tile_stage<S>(k, g, lane, sm.box[w], sm.rowoff[w]);
     cp_async_commit();
     cp_async_wait<0>();
     __syncwarp();
@@ -1055,16 +1070,29 @@ alb_status launch_tile_geometric(int32_t tid, const Plan& plan, const ImgList& i
   int32_t* prefix = const_cast<int32_t*>(plan.prefix);
   int32_t* tiles_x = const_cast<int32_t*>(plan.rows_per_item);
   if ((resize || grid) && !mask) {
-    k_plan_tiles<<<1, 1024, 0, st>>>(out, plan.n, RT_W, RT_H, prefix, tiles_x, chk);
+    // resizes with a second plan: reductions beyond 17/16 on an axis through
+    // the 68 x 36 box (32 x 16 tiles), the rest through the 36 x 36 box
+    const bool split = resize && plan.prefix2 && plan.rows2;
+    PlanCheck c0 = chk;
+    c0.reduce = split ? -1 : 0;
+    k_plan_tiles<<<1, 1024, 0, st>>>(out, plan.n, RShape<0>::TW, RShape<0>::TH, prefix, tiles_x, c0);
     ALB_CUDA(cudaGetLastError());
-    const int smem = (int)sizeof(RShared);
-    auto kern = grid ? k_resize_rows<MAP_GRID> : k_resize_rows<MAP_RESIZE>;
-    ALB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * RWARP, smem);
-    kern<<<(per_sm < 1 ? 1 : per_sm) * sm_count(), 32 * RWARP, smem, st>>>(plan, in, out, prm);
+    auto run = [&](auto kern, int smem, const Plan& pl) -> alb_status {
+      ALB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+      int per_sm = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * RWARP, smem);
+      kern<<<(per_sm < 1 ? 1 : per_sm) * sm_count(), 32 * RWARP, smem, st>>>(pl, in, out, prm);
+      ALB_CUDA(cudaGetLastError());
+      return ALB_OK;
+    };
+    alb_status rc = run(grid ? k_resize_rows<MAP_GRID, 0> : k_resize_rows<MAP_RESIZE, 0>, (int)sizeof(RShared<0>), plan);
+    if (rc != ALB_OK || !split) return rc;
+    PlanCheck c1 = chk;
+    c1.reduce = 1;
+    k_plan_tiles<<<1, 1024, 0, st>>>(out, plan.n, RShape<1>::TW, RShape<1>::TH, plan.prefix2, plan.rows2, c1);
     ALB_CUDA(cudaGetLastError());
-    return ALB_OK;
+    const Plan p2{plan.prefix2, plan.rows2, plan.n};
+    return run(k_resize_rows<MAP_RESIZE, 1>, (int)sizeof(RShared<1>), p2);
   }
   if (grid) return ALB_EINVAL;   // masks of a grid distortion: the general kernel
   if (tid == ALB_ELASTIC) {
