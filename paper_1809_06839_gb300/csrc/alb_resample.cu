@@ -1075,8 +1075,15 @@ alb_status launch_tile_geometric(int32_t tid, const Plan& plan, const ImgList& i
     const bool split = resize && plan.prefix2 && plan.rows2;
     PlanCheck c0 = chk;
     c0.reduce = split ? -1 : 0;
-    k_plan_tiles<<<1, 1024, 0, st>>>(out, plan.n, RShape<0>::TW, RShape<0>::TH, prefix, tiles_x, c0);
-    ALB_CUDA(cudaGetLastError());
+    if (grid) {
+      // grid distortion: cell factors up to ~1.9 stretch many tiles' footprints
+      // past the small box, so every image takes the 68 x 36 box
+      k_plan_tiles<<<1, 1024, 0, st>>>(out, plan.n, RShape<1>::TW, RShape<1>::TH, prefix, tiles_x, c0);
+      ALB_CUDA(cudaGetLastError());
+    } else {
+      k_plan_tiles<<<1, 1024, 0, st>>>(out, plan.n, RShape<0>::TW, RShape<0>::TH, prefix, tiles_x, c0);
+      ALB_CUDA(cudaGetLastError());
+    }
     auto run = [&](auto kern, int smem, const Plan& pl) -> alb_status {
       ALB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
       int per_sm = 0;
@@ -1085,7 +1092,8 @@ alb_status launch_tile_geometric(int32_t tid, const Plan& plan, const ImgList& i
       ALB_CUDA(cudaGetLastError());
       return ALB_OK;
     };
-    alb_status rc = run(grid ? k_resize_rows<MAP_GRID, 0> : k_resize_rows<MAP_RESIZE, 0>, (int)sizeof(RShared<0>), plan);
+    if (grid) return run(k_resize_rows<MAP_GRID, 1>, (int)sizeof(RShared<1>), plan);
+    alb_status rc = run(k_resize_rows<MAP_RESIZE, 0>, (int)sizeof(RShared<0>), plan);
     if (rc != ALB_OK || !split) return rc;
     PlanCheck c1 = chk;
     c1.reduce = 1;
