@@ -237,7 +237,7 @@ struct PlanCheck {
   PrmList prm;
   int32_t* status;
   int32_t filter_c;   // 0: all images; k > 0: only images with c == k; k < 0: only c != -k (others: no items, no error)
-  int32_t reduce = 0; // resizes: 0 all images; 1 only reductions (window over 17/16 of the output on an axis); -1 the others
+  int32_t reduce = 0; // resizes: 0 all images; 1 only reductions past 17/16 that fit the large box; -1 the others
 };
 
 ALB_D bool plan_filtered_out(const PlanCheck& chk, const alb_image& im) {

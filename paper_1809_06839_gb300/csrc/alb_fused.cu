@@ -389,9 +389,10 @@ __global__ void __launch_bounds__(256) k_chain_fused(int32_t n, const alb_params
 #pragma unroll
           for (int q = 0; q < 3; q++) v[q] = (float)rgb[q];
         }
+        if (ALB_IN(y < K.oh && x < K.ow)) {
 #pragma unroll
-        if (ALB_IN(y < K.oh && x < K.ow))
           for (int q = 0; q < 3; q++) ob[q * plane + (int64_t)y * K.ow + x] = chain_normalize(v[q], K.k[q], K.m[q]);
+        }
       }
     }
     if (MASKS) {
@@ -888,7 +889,7 @@ size_t chain_workspace(const alb_chain_cfg& cfg, int32_t n, int32_t mode) {
   size_t b = 4096 + (size_t)n * 512 + (size_t)n * 8 + 512;   // queue, tables, pivot sums
   if (mode == ALB_MODE_PLAIN)   // intermediates, step records, descriptors, plan, 3-channel tables
     b += 2 * px * 3 + px * 3 * 4 + (size_t)n * 3 * sizeof(alb_params) + (size_t)n * 2 * sizeof(alb_image) +
-         (size_t)(2 * n + 1) * 4 + (size_t)n * 768 + 8 * 256;
+         (size_t)(4 * n + 2) * 4 + (size_t)n * 768 + 10 * 256;
   return b;
 }
 
@@ -1140,15 +1141,17 @@ alb_status launch_chain(const alb_chain_cfg& cfg, int32_t n, const alb_params* p
   alb_image* desc = ws.take<alb_image>((size_t)n * 2);
   int32_t* prefix = ws.take<int32_t>((size_t)n + 1);
   int32_t* rpi = ws.take<int32_t>((size_t)n);
+  int32_t* prefix2 = ws.take<int32_t>((size_t)n + 1);   // the resize step's second tile plan (reductions)
+  int32_t* rpi2 = ws.take<int32_t>((size_t)n);
   uint8_t* luts768 = jit ? nullptr : ws.take<uint8_t>((size_t)n * 768);
-  ALB_REQUIRE(a && b && (jit || (f && luts768)) && rec && desc && prefix && rpi, ALB_EWORKSPACE,
+  ALB_REQUIRE(a && b && (jit || (f && luts768)) && rec && desc && prefix && rpi && prefix2 && rpi2, ALB_EWORKSPACE,
               "alb_apply_batch: workspace too small for plain mode");
   alb_params *rrc = rec, *fl = rec + n, *lr = rec + 2 * n;
   alb_image *da = desc, *db = desc + n;
   k_plain_records<<<(n + 127) / 128, 128, 0, st>>>(n, params, K, a, b, rrc, fl, lr, da, db);
   ALB_CUDA(cudaGetLastError());
   const ImgList lin{in, {}}, la{da, {}}, lb{db, {}};
-  const Plan plan{prefix, rpi, n};
+  const Plan plan{prefix, rpi, n, prefix2, rpi2};
   // crop + resize: the ragged RandomResizedCrop launch
   {
     const PrmList pr{rrc, {}};

@@ -57,7 +57,11 @@ __global__ void k_plan_tiles(ImgList out, int32_t n, int32_t tile_w, int32_t til
       if (plan_filtered_out(chk, im)) cnt = 0;
       if (chk.reduce != 0 && cnt) {
         const alb_params& pr = chk.prm.get(i);
-        const bool red = 16 * (int64_t)pr.cw > 17 * (int64_t)im.w || 16 * (int64_t)pr.ch > 17 * (int64_t)im.h;
+        // reductions past 17/16 on an axis whose 32 x 16 tiles fit the 68 x 36 box
+        // (31 f + 2 <= 67 columns, 15 f + 2 <= 35 rows); stronger ones keep the
+        // 32 x 32 tiles, which read global memory either way
+        const bool red = (16 * (int64_t)pr.cw > 17 * (int64_t)im.w || 16 * (int64_t)pr.ch > 17 * (int64_t)im.h) &&
+                         100 * (int64_t)pr.cw <= 209 * (int64_t)im.w && 10 * (int64_t)pr.ch <= 22 * (int64_t)im.h;
         if (red != (chk.reduce > 0)) cnt = 0;
       }
     }
@@ -1070,8 +1074,8 @@ alb_status launch_tile_geometric(int32_t tid, const Plan& plan, const ImgList& i
   int32_t* prefix = const_cast<int32_t*>(plan.prefix);
   int32_t* tiles_x = const_cast<int32_t*>(plan.rows_per_item);
   if ((resize || grid) && !mask) {
-    // resizes with a second plan: reductions beyond 17/16 on an axis through
-    // the 68 x 36 box (32 x 16 tiles), the rest through the 36 x 36 box
+    // resizes with a second plan: reductions beyond 17/16 on an axis that fit
+    // the 68 x 36 box (32 x 16 tiles) through it, the rest through the 36 x 36 box
     const bool split = resize && plan.prefix2 && plan.rows2;
     PlanCheck c0 = chk;
     c0.reduce = split ? -1 : 0;
