@@ -444,13 +444,15 @@ def fused_pipeline(dev, stream, steps=3, warmup=2, n=FUSED_N):
     try:
         kt = kernel_times(lambda: run(A.MODE_PLAIN, wsp), reps=3)
         kt.update({k: v for k, v in kernel_times(lambda: run(A.MODE_FUSED, wsf), reps=3).items() if "k_chain_fused" in k})
-        step_res = {}
-        for name, t in kt.items():
+        tsum = {}
+        for name, t in kt.items():   # a step may run as several kernel instantiations: their times add
             base = next((b for b in steps_bytes if b in name), None)
-            if base is None or t <= 0:
-                continue
+            if base is not None and t > 0:
+                tsum[base] = tsum.get(base, 0.0) + t
+        step_res = {}
+        for base, t in tsum.items():
             step_res[base] = {"ms": round(t * 1e3, 4), "gbs": round(steps_bytes[base] / t / 1e9, 1),
-                           "frac": round(steps_bytes[base] / t / 1e9 / hbm, 4)}
+                              "frac": round(steps_bytes[base] / t / 1e9 / hbm, 4)}
         res["steps"] = step_res
     except Exception as ex:  # the per-kernel breakdown needs the profiler's CUDA activity trace
         res["steps"] = {"error": str(ex)[:160]}
