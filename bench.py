@@ -625,10 +625,10 @@ def distortions(dev, stream, hbm, n=SUITE_N):
     return res
 
 
-def large_suite(dev, stream, hbm, n=LARGE_N):
+def large_suite(dev, stream, hbm, n=LARGE_N, only=None):
     """The same 15 transforms on images of at least 512 x 512 (H, W ~ U[512, 1024]),
     the size class the HBM-fraction target refers to."""
-    s = Suite(dev, 0, n=n, lo=512, hi=1024)
+    s = Suite(dev, 0, n=n, only=only, lo=512, hi=1024)
     t = per_op_times(s, stream, reps=5)
     res = {}
     for op in s.ops:
@@ -862,6 +862,7 @@ def main():
                     help="sub-workloads to run after the suite (comma-separated)")
     ap.add_argument("--fused-n", type=int, default=FUSED_N, help="images of the fused workload (profiling runs)")
     ap.add_argument("--diff-b", type=int, default=DIFF_B, help="batch of the differentiable workload (profiling runs)")
+    ap.add_argument("--large-n", type=int, default=LARGE_N, help="images of the 512-1024 px leg (profiling runs)")
     args = ap.parse_args()
     ws, rank, local, dist = dist_setup(args)
     if args.impl == "reference":
@@ -920,7 +921,8 @@ def main():
         if "differentiable" in which:
             extra["differentiable"] = differentiable(dev, stream, n=args.diff_b)
         if "large" in which:
-            extra["per_transform_large"] = large_suite(dev, stream, hbm)
+            extra["per_transform_large"] = large_suite(dev, stream, hbm, n=args.large_n,
+                                                       only=set(args.only.split(",")) if args.only else None)
         if "distort" in which:
             extra["distortions"] = distortions(dev, stream, hbm)
         if "targets" in which:
