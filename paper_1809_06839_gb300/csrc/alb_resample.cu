@@ -705,8 +705,10 @@ __global__ void __launch_bounds__(32 * RWARP) k_resize_rows(Plan plan, ImgList i
 // table holds row * pitch + byte
 // phase, so a tap row's
 // offset is one shared load.  Tiles whose box crosses the left/right image
-// border map each tap column through reflect-101; tiles whose footprint does
-// not fit read their taps from global memory.
+// border stage the reflected column range in source order and map the two tap
+// columns through the fold, reading a mirrored pair as the staged pair with
+// its horizontal weights swapped; tiles whose footprint does not fit read
+// their taps from global memory.
 constexpr int AT_W = 32, AT_H = 20;   // output tile (columns x rows)
 constexpr int AB = 48;                // staged box side (pixels)
 constexpr int APITCH = 176;           // staged row pitch in bytes
@@ -834,6 +836,25 @@ ALB_D void a_tile_stage(const AImg& k, const ATile& g, int lane, uint8_t* box, i
   }
 }
 
+// reflect-101 of a column within one fold (|i| < n for i < 0, i <= 2 (n - 1) above)
+ALB_D int32_t refl1(int32_t i, int32_t n) { return i < 0 ? -i : (i >= n ? 2 * (n - 1) - i : i); }
+
+// Q5 bilinear of one RGB pixel from the raw tap pairs of its two rows (lo =
+// bytes 0..3, hi = bytes 4..5 of pixels (x, x + 1)): the pairs as {R0, R1, G0,
+// G1} and {B0, B1} against the 16-bit weight pairs (wxp.lo wy, wxp.hi wy) of
+// the top (wy = 32 - fy) and bottom (wy = fy) row, where wxp holds the
+// horizontal weights of the first and second pixel; two dp2a per channel
+// give sum w_ij p_ij + 512 exactly
+ALB_D void a_bilerp(uint32_t tl, uint32_t th2, uint32_t bl, uint32_t bh2, uint32_t wxp, int32_t fy, uint32_t& vr,
+                    uint32_t& vg, uint32_t& vb) {
+  const uint32_t wt = wxp * (uint32_t)(32 - fy), wb = wxp * (uint32_t)fy;
+  const uint32_t pt = __byte_perm(tl, th2, 0x4130), qt = __byte_perm(tl, th2, 0x0052);
+  const uint32_t pb = __byte_perm(bl, bh2, 0x4130), qb = __byte_perm(bl, bh2, 0x0052);
+  vr = __dp2a_lo(wt, pt, __dp2a_lo(wb, pb, 512u)) >> 10;
+  vg = __dp2a_hi(wt, pt, __dp2a_hi(wb, pb, 512u)) >> 10;
+  vb = __dp2a_lo(wt, qt, __dp2a_lo(wb, qb, 512u)) >> 10;
+}
+
 ALB_D void a_store3(uint8_t* od, uint32_t r, uint32_t g, uint32_t b) {
   od[0] = (uint8_t)r; od[1] = (uint8_t)g; od[2] = (uint8_t)b;
 }
@@ -858,34 +879,29 @@ ALB_D void a_tile_compute(const AImg& k, const ATile& g, int lane, const uint8_t
           taps_row(box, rowoff[iy] + o, tl, th2);
           taps_row(box, rowoff[iy + 1] + o, bl, bh2);
         }
-        // the tap pairs as {R0, R1, G0, G1} and {B0, B1} per row, against the
-        // 16-bit weight pairs ((32 - fx) wy, fx wy) of the top (wy = 32 - fy) and
-        // bottom (wy = fy) row: two dp2a per channel give sum w_ij p_ij + 512
-        const uint32_t wxp = 32u + 65535u * (uint32_t)fx;                  // {32 - fx, fx}
-        const uint32_t wt = wxp * (uint32_t)(32 - fy), wb = wxp * (uint32_t)fy;
-        const uint32_t pt = __byte_perm(tl, th2, 0x4130), qt = __byte_perm(tl, th2, 0x0052);
-        const uint32_t pb = __byte_perm(bl, bh2, 0x4130), qb = __byte_perm(bl, bh2, 0x0052);
-        const uint32_t vr = __dp2a_lo(wt, pt, __dp2a_lo(wb, pb, 512u)) >> 10;
-        const uint32_t vg = __dp2a_hi(wt, pt, __dp2a_hi(wb, pb, 512u)) >> 10;
-        const uint32_t vb = __dp2a_lo(wt, qt, __dp2a_lo(wb, qb, 512u)) >> 10;
+        uint32_t vr, vg, vb;
+        a_bilerp(tl, th2, bl, bh2, 32u + 65535u * (uint32_t)fx, fy, vr, vg, vb);   // {32 - fx, fx}
         if (store && ALB_IN(g.oy0 + r < k.OH && g.ox0 + lane < k.OW)) a_store3(od, vr, vg, vb);
       }
     } else {
-      const int32_t W = k.W;
+      // the box spans one fold at most: the two tap columns map through it with
+      // one comparison each; a mirrored pair (x, x - 1) is the staged pair
+      // (x - 1, x) with the horizontal weights swapped
+      const int32_t W = k.W, span3 = 3 * (g.rb - g.ra);
       for (int r = 0; r < g.th; r++, X += q1, Y += q4, od += k.dstride) {
         const int32_t ix = X >> 16, fx = (X >> 11) & 31, iy = Y >> 16, fy = (Y >> 11) & 31;
-        const int xa = 3 * (reflect101(g.bx0 + ix, W) - g.ra), xb = 3 * (reflect101(g.bx0 + ix + 1, W) - g.ra);
-        if (!ALB_IN(iy >= 0 && iy + 1 < g.bh && xa >= 0 && xb >= 0 && xa <= 3 * (g.rb - g.ra) && xb <= 3 * (g.rb - g.ra)))
-          continue;
-        const int o0 = rowoff[iy], o1 = rowoff[iy + 1];
-        const int w11 = fx * fy, w01 = 32 * fx - w11, w10 = 32 * fy - w11, w00 = 1024 - 32 * fx - 32 * fy + w11;
-        uint32_t v[3];
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-          const int acc = w00 * box[o0 + xa + c] + w01 * box[o0 + xb + c] + w10 * box[o1 + xa + c] + w11 * box[o1 + xb + c];
-          v[c] = (uint32_t)((acc + 512) >> 10);
+        const int32_t xa = refl1(g.bx0 + ix, W), xb = refl1(g.bx0 + ix + 1, W);
+        const bool swp = xb < xa;
+        const int32_t o = 3 * ((swp ? xb : xa) - g.ra);
+        uint32_t tl = 0u, th2 = 0u, bl = 0u, bh2 = 0u;
+        if (ALB_IN(iy >= 0 && iy + 1 < g.bh && o >= 0 && o + 3 <= span3)) {
+          taps_row(box, rowoff[iy] + o, tl, th2);
+          taps_row(box, rowoff[iy + 1] + o, bl, bh2);
         }
-        if (store && ALB_IN(g.oy0 + r < k.OH && g.ox0 + lane < k.OW)) a_store3(od, v[0], v[1], v[2]);
+        const uint32_t wxp = swp ? (32u << 16) - 65535u * (uint32_t)fx : 32u + 65535u * (uint32_t)fx;
+        uint32_t vr, vg, vb;
+        a_bilerp(tl, th2, bl, bh2, wxp, fy, vr, vg, vb);
+        if (store && ALB_IN(g.oy0 + r < k.OH && g.ox0 + lane < k.OW)) a_store3(od, vr, vg, vb);
       }
     }
   } else {
