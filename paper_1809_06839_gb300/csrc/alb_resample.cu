@@ -773,45 +773,72 @@ ALB_D void a_tile_geo(const AImg& k, int32_t item, ATile& g) {
     g.mode = ok && hi - lo + 1 <= AB - 1 ? 1 : 2;
   }
 }
+// reflect-101 of a column within one fold (|i| < n for i < 0, i <= 2 (n - 1) above)
+ALB_D int32_t refl1(int32_t i, int32_t n) { return i < 0 ? -i : (i >= n ? 2 * (n - 1) - i : i); }
 
-// Lane r (and r + 32) stages box row r (reflected source row): raw aligned
-// chunks; rowoff[r] = r * pitch + the row's byte phase.
-// x-extent [lo, hi] of the parallelogram V0 V1 V2 V3 (in order) inside the
-// horizontal band [yl, yh]; lo > hi when they do not meet
-ALB_D void band_extent(const float (&vx)[4], const float (&vy)[4], float yl, float yh, float& lo, float& hi) {
-  lo = 3e38f; hi = -3e38f;
+// The mapped tile as a convex parallelogram (box-relative pixel units, with
+// the Q16 -> Q5 rounding bias): its y-range and its left and right chains.
+// The least x over a horizontal band is the left chain at the band point
+// nearest to the leftmost vertex (the chain is convex), and likewise on the
+// right; the chains' slopes are computed once per tile.
+struct AChains {
+  float ymin, ymax;
+  float xl, yl, kl_up, kl_dn;   // leftmost vertex; dx/dy of the chain above and below it
+  float xr, yr, kr_up, kr_dn;   // rightmost vertex
+};
+
+ALB_D void a_chains(const AImg& k, const ATile& g, AChains& c) {
+  const float s = 1.0f / 65536.0f;
+  const float x0 = (float)(g.X00 + 1024 - 65536 * (int64_t)g.bx0) * s, y0 = (float)(g.Y00 + 1024 - 65536 * (int64_t)g.by0) * s;
+  const float ux = (float)(k.q[0] * (g.tw - 1)) * s, uy = (float)(k.q[3] * (g.tw - 1)) * s;
+  const float wx = (float)(k.q[1] * (g.th - 1)) * s, wy = (float)(k.q[4] * (g.th - 1)) * s;
+  const float vx[4] = {x0, x0 + ux, x0 + ux + wx, x0 + wx}, vy[4] = {y0, y0 + uy, y0 + uy + wy, y0 + wy};
+  // running extreme vertices as values (indexed arrays would live in local memory)
+  float lx = vx[0], ly = vy[0], rx = vx[0], ry = vy[0];
+  float tlx = vx[0], tly = vy[0], blx = vx[0], bly = vy[0], trx = vx[0], try_ = vy[0], brx = vx[0], bry = vy[0];
 #pragma unroll
-  for (int i = 0; i < 4; i++) {
-    const float x0 = vx[i], y0 = vy[i], x1 = vx[(i + 1) & 3], y1 = vy[(i + 1) & 3];
-    if (y0 >= yl && y0 <= yh) { lo = fminf(lo, x0); hi = fmaxf(hi, x0); }
-    const float dy = y1 - y0;
-    if (dy != 0.0f) {
-      const float rdx = (x1 - x0) / dy;
-      const float ta = yl - y0, tb = yh - y0;
-      if ((ta > 0.0f) == (ta < dy) && ta != 0.0f) { const float x = fmaf(ta, rdx, x0); lo = fminf(lo, x); hi = fmaxf(hi, x); }
-      if ((tb > 0.0f) == (tb < dy) && tb != 0.0f) { const float x = fmaf(tb, rdx, x0); lo = fminf(lo, x); hi = fmaxf(hi, x); }
-    }
+  for (int i = 1; i < 4; i++) {
+    const float x = vx[i], y = vy[i];
+    if (x < lx) { lx = x; ly = y; }
+    if (x > rx) { rx = x; ry = y; }
+    // top / bottom vertex, ties broken to the left (left chain) or right (right chain)
+    if (y < tly || (y == tly && x < tlx)) { tlx = x; tly = y; }
+    if (y > bly || (y == bly && x < blx)) { blx = x; bly = y; }
+    if (y < try_ || (y == try_ && x > trx)) { trx = x; try_ = y; }
+    if (y > bry || (y == bry && x > brx)) { brx = x; bry = y; }
   }
+  c.ymin = tly; c.ymax = bly;
+  c.xl = lx; c.yl = ly; c.xr = rx; c.yr = ry;
+  c.kl_up = ly > tly ? (lx - tlx) / (ly - tly) : 0.0f;
+  c.kl_dn = bly > ly ? (blx - lx) / (bly - ly) : 0.0f;
+  c.kr_up = ry > try_ ? (rx - trx) / (ry - try_) : 0.0f;
+  c.kr_dn = bry > ry ? (brx - rx) / (bry - ry) : 0.0f;
+}
+
+// x-extent [lo, hi] of the parallelogram inside the band [ya, yb]; lo > hi when they do not meet
+ALB_D void a_band(const AChains& c, float ya, float yb, float& lo, float& hi) {
+  const float y0 = fmaxf(ya, c.ymin), y1 = fminf(yb, c.ymax);
+  if (y0 > y1) { lo = 1.0f; hi = 0.0f; return; }
+  const float yl = fminf(fmaxf(c.yl, y0), y1), yr = fminf(fmaxf(c.yr, y0), y1);
+  lo = fmaf(yl - c.yl, yl < c.yl ? c.kl_up : c.kl_dn, c.xl);
+  hi = fmaf(yr - c.yr, yr < c.yr ? c.kr_up : c.kr_dn, c.xr);
 }
 
 ALB_D void a_tile_stage(const AImg& k, const ATile& g, int lane, uint8_t* box, int32_t* rowoff) {
   if (g.mode == 2) return;
   const int span = 3 * (g.rb - g.ra + 1);
   // inside tiles stage, per box row, only the columns that the tile's taps
-  // can read: the mapped tile (a parallelogram, box-relative pixel units with
-  // the Q16 -> Q5 rounding bias) meets row r's band [r - 1, r + 1) of tap
-  // rows; columns floor(x) and floor(x) + 1 of that extent, with a margin
-  float vx[4], vy[4];
-  if (g.mode == 0) {
-    const float s = 1.0f / 65536.0f;
-    const float x0 = (float)(g.X00 + 1024 - 65536 * (int64_t)g.bx0) * s, y0 = (float)(g.Y00 + 1024 - 65536 * (int64_t)g.by0) * s;
-    const float ux = (float)(k.q[0] * (g.tw - 1)) * s, uy = (float)(k.q[3] * (g.tw - 1)) * s;
-    const float wx = (float)(k.q[1] * (g.th - 1)) * s, wy = (float)(k.q[4] * (g.th - 1)) * s;
-    vx[0] = x0; vy[0] = y0; vx[1] = x0 + ux; vy[1] = y0 + uy;
-    vx[2] = x0 + ux + wx; vy[2] = y0 + uy + wy; vx[3] = x0 + wx; vy[3] = y0 + wy;
-  }
+  // can read: the mapped tile meets row r's band [r - 1, r + 1) of tap rows;
+  // columns floor(x) and floor(x) + 1 of that extent, with a margin
+  AChains ch;
+  if (g.mode == 0) a_chains(k, g, ch);
   for (int r = lane; r < g.bh; r += 32) {
-    const int ry = reflect101(g.by0 + r, k.H);
+    const int32_t yr = g.by0 + r;
+    int32_t ry = yr;
+    if ((uint32_t)yr >= (uint32_t)k.H) {
+      const int32_t t1 = refl1(yr, k.H);
+      ry = (k.H > 1 && (uint32_t)t1 < (uint32_t)k.H) ? t1 : reflect101(yr, k.H);
+    }
     const uintptr_t first = reinterpret_cast<uintptr_t>(k.src) + (uintptr_t)((int64_t)ry * k.sstride) +
                             (uintptr_t)(3 * g.ra);
     const uintptr_t c0 = first & ~uintptr_t(15);
@@ -820,7 +847,7 @@ ALB_D void a_tile_stage(const AImg& k, const ATile& g, int lane, uint8_t* box, i
     int j0 = 0, j1 = ((ph + span + 15) >> 4) - 1;
     if (g.mode == 0) {
       float lo, hi;
-      band_extent(vx, vy, (float)r - 1.05f, (float)r + 1.05f, lo, hi);
+      a_band(ch, (float)r - 1.05f, (float)r + 1.05f, lo, hi);
       if (lo > hi) continue;                                   // no tap reads this row
       const int cl = imax((int)floorf(lo - 0.05f), 0), chh = imin((int)floorf(hi + 0.05f) + 1, g.bw - 1);
       if (cl > chh) continue;
@@ -835,9 +862,6 @@ ALB_D void a_tile_stage(const AImg& k, const ATile& g, int lane, uint8_t* box, i
         cp_async16(d + 16 * j, reinterpret_cast<const void*>(c0 + 16 * j));
   }
 }
-
-// reflect-101 of a column within one fold (|i| < n for i < 0, i <= 2 (n - 1) above)
-ALB_D int32_t refl1(int32_t i, int32_t n) { return i < 0 ? -i : (i >= n ? 2 * (n - 1) - i : i); }
 
 // Q5 bilinear of one RGB pixel from the raw tap pairs of its two rows (lo =
 // bytes 0..3, hi = bytes 4..5 of pixels (x, x + 1)): the pairs as {R0, R1, G0,
