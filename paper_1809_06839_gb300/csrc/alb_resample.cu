@@ -788,10 +788,13 @@ struct AChains {
 };
 
 ALB_D void a_chains(const AImg& k, const ATile& g, AChains& c) {
+  // inside tiles span at most AB pixels, so every Q16 value here fits 32 bits
+  // (64-bit integer to float conversions run on the slow double-precision pipe)
   const float s = 1.0f / 65536.0f;
-  const float x0 = (float)(g.X00 + 1024 - 65536 * (int64_t)g.bx0) * s, y0 = (float)(g.Y00 + 1024 - 65536 * (int64_t)g.by0) * s;
-  const float ux = (float)(k.q[0] * (g.tw - 1)) * s, uy = (float)(k.q[3] * (g.tw - 1)) * s;
-  const float wx = (float)(k.q[1] * (g.th - 1)) * s, wy = (float)(k.q[4] * (g.th - 1)) * s;
+  const float x0 = (float)(int32_t)(g.X00 + 1024 - 65536 * (int64_t)g.bx0) * s;
+  const float y0 = (float)(int32_t)(g.Y00 + 1024 - 65536 * (int64_t)g.by0) * s;
+  const float ux = (float)((int32_t)k.q[0] * (g.tw - 1)) * s, uy = (float)((int32_t)k.q[3] * (g.tw - 1)) * s;
+  const float wx = (float)((int32_t)k.q[1] * (g.th - 1)) * s, wy = (float)((int32_t)k.q[4] * (g.th - 1)) * s;
   const float vx[4] = {x0, x0 + ux, x0 + ux + wx, x0 + wx}, vy[4] = {y0, y0 + uy, y0 + uy + wy, y0 + wy};
   // running extreme vertices as values (indexed arrays would live in local memory)
   float lx = vx[0], ly = vy[0], rx = vx[0], ry = vy[0];

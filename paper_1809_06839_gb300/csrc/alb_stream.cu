@@ -405,8 +405,20 @@ __global__ void __launch_bounds__(256) k_pixel_stream(Plan plan, ImgList in, Img
     const alb_params& p = prm.get(b);
     r1 = imin(r1, so.h);
     const bool act = p.apply != 0;
-    const PixArgs pa{s_rcp, (float)(2.0 * p.shift[0]) * (1.0f / 60.0f), (float)(p.shift[1] / 255.0),
-                     (float)(p.shift[2] / 255.0)};
+    // the per-image shifts in float (from the record's doubles), formed by one
+    // lane per warp: double-precision work is slow on this part
+    float dh6 = 0.0f, ds = 0.0f, dv = 0.0f;
+    if (OP == 1) {
+      if ((threadIdx.x & 31) == 0) {
+        dh6 = (float)(2.0 * p.shift[0]) * (1.0f / 60.0f);
+        ds = (float)(p.shift[1] / 255.0);
+        dv = (float)(p.shift[2] / 255.0);
+      }
+      dh6 = __shfl_sync(0xffffffffu, dh6, 0);
+      ds = __shfl_sync(0xffffffffu, ds, 0);
+      dv = __shfl_sync(0xffffffffu, dv, 0);
+    }
+    const PixArgs pa{s_rcp, dh6, ds, dv};
     const uint8_t* __restrict__ ip = (const uint8_t*)si.data;
     uint8_t* __restrict__ op = (uint8_t*)so.data;
     if (flat_aligned(si) && flat_aligned(so)) {
