@@ -62,28 +62,25 @@ ALB_D void chain_pair(const uint8_t* p, uint32_t& lo, uint32_t& hi) {
   hi = __funnelshift_r(w1, w2, 8 * s);
 }
 
-// Q5 bilinear sample (3 channels) of the crop window at Q5 coordinates
-// (xq, yq): (sum w_ij p_ij + 512) >> 10, evaluated exactly as
-// ((32 - fy) h_top + fy h_bot + 512) >> 10, h = (32 - fx) p0 + fx p1, with
-// dp4a for the horizontal pairs and dp2a for the vertical pair.
-ALB_D void chain_bilinear(const uint8_t* __restrict__ win, int64_t stride, int32_t ch, int32_t cw, int32_t xq,
-                          int32_t yq, uint32_t rgb[3]) {
+// Q5 bilinear sample (3 channels) from the window's two tap rows ra (row iy)
+// and rb (row min(iy + 1, ch - 1)) at the Q5 column xq, vertical fraction fy:
+// (sum w_ij p_ij + 512) >> 10.  The tap pairs as {R0, R1, G0, G1} and {B0, B1}
+// per row against the 16-bit weight pairs (wx0 wy, wx1 wy) of the top (wy =
+// 32 - fy) and bottom (wy = fy) row: two dp2a per channel.
+ALB_D void chain_bilerp(const uint8_t* __restrict__ ra, const uint8_t* __restrict__ rb, int32_t cw, int32_t xq,
+                        int32_t fy, uint32_t rgb[3]) {
   int32_t ix = xq >> 5;
-  const int32_t fx = xq & 31, iy = yq >> 5, fy = yq & 31;
-  const int32_t iyb = imin(iy + 1, ch - 1);
-  if (!ALB_IN(iy >= 0 && iy < ch && ix >= 0 && ix < cw)) {
+  const int32_t fx = xq & 31;
+  if (!ALB_IN(ix >= 0 && ix < cw)) {
     rgb[0] = rgb[1] = rgb[2] = 0u;
     return;
   }
-  const uint8_t* ra = win + (int64_t)iy * stride;
-  const uint8_t* rb = win + (int64_t)iyb * stride;
-  uint32_t wx = (uint32_t)(32 - fx) | ((uint32_t)fx << 8);
-  const uint32_t wy = (uint32_t)(32 - fy) | ((uint32_t)fy << 8);
+  uint32_t wxp = 32u + 65535u * (uint32_t)fx;       // {32 - fx, fx}: weights of pixels ix, ix + 1
   uint32_t tl, th, bl, bh;
   if (cw >= 2) {
-    if (ix + 1 >= cw) {   // clamped last column (fx = 0): pair (ix - 1, ix), weights swapped
+    if (ix + 1 >= cw) {   // clamped last column (fx = 0): the pair (ix - 1, ix), all weight on the second
       ix -= 1;
-      wx = 32u << 8;
+      wxp = 32u << 16;
     }
     chain_pair(ra + 3 * ix, tl, th);
     chain_pair(rb + 3 * ix, bl, bh);
@@ -91,26 +88,37 @@ ALB_D void chain_bilinear(const uint8_t* __restrict__ win, int64_t stride, int32
     const uint32_t t = (uint32_t)ra[0] | ((uint32_t)ra[1] << 8) | ((uint32_t)ra[2] << 16);
     const uint32_t u = (uint32_t)rb[0] | ((uint32_t)rb[1] << 8) | ((uint32_t)rb[2] << 16);
     tl = t | (t << 24); th = t >> 8; bl = u | (u << 24); bh = u >> 8;
-    wx = 32u;
+    wxp = 32u;
   }
-  const uint32_t ht_r = __dp4a(__byte_perm(tl, th, 0x0030), wx, 0u);
-  const uint32_t hb_r = __dp4a(__byte_perm(bl, bh, 0x0030), wx, 0u);
-  const uint32_t ht_g = __dp4a(__byte_perm(tl, th, 0x0041), wx, 0u);
-  const uint32_t hb_g = __dp4a(__byte_perm(bl, bh, 0x0041), wx, 0u);
-  const uint32_t ht_b = __dp4a(__byte_perm(tl, th, 0x0052), wx, 0u);
-  const uint32_t hb_b = __dp4a(__byte_perm(bl, bh, 0x0052), wx, 0u);
-  rgb[0] = __dp2a_lo(__byte_perm(ht_r, hb_r, 0x5410), wy, 512u) >> 10;
-  rgb[1] = __dp2a_lo(__byte_perm(ht_g, hb_g, 0x5410), wy, 512u) >> 10;
-  rgb[2] = __dp2a_lo(__byte_perm(ht_b, hb_b, 0x5410), wy, 512u) >> 10;
+  const uint32_t wt = wxp * (uint32_t)(32 - fy), wb = wxp * (uint32_t)fy;
+  const uint32_t pt = __byte_perm(tl, th, 0x4130), qt = __byte_perm(tl, th, 0x0052);
+  const uint32_t pb = __byte_perm(bl, bh, 0x4130), qb = __byte_perm(bl, bh, 0x0052);
+  rgb[0] = __dp2a_lo(wt, pt, __dp2a_lo(wb, pb, 512u)) >> 10;
+  rgb[1] = __dp2a_hi(wt, pt, __dp2a_hi(wb, pb, 512u)) >> 10;
+  rgb[2] = __dp2a_lo(wt, qt, __dp2a_lo(wb, qb, 512u)) >> 10;
 }
+
+// the same at Q5 coordinates (xq, yq) of the window
+ALB_D void chain_bilinear(const uint8_t* __restrict__ win, int64_t stride, int32_t ch, int32_t cw, int32_t xq,
+                          int32_t yq, uint32_t rgb[3]) {
+  const int32_t iy = yq >> 5;
+  if (!ALB_IN(iy >= 0 && iy < ch)) {
+    rgb[0] = rgb[1] = rgb[2] = 0u;
+    return;
+  }
+  chain_bilerp(win + (int64_t)iy * stride, win + (int64_t)imin(iy + 1, ch - 1) * stride, cw, xq, yq & 31, rgb);
+}
+
+// a byte as float through the 2^23 bias (exact; no integer conversion unit)
+ALB_D float u8f(uint32_t v) { return __uint_as_float(0x4B000000u | v) - 8388608.0f; }
 
 // saturation blend with the BT.601 grey value, float32, clamped, not rounded
 ALB_D void chain_saturate(const uint32_t rgb[3], float s, float out[3]) {
-  const float r = (float)rgb[0], g = (float)rgb[1], b = (float)rgb[2];
-  const float grey = __fmaf_rn(0.114f, b, __fmaf_rn(0.587f, g, __fmul_rn(0.299f, r)));
+  const float f[3] = {u8f(rgb[0]), u8f(rgb[1]), u8f(rgb[2])};
+  const float grey = __fmaf_rn(0.114f, f[2], __fmaf_rn(0.587f, f[1], __fmul_rn(0.299f, f[0])));
 #pragma unroll
   for (int c = 0; c < 3; c++) {
-    float v = __fmaf_rn(s, __fsub_rn((float)rgb[c], grey), grey);
+    float v = __fmaf_rn(s, __fsub_rn(f[c], grey), grey);
     out[c] = fminf(fmaxf(v, 0.0f), 255.0f);
   }
 }
@@ -310,6 +318,8 @@ __global__ void __launch_bounds__(256) k_chain_fused(int32_t n, const alb_params
   __shared__ uint8_t s_lut[TAB];
   __shared__ int32_t s_col[1024];
   __shared__ int32_t s_row[kBandMax];
+  __shared__ const uint8_t* s_ra[kBandMax];   // per band row: the window's two tap rows
+  __shared__ const uint8_t* s_rb[kBandMax];
   __shared__ int32_t s_cnn[1024];      // masks: nearest source column of each output column (flip folded)
   __shared__ int32_t s_rnn[kBandMax];
   const int32_t bands = (K.oh + band - 1) / band;
@@ -333,24 +343,35 @@ __global__ void __launch_bounds__(256) k_chain_fused(int32_t n, const alb_params
       }
       cached = b;
     }
+    const alb_image im = imgs[b];
+    const uint8_t* win = (const uint8_t*)im.data + (int64_t)p.y0 * im.row_stride + 3 * (int64_t)p.x0;
     if (threadIdx.x < r1 - r0) {
-      s_row[threadIdx.x] = chain_q5(r0 + threadIdx.x, p.ch, K.oh);
+      const int32_t yq = chain_q5(r0 + threadIdx.x, p.ch, K.oh), iy = yq >> 5;
+      s_row[threadIdx.x] = yq;
+      s_ra[threadIdx.x] = win + (int64_t)iy * im.row_stride;
+      s_rb[threadIdx.x] = win + (int64_t)imin(iy + 1, p.ch - 1) * im.row_stride;
       if (MASKS) s_rnn[threadIdx.x] = chain_nn(r0 + threadIdx.x, p.ch, K.oh);
     }
     __syncthreads();
-    const alb_image im = imgs[b];
-    const uint8_t* win = (const uint8_t*)im.data + (int64_t)p.y0 * im.row_stride + 3 * (int64_t)p.x0;
     const float s = (float)p.sat;
     __nv_bfloat16* ob = out + (int64_t)b * 3 * plane;
     if (pairs) {
       const int32_t hw = K.ow >> 1;
       const int32_t npair = (r1 - r0) * hw;
+      // pair i = (band row yy, pair column xp), advanced by blockDim.x pairs a
+      // step without dividing
+      const int32_t dyy = (int32_t)blockDim.x / hw, dxp = (int32_t)blockDim.x - dyy * hw;
+      int32_t yy = (int32_t)threadIdx.x / hw, xp = (int32_t)threadIdx.x - yy * hw;
       for (int32_t i = threadIdx.x; i < npair; i += blockDim.x) {
-        const int32_t yy = i / hw, x = 2 * (i - yy * hw), y = r0 + yy;
-        const int32_t yq = s_row[yy];
+        const int32_t x = 2 * xp, y = r0 + yy;
+        const int32_t fy = s_row[yy] & 31;
+        const uint8_t* ra = s_ra[yy];
+        const uint8_t* rb = s_rb[yy];
+        xp += dxp; yy += dyy;
+        if (xp >= hw) { xp -= hw; yy++; }
         uint32_t a[3], c[3];
-        chain_bilinear(win, im.row_stride, p.ch, p.cw, s_col[x], yq, a);
-        chain_bilinear(win, im.row_stride, p.ch, p.cw, s_col[x + 1], yq, c);
+        chain_bilerp(ra, rb, p.cw, s_col[x], fy, a);
+        chain_bilerp(ra, rb, p.cw, s_col[x + 1], fy, c);
         float va[3], vc[3];
         if (MODE == 0) {
 #pragma unroll
@@ -361,17 +382,14 @@ __global__ void __launch_bounds__(256) k_chain_fused(int32_t n, const alb_params
           jitter_ops(a, p.k, 0, 3, s_lut, s_lut + 256, s);
           jitter_ops(c, p.k, 0, 3, s_lut, s_lut + 256, s);
 #pragma unroll
-          for (int q = 0; q < 3; q++) { va[q] = (float)a[q]; vc[q] = (float)c[q]; }
+          for (int q = 0; q < 3; q++) { va[q] = u8f(a[q]); vc[q] = u8f(c[q]); }
         }
         const int64_t o = (int64_t)y * K.ow + x;
         if (!ALB_IN(y < K.oh && x + 1 < K.ow)) continue;
 #pragma unroll
-        for (int q = 0; q < 3; q++) {
-          __nv_bfloat162 v2;
-          v2.x = chain_normalize(va[q], K.k[q], K.m[q]);
-          v2.y = chain_normalize(vc[q], K.k[q], K.m[q]);
-          *reinterpret_cast<__nv_bfloat162*>(ob + q * plane + o) = v2;
-        }
+        for (int q = 0; q < 3; q++)   // both values rounded to bf16 by one packing conversion
+          *reinterpret_cast<__nv_bfloat162*>(ob + q * plane + o) =
+              __floats2bfloat162_rn(__fmaf_rn(va[q], K.k[q], K.m[q]), __fmaf_rn(vc[q], K.k[q], K.m[q]));
       }
     } else {
       const int32_t npx = (r1 - r0) * K.ow;
