@@ -140,17 +140,18 @@ ALB_D int jitter_op(int k, int i) {
 }
 
 ALB_D uint32_t sat_rne_f(float v) {
-  const float r = fminf(fmaxf(rintf(v), 0.0f), 255.0f);
-  return (uint32_t)r;
+  // clamping first and rounding after gives the same byte; adding 2^23 rounds
+  // half to even into the low bits (no float-to-integer conversion)
+  return __float_as_uint(fminf(fmaxf(v, 0.0f), 255.0f) + 8388608.0f) & 0xFFu;
 }
 
 // saturation of jitter mode 1: the float32 blend of chain_saturate, rounded to uint8
 ALB_D void jitter_saturate(uint32_t rgb[3], float s) {
-  const float r = (float)rgb[0], g = (float)rgb[1], b = (float)rgb[2];
-  const float grey = __fmaf_rn(0.114f, b, __fmaf_rn(0.587f, g, __fmul_rn(0.299f, r)));
+  const float f[3] = {u8f(rgb[0]), u8f(rgb[1]), u8f(rgb[2])};
+  const float grey = __fmaf_rn(0.114f, f[2], __fmaf_rn(0.587f, f[1], __fmul_rn(0.299f, f[0])));
   uint32_t o[3];
 #pragma unroll
-  for (int c = 0; c < 3; c++) o[c] = sat_rne_f(__fmaf_rn(s, __fsub_rn((float)rgb[c], grey), grey));
+  for (int c = 0; c < 3; c++) o[c] = sat_rne_f(__fmaf_rn(s, __fsub_rn(f[c], grey), grey));
   rgb[0] = o[0]; rgb[1] = o[1]; rgb[2] = o[2];
 }
 
@@ -477,18 +478,24 @@ __global__ void __launch_bounds__(1024, 1) k_chain_jitter_img(int32_t n, const a
     // ---- pass 1: ops before contrast, grey sum
     uint32_t acc = 0;        // at most 32 pairs of 2 * 255 per thread for images <= 256 x 256
     const int32_t npair = OH * hw;
+    const int32_t dyy = bs / hw, dxp = bs - dyy * hw;   // pair indices advanced without division
+    int32_t py = tid / hw, pxp = tid - py * hw;
     for (int32_t i = tid; i < npair; i += bs) {
-      const int32_t y = i / hw, x = 2 * (i - y * hw);
-      const int32_t yq = s_row[y];
-      uint8_t* d = s_img + 3 * ((int64_t)y * OW + x);
+      const int32_t y = py, x = 2 * pxp;
+      pxp += dxp; py += dyy;
+      if (pxp >= hw) { pxp -= hw; py++; }
+      const int32_t yq = s_row[y], iy = yq >> 5;
+      const uint8_t* ra = win + (int64_t)iy * im.row_stride;
+      const uint8_t* rb = win + (int64_t)imin(iy + 1, p.ch - 1) * im.row_stride;
+      uint8_t* d = s_img + 3 * (y * OW + x);
       uint32_t a[3];
-      chain_bilinear(win, im.row_stride, p.ch, p.cw, s_col[x], yq, a);
+      chain_bilerp(ra, rb, p.cw, s_col[x], yq & 31, a);
       jitter_ops(a, p.k, 0, pos_c, s_tb, s_tb, s);
       acc += grey_bt601(a);
       d[0] = (uint8_t)a[0]; d[1] = (uint8_t)a[1]; d[2] = (uint8_t)a[2];
       if (x + 1 < OW) {
         uint32_t c[3];
-        chain_bilinear(win, im.row_stride, p.ch, p.cw, s_col[x + 1], yq, c);
+        chain_bilerp(ra, rb, p.cw, s_col[x + 1], yq & 31, c);
         jitter_ops(c, p.k, 0, pos_c, s_tb, s_tb, s);
         acc += grey_bt601(c);
         d[3] = (uint8_t)c[0]; d[4] = (uint8_t)c[1]; d[5] = (uint8_t)c[2];
@@ -513,8 +520,11 @@ __global__ void __launch_bounds__(1024, 1) k_chain_jitter_img(int32_t n, const a
     __syncthreads();
     // ---- pass 2: the remaining ops, flip, Normalize, bf16 NCHW
     __nv_bfloat16* ob = out + (int64_t)b * 3 * plane;
+    py = tid / hw; pxp = tid - py * hw;
     for (int32_t i = tid; i < npair; i += bs) {
-      const int32_t y = i / hw, x = 2 * (i - y * hw);
+      const int32_t y = py, x = 2 * pxp;
+      pxp += dxp; py += dyy;
+      if (pxp >= hw) { pxp -= hw; py++; }
       const bool two = x + 1 < OW;
       const int32_t xa = p.flip ? OW - 1 - x : x, xb = p.flip ? OW - 2 - x : x + 1;   // resized columns shown
       const uint8_t* sa = s_img + 3 * ((int64_t)y * OW + xa);
@@ -528,12 +538,9 @@ __global__ void __launch_bounds__(1024, 1) k_chain_jitter_img(int32_t n, const a
         jitter_ops(c, p.k, pos_c, 3, s_tb, s_tc, s);
         if (pairs) {
 #pragma unroll
-          for (int q = 0; q < 3; q++) {
-            __nv_bfloat162 v2;
-            v2.x = chain_normalize((float)a[q], K.k[q], K.m[q]);
-            v2.y = chain_normalize((float)c[q], K.k[q], K.m[q]);
-            *reinterpret_cast<__nv_bfloat162*>(ob + q * plane + o) = v2;
-          }
+          for (int q = 0; q < 3; q++)
+            *reinterpret_cast<__nv_bfloat162*>(ob + q * plane + o) =
+                __floats2bfloat162_rn(__fmaf_rn(u8f(a[q]), K.k[q], K.m[q]), __fmaf_rn(u8f(c[q]), K.k[q], K.m[q]));
         } else {
 #pragma unroll
           for (int q = 0; q < 3; q++) {
