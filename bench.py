@@ -42,7 +42,7 @@ UNIT = "images/s"
 # suite workload (same H, W distribution), scaled per image; the roofline's
 # traffic figure is this times the images of one launch.  Only kernels whose
 # code is unchanged since that capture are listed.
-NCU_DRAM_BYTES_PER_IMAGE = {"ShiftHSV": 850022.0, "PadToSize512": 1172000.0}
+NCU_DRAM_BYTES_PER_IMAGE = {"Rotate": 1048317.0, "PadToSize512": 1172000.0}
 SUITE_N, SUITE_LO, SUITE_HI = 2000, 333, 500
 FUSED_N, FUSED_LO, FUSED_HI = 4096, 256, 1024
 DET_N, DET_HW = 256, 1024
@@ -367,7 +367,7 @@ def chain_read_bytes(params, shapes, offsets, out_h=224, out_w=224, mask_planes=
 
 
 # ------------------------------------------------------------------ sub-workloads
-def fused_pipeline(dev, stream, steps=3, warmup=2, n=FUSED_N):
+def fused_pipeline(dev, stream, steps=3, warmup=2, n=FUSED_N, schedule=None):
     from paper_1809_06839_gb300 import alb as A, synth
     from paper_1809_06839_gb300.ragged import DeviceBatch
     FUSED_N = n
@@ -393,8 +393,12 @@ def fused_pipeline(dev, stream, steps=3, warmup=2, n=FUSED_N):
 
     # schedule chosen by the library's autotuner on this batch (outside the
     # timed region); ccfg keeps zero fields, so the fused runs use the cached pick
-    best = A.alb_autotune_batch(ccfg, FUSED_N, pdev, din.dev, out, wsf, reps=3, stream=stream)
-    res = {"schedule": {"rows_per_item": best.tile_h, "ctas_per_sm": best.ctas_per_sm, "by": "alb_autotune_batch"}}
+    if schedule:     # a fixed schedule (profiling runs): no autotuner launches before the measured ones
+        ccfg = A.chain_cfg(tile_h=schedule[0], ctas_per_sm=schedule[1])
+        res = {"schedule": {"rows_per_item": schedule[0], "ctas_per_sm": schedule[1], "by": "--fused-schedule"}}
+    else:
+        best = A.alb_autotune_batch(ccfg, FUSED_N, pdev, din.dev, out, wsf, reps=3, stream=stream)
+        res = {"schedule": {"rows_per_item": best.tile_h, "ctas_per_sm": best.ctas_per_sm, "by": "alb_autotune_batch"}}
     # the schedule cache persisted to JSON and read back (the next process can
     # start from it with alb_autotune_load)
     cache = os.path.join(ROOT, "paper_1809_06839_gb300", "_build", "autotune.json")
@@ -863,6 +867,8 @@ def main():
     ap.add_argument("--fused-n", type=int, default=FUSED_N, help="images of the fused workload (profiling runs)")
     ap.add_argument("--diff-b", type=int, default=DIFF_B, help="batch of the differentiable workload (profiling runs)")
     ap.add_argument("--large-n", type=int, default=LARGE_N, help="images of the 512-1024 px leg (profiling runs)")
+    ap.add_argument("--fused-schedule", default="", help="rows per item,CTAs per SM of the fused kernel instead of "
+                    "the autotuner's pick (profiling runs)")
     args = ap.parse_args()
     ws, rank, local, dist = dist_setup(args)
     if args.impl == "reference":
@@ -915,7 +921,8 @@ def main():
         torch.cuda.empty_cache()
         which = set(args.extras.split(","))
         if "fused" in which:
-            extra["fused_pipeline"] = fused_pipeline(dev, stream, n=args.fused_n)
+            sched = tuple(int(v) for v in args.fused_schedule.split(",")) if args.fused_schedule else None
+            extra["fused_pipeline"] = fused_pipeline(dev, stream, n=args.fused_n, schedule=sched)
         if "detection" in which:
             extra["detection"] = detection(dev, stream)
         if "differentiable" in which:
