@@ -167,8 +167,9 @@ ALB_D int warp_units(int tiles, int groups) {
 }
 
 // forward: grid (CTAs per image, B); each CTA sets up its image's map once
-// and runs the unit pipeline
-template <bool AL>
+// and runs the unit pipeline.  F3: every channel group is full (C a multiple
+// of three), so no channel test is left in the loops.
+template <bool AL, bool F3>
 __global__ void __launch_bounds__(kWT_THREADS) k_warp_f32_fwd(int B, int C, int H, int W, int tiles_x, int tiles,
                                                               const float* __restrict__ x,
                                                               const float* __restrict__ prm, float* __restrict__ y) {
@@ -190,21 +191,22 @@ __global__ void __launch_bounds__(kWT_THREADS) k_warp_f32_fwd(int B, int C, int 
   if (units > 0) {
     int X0, Y0, c0;
     warp_unit(0, groups, tiles_x, rtx, X0, Y0, c0);
-    nb = warp_fwd_box<AL>(g, X0, Y0, H, W, min(C - c0, kWT_CG));
-    if (nb.staged) warp_stage_async<AL>(sm, xb + (int64_t)c0 * plane, min(C - c0, kWT_CG), H, W, nb);
+    const int cn0 = F3 ? kWT_CG : min(C - c0, kWT_CG);
+    nb = warp_fwd_box<AL>(g, X0, Y0, H, W, cn0);
+    if (nb.staged) warp_stage_async<AL>(sm, xb + (int64_t)c0 * plane, cn0, H, W, nb);
   }
   cp_async_commit_f();
   for (int u = 0; u < units; u++) {
     const WarpBox bx = nb;
     int ox0, oy0, c0;
     warp_unit(u, groups, tiles_x, rtx, ox0, oy0, c0);
-    const int cn = min(C - c0, kWT_CG);
+    const int cn = F3 ? kWT_CG : min(C - c0, kWT_CG);
     if (u + 1 < units) {
       int X1, Y1, c1;
       warp_unit(u + 1, groups, tiles_x, rtx, X1, Y1, c1);
-      nb = warp_fwd_box<AL>(g, X1, Y1, H, W, min(C - c1, kWT_CG));
-      if (nb.staged)
-        warp_stage_async<AL>(sm + ((u + 1) & 1) * kWT_BUF, xb + (int64_t)c1 * plane, min(C - c1, kWT_CG), H, W, nb);
+      const int cn1 = F3 ? kWT_CG : min(C - c1, kWT_CG);
+      nb = warp_fwd_box<AL>(g, X1, Y1, H, W, cn1);
+      if (nb.staged) warp_stage_async<AL>(sm + ((u + 1) & 1) * kWT_BUF, xb + (int64_t)c1 * plane, cn1, H, W, nb);
     }
     cp_async_commit_f();
     cp_async_wait_prev();
@@ -229,7 +231,7 @@ __global__ void __launch_bounds__(kWT_THREADS) k_warp_f32_fwd(int B, int C, int 
         const int s0 = ly * bp + lx;
 #pragma unroll
         for (int k = 0; k < kWT_CG; k++) {
-          if (k < cn && ALB_IN(k * bpl + s0 + bp + 1 < kWT_BUF && s0 >= 0)) {
+          if ((F3 || k < cn) && ALB_IN(k * bpl + s0 + bp + 1 < kWT_BUF && s0 >= 0)) {
             const float* s = buf + k * bpl + s0;
             dstp[k * plane + o] = w00 * s[0] + w10 * s[1] + w01 * s[bp] + w11 * s[bp + 1];
           }
@@ -317,7 +319,7 @@ struct GatherK {
 // into dL/dsx, dL/dsy before the eight parameter sums S.  G: the gradient rows
 // (staged box: `gp` row pitch, `gpl` channel pitch, rows and columns relative
 // to (oxb, oyb); or the image itself).
-template <typename GPtr>
+template <bool F3, typename GPtr>
 ALB_D void warp_gather_pair(const GatherK& K, const WarpBox& bx, GPtr G, int gp, int gpl, int oxb, int oyb,
                             int px, int py, int cn, bool has1, const float (&xa)[kWT_CG], const float (&xc)[kWT_CG],
                             float (&acc0)[kWT_CG], float (&acc1)[kWT_CG], float (&S)[8]) {
@@ -352,7 +354,7 @@ ALB_D void warp_gather_pair(const GatherK& K, const WarpBox& bx, GPtr G, int gp,
       float a0 = 0.0f, a1 = 0.0f;
 #pragma unroll
       for (int k = 0; k < kWT_CG; k++) {
-        if (k < cn) {
+        if (F3 || k < cn) {
           const float gv = G[k * gpl + rowoff + ox];
           if (h0) {
             acc0[k] = __fmaf_rn(gv, w0, acc0[k]);
@@ -394,7 +396,8 @@ ALB_D void warp_gather_pair(const GatherK& K, const WarpBox& bx, GPtr G, int gp,
 // same pairs carry the parameter gradient: pair (p, q) adds g_q x_p times the
 // weight's derivative to dL/dsx_q, dL/dsy_q, and those are folded against the
 // coordinate's derivatives through eight running sums per thread.
-template <bool AL>
+// F3: every channel group is full (C a multiple of three).
+template <bool AL, bool F3>
 __global__ void __launch_bounds__(kWT_THREADS, 4) k_warp_f32_bwd(int B, int C, int H, int W, int tiles_x, int tiles,
                                                               const float* __restrict__ x,
                                                               const float* __restrict__ prm,
@@ -445,21 +448,22 @@ __global__ void __launch_bounds__(kWT_THREADS, 4) k_warp_f32_bwd(int B, int C, i
   if (units > 0) {
     int X0, Y0, c0;
     warp_unit(0, groups, tiles_x, rtx, X0, Y0, c0);
-    nb = warp_bwd_box<AL>(g, M, finite, X0, Y0, H, W, min(C - c0, kWT_CG));
-    if (nb.staged) warp_stage_async<AL>(sm, gyb + (int64_t)c0 * plane, min(C - c0, kWT_CG), H, W, nb);
+    const int cn0 = F3 ? kWT_CG : min(C - c0, kWT_CG);
+    nb = warp_bwd_box<AL>(g, M, finite, X0, Y0, H, W, cn0);
+    if (nb.staged) warp_stage_async<AL>(sm, gyb + (int64_t)c0 * plane, cn0, H, W, nb);
   }
   cp_async_commit_f();
   for (int u = 0; u < units; u++) {
     const WarpBox bx = nb;
     int X0, Y0, c0;
     warp_unit(u, groups, tiles_x, rtx, X0, Y0, c0);
-    const int cn = min(C - c0, kWT_CG);
+    const int cn = F3 ? kWT_CG : min(C - c0, kWT_CG);
     if (u + 1 < units) {
       int X1, Y1, c1;
       warp_unit(u + 1, groups, tiles_x, rtx, X1, Y1, c1);
-      nb = warp_bwd_box<AL>(g, M, finite, X1, Y1, H, W, min(C - c1, kWT_CG));
-      if (nb.staged)
-        warp_stage_async<AL>(sm + ((u + 1) & 1) * kWT_BUF, gyb + (int64_t)c1 * plane, min(C - c1, kWT_CG), H, W, nb);
+      const int cn1 = F3 ? kWT_CG : min(C - c1, kWT_CG);
+      nb = warp_bwd_box<AL>(g, M, finite, X1, Y1, H, W, cn1);
+      if (nb.staged) warp_stage_async<AL>(sm + ((u + 1) & 1) * kWT_BUF, gyb + (int64_t)c1 * plane, cn1, H, W, nb);
     }
     cp_async_commit_f();
     // this unit's source values, loaded while its copies land: each thread
@@ -471,8 +475,8 @@ __global__ void __launch_bounds__(kWT_THREADS, 4) k_warp_f32_bwd(int B, int C, i
       const int o = in0 ? py * W + px : 0;
 #pragma unroll
       for (int k = 0; k < kWT_CG; k++) {
-        xa[k] = (in0 && k < cn) ? __ldg(xb + (int64_t)(c0 + k) * plane + o) : 0.0f;
-        xc[k] = (has1 && k < cn) ? __ldg(xb + (int64_t)(c0 + k) * plane + o + 1) : 0.0f;
+        xa[k] = (in0 && (F3 || k < cn)) ? __ldg(xb + (int64_t)(c0 + k) * plane + o) : 0.0f;
+        xc[k] = (has1 && (F3 || k < cn)) ? __ldg(xb + (int64_t)(c0 + k) * plane + o + 1) : 0.0f;
       }
     }
     cp_async_wait_prev();
@@ -485,15 +489,15 @@ __global__ void __launch_bounds__(kWT_THREADS, 4) k_warp_f32_bwd(int B, int C, i
       for (int k = 0; k < kWT_CG; k++) acc0[k] = acc1[k] = finite ? 0.0f : __int_as_float(0x7fc00000);
       if (finite && bx.x1 >= bx.x0) {
         if (bx.staged)
-          warp_gather_pair(K, bx, buf, bx.pitch, bh * bx.pitch, bx.x0, bx.y0, px, py, cn, has1, xa, xc, acc0, acc1,
+          warp_gather_pair<F3>(K, bx, buf, bx.pitch, bh * bx.pitch, bx.x0, bx.y0, px, py, cn, has1, xa, xc, acc0, acc1,
                            S);
         else
-          warp_gather_pair(K, bx, gyb + (int64_t)c0 * plane, W, plane, 0, 0, px, py, cn, has1, xa, xc, acc0, acc1, S);
+          warp_gather_pair<F3>(K, bx, gyb + (int64_t)c0 * plane, W, plane, 0, 0, px, py, cn, has1, xa, xc, acc0, acc1, S);
       }
       const int o = py * W + px;
 #pragma unroll
       for (int k = 0; k < kWT_CG; k++) {
-        if (k < cn) {
+        if (F3 || k < cn) {
           gxb[(int64_t)(c0 + k) * plane + o] = acc0[k];
           if (has1) gxb[(int64_t)(c0 + k) * plane + o + 1] = acc1[k];
         }
@@ -645,8 +649,10 @@ static alb_status warp_smem_optin() {
   ALB_CUDA(cudaGetDevice(&dev));
   if (dev >= 0 && dev < 64 && done[dev]) return ALB_OK;
   const int bytes = 2 * kWT_BUF * (int)sizeof(float);
-  const void* kernels[4] = {(const void*)k_warp_f32_fwd<true>, (const void*)k_warp_f32_fwd<false>,
-                            (const void*)k_warp_f32_bwd<true>, (const void*)k_warp_f32_bwd<false>};
+  const void* kernels[8] = {(const void*)k_warp_f32_fwd<true, true>,  (const void*)k_warp_f32_fwd<true, false>,
+                            (const void*)k_warp_f32_fwd<false, true>, (const void*)k_warp_f32_fwd<false, false>,
+                            (const void*)k_warp_f32_bwd<true, true>,  (const void*)k_warp_f32_bwd<true, false>,
+                            (const void*)k_warp_f32_bwd<false, true>, (const void*)k_warp_f32_bwd<false, false>};
   for (const void* k : kernels) ALB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
   if (dev >= 0 && dev < 64) done[dev] = true;
   return ALB_OK;
@@ -718,15 +724,13 @@ extern "C" alb_status alb_warp_affine_f32_fwd(int32_t B, int32_t C, int32_t H, i
   if (rc != ALB_OK) return rc;
   const int tiles_x = (W + kWT_W - 1) / kWT_W, tiles_y = (H + kWT_H - 1) / kWT_H;
   const int tiles = tiles_x * tiles_y;
-  const bool al = warp_aligned(W, x);
-  const void* kern = al ? (const void*)k_warp_f32_fwd<true> : (const void*)k_warp_f32_fwd<false>;
-  const int nblk = warp_ctas_per_image(kern, tiles, B);
-  const dim3 grid(nblk, B);
-  const size_t smem = 2 * kWT_BUF * sizeof(float);
-  if (al)
-    k_warp_f32_fwd<true><<<grid, kWT_THREADS, smem, (cudaStream_t)stream>>>(B, C, H, W, tiles_x, tiles, x, prm, y);
-  else
-    k_warp_f32_fwd<false><<<grid, kWT_THREADS, smem, (cudaStream_t)stream>>>(B, C, H, W, tiles_x, tiles, x, prm, y);
+  const bool al = warp_aligned(W, x), f3 = C % kWT_CG == 0;
+  void (*kern)(int, int, int, int, int, int, const float*, const float*, float*) =
+      al ? (f3 ? k_warp_f32_fwd<true, true> : k_warp_f32_fwd<true, false>)
+         : (f3 ? k_warp_f32_fwd<false, true> : k_warp_f32_fwd<false, false>);
+  const int nblk = warp_ctas_per_image((const void*)kern, tiles, B);
+  kern<<<dim3(nblk, B), kWT_THREADS, 2 * kWT_BUF * sizeof(float), (cudaStream_t)stream>>>(B, C, H, W, tiles_x, tiles,
+                                                                                        x, prm, y);
   ALB_CUDA(cudaGetLastError());
   return ALB_OK;
 }
@@ -743,20 +747,16 @@ extern "C" alb_status alb_warp_affine_f32_bwd(int32_t B, int32_t C, int32_t H, i
   if (rc != ALB_OK) return rc;
   const int tiles_x = (W + kWT_W - 1) / kWT_W, tiles_y = (H + kWT_H - 1) / kWT_H;
   const int tiles = tiles_x * tiles_y;
-  const bool al = warp_aligned(W, gy);
-  const void* kern = al ? (const void*)k_warp_f32_bwd<true> : (const void*)k_warp_f32_bwd<false>;
-  const int nblk = warp_ctas_per_image(kern, tiles, B);
+  const bool al = warp_aligned(W, gy), f3 = C % kWT_CG == 0;
+  void (*kern)(int, int, int, int, int, int, const float*, const float*, const float*, float*, float*) =
+      al ? (f3 ? k_warp_f32_bwd<true, true> : k_warp_f32_bwd<true, false>)
+         : (f3 ? k_warp_f32_bwd<false, true> : k_warp_f32_bwd<false, false>);
+  const int nblk = warp_ctas_per_image((const void*)kern, tiles, B);
   ALB_REQUIRE(workspace && workspace_bytes >= (size_t)B * nblk * 4 * sizeof(float), ALB_EWORKSPACE,
               "alb_warp_affine_f32_bwd: workspace too small");
   cudaStream_t st = (cudaStream_t)stream;
-  const dim3 grid(nblk, B);
-  const size_t smem = 2 * kWT_BUF * sizeof(float);
-  if (al)
-    k_warp_f32_bwd<true><<<grid, kWT_THREADS, smem, st>>>(B, C, H, W, tiles_x, tiles, x, prm, gy, gx,
-                                                          (float*)workspace);
-  else
-    k_warp_f32_bwd<false><<<grid, kWT_THREADS, smem, st>>>(B, C, H, W, tiles_x, tiles, x, prm, gy, gx,
-                                                           (float*)workspace);
+  kern<<<dim3(nblk, B), kWT_THREADS, 2 * kWT_BUF * sizeof(float), st>>>(B, C, H, W, tiles_x, tiles, x, prm, gy, gx,
+                                                                      (float*)workspace);
   ALB_CUDA(cudaGetLastError());
   k_reduce_partials<<<B, 256, 0, st>>>(nblk, 4, (const float*)workspace, gprm);
   ALB_CUDA(cudaGetLastError());
