@@ -211,12 +211,15 @@ __global__ void __launch_bounds__(256) k_lut_bulk(Plan plan, ImgList in, ImgList
   if (tid == 0) bulk_wait_all();
 }
 
-// Per-channel histograms through the bulk-copy stages (read only): per-warp
-// shared copies, merged into the image's global histogram at the end of each
-// run (one image per run).
+// Per-channel histograms through the bulk-copy stages (read only): one shared
+// histogram per CTA held as 8 interleaved copies, word (256 c + v) * 8 +
+// (lane & 7), merged into the image's global histogram at the end of each run
+// (one image per run).  A lane's word lies in bank 8 (v mod 4) + (lane & 7),
+// so at most the 4 lanes of one residue class of lane & 7 can meet in a bank,
+// where per-warp copies let all 32 lanes collide at random.
 struct HistBulkSmem {
   uint8_t stage[kBulkStages][kBulkChunk];
-  uint32_t sh[8][768];
+  uint32_t sh[768 * 8];
   uint64_t full[kBulkStages];
 };
 
@@ -225,8 +228,9 @@ __global__ void __launch_bounds__(256) k_hist_bulk(Plan plan, ImgList in, uint32
   extern __shared__ __align__(128) uint8_t hist_dyn[];
   HistBulkSmem& sm = *reinterpret_cast<HistBulkSmem*>(hist_dyn);
   const int tid = threadIdx.x, bs = blockDim.x;
-  uint32_t* my = sm.sh[tid >> 5];
-  for (int i = tid; i < 8 * 768; i += bs) (&sm.sh[0][0])[i] = 0;
+  // bin (256 c + v) of this lane's copy: my[8 * bin]
+  uint32_t* my = sm.sh + (tid & 7);
+  for (int i = tid; i < 8 * 768; i += bs) sm.sh[i] = 0;
   if (tid == 0) {
     for (int i = 0; i < kBulkStages; i++) mbar_init(&sm.full[i], 1);
     mbar_init_fence();
@@ -243,8 +247,8 @@ __global__ void __launch_bounds__(256) k_hist_bulk(Plan plan, ImgList in, uint32
       int64_t A, E;
       const int64_t S0 = 3 * (int64_t)r0 * si.w, E0 = 3 * (int64_t)r1 * si.w;
       aligned_core(S0, E0, A, E);
-      for (int64_t q = S0 + tid; q < A; q += bs) atomicAdd(&my[256 * (int)(q % 3) + ip[q]], 1u);
-      for (int64_t q = E + tid; q < E0; q += bs) atomicAdd(&my[256 * (int)(q % 3) + ip[q]], 1u);
+      for (int64_t q = S0 + tid; q < A; q += bs) atomicAdd(&my[8 * (256 * (int)(q % 3) + ip[q])], 1u);
+      for (int64_t q = E + tid; q < E0; q += bs) atomicAdd(&my[8 * (256 * (int)(q % 3) + ip[q])], 1u);
       const int phi = (int)(A % 3);
       dead = !bulk_pipeline(sm.stage, sm.full, seq, ip + A, nullptr, E - A, status,
                             [&](uint8_t* sb, int nbytes, int64_t) {
@@ -252,14 +256,14 @@ __global__ void __launch_bounds__(256) k_hist_bulk(Plan plan, ImgList in, uint32
         for (int v = tid; v < nv; v += bs) {
           const uint4 x = *reinterpret_cast<const uint4*>(sb + 16 * v);
           const int rho = (phi + v) % 3;
-          uint32_t* h0 = my + 256 * rho;
-          uint32_t* h1 = my + 256 * (rho == 2 ? 0 : rho + 1);
-          uint32_t* h2 = my + 256 * (rho == 0 ? 2 : rho - 1);
+          uint32_t* h0 = my + 2048 * rho;
+          uint32_t* h1 = my + 2048 * (rho == 2 ? 0 : rho + 1);
+          uint32_t* h2 = my + 2048 * (rho == 0 ? 2 : rho - 1);
           const uint32_t w[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
           for (int k = 0; k < 16; k++) {
             uint32_t* hb = k % 3 == 0 ? h0 : (k % 3 == 1 ? h1 : h2);
-            atomicAdd(&hb[(w[k >> 2] >> (8 * (k & 3))) & 0xFFu], 1u);
+            atomicAdd(&hb[8 * ((w[k >> 2] >> (8 * (k & 3))) & 0xFFu)], 1u);
           }
         }
       });
@@ -270,14 +274,14 @@ __global__ void __launch_bounds__(256) k_hist_bulk(Plan plan, ImgList in, uint32
         const int32_t y = r0 + (int32_t)(i / si.w), x = (int32_t)(i % si.w);
         const uint8_t* s = ip + (int64_t)y * si.row_stride + 3 * (int64_t)x;
 #pragma unroll
-        for (int c = 0; c < 3; c++) atomicAdd(&my[256 * c + s[c]], 1u);
+        for (int c = 0; c < 3; c++) atomicAdd(&my[8 * (256 * c + s[c])], 1u);
       }
     }
     __syncthreads();
     for (int i = tid; i < 768; i += bs) {
       uint32_t sum = 0;
 #pragma unroll
-      for (int w = 0; w < 8; w++) { sum += sm.sh[w][i]; sm.sh[w][i] = 0; }
+      for (int w = 0; w < 8; w++) { sum += sm.sh[8 * i + w]; sm.sh[8 * i + w] = 0; }
       if (sum) atomicAdd(&hist[(int64_t)b * 768 + i], sum);
     }
     __syncthreads();
