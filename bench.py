@@ -80,8 +80,9 @@ def launches_per_op(tid):
         return 1 + 2
     if tid == A.EQUALIZE:
         return 1 + 3          # plan, histogram, tables, apply (the memset is a copy-engine op)
-    if tid in (A.ROTATE, A.SHIFT_SCALE_ROTATE, A.RESIZE, A.RANDOM_SIZED_CROP, A.RANDOM_RESIZED_CROP,
-               A.GRID_DISTORTION, A.ELASTIC):
+    if tid in (A.RESIZE, A.RANDOM_SIZED_CROP, A.RANDOM_RESIZED_CROP):
+        return 1 + 6          # row plan, and a tile plan and a tile kernel per scale class (three)
+    if tid in (A.ROTATE, A.SHIFT_SCALE_ROTATE, A.GRID_DISTORTION, A.ELASTIC):
         return 1 + 2          # row plan, tile plan, tile kernel
     return 1 + 1
 

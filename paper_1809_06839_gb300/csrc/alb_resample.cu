@@ -57,12 +57,15 @@ __global__ void k_plan_tiles(ImgList out, int32_t n, int32_t tile_w, int32_t til
       if (plan_filtered_out(chk, im)) cnt = 0;
       if (chk.reduce != 0 && cnt) {
         const alb_params& pr = chk.prm.get(i);
-        // reductions past 17/16 on an axis whose 32 x 16 tiles fit the 68 x 36 box
-        // (31 f + 2 <= 67 columns, 15 f + 2 <= 35 rows); stronger ones keep the
-        // 32 x 32 tiles, which read global memory either way
-        const bool red = (16 * (int64_t)pr.cw > 17 * (int64_t)im.w || 16 * (int64_t)pr.ch > 17 * (int64_t)im.h) &&
-                         100 * (int64_t)pr.cw <= 209 * (int64_t)im.w && 10 * (int64_t)pr.ch <= 22 * (int64_t)im.h;
-        if (red != (chk.reduce > 0)) cnt = 0;
+        // class 2: windows within 17/16 of the output on both axes (64 x 32
+        // tiles fit the 72 x 36 box: 63 f + 2 <= 71 columns, 31 f + 2 <= 35 rows);
+        // class 1: reductions past 17/16 whose 32 x 16 tiles fit the 68 x 36 box
+        // (31 f + 2 <= 67 columns, 15 f + 2 <= 35 rows); class 3: stronger
+        // reductions, whose 32 x 32 tiles read global memory
+        const bool past = 16 * (int64_t)pr.cw > 17 * (int64_t)im.w || 16 * (int64_t)pr.ch > 17 * (int64_t)im.h;
+        const bool fits = 100 * (int64_t)pr.cw <= 209 * (int64_t)im.w && 10 * (int64_t)pr.ch <= 22 * (int64_t)im.h;
+        const int32_t cls = !past ? 2 : (fits ? 1 : 3);
+        if (cls != chk.reduce) cnt = 0;
       }
     }
     int32_t v = cnt;
@@ -465,9 +468,12 @@ __global__ void __launch_bounds__(32 * NWARP, 5) k_resample_warp(Plan plan, ImgL
 // box (reductions by up to ~2, routed there per image).
 template <int S>
 struct RShape {
-  static constexpr int TW = 32, TH = S ? 16 : 32;         // output tile (columns x rows)
-  static constexpr int BX = S ? 68 : 36, BY = 36;         // staged box (source pixels x rows)
-  static constexpr int PITCH = S ? 240 : 144;             // staged row pitch in bytes
+  // S = 0: windows within 17/16 of the output; 1: reductions up to ~2x;
+  // 2: the rest (and every image when there is no second plan)
+  static constexpr int TW = S == 0 ? 64 : 32, TH = S == 1 ? 16 : 32;   // output tile (columns x rows)
+  static constexpr int NC = TW / 32;                      // output columns per lane: lane, lane + 32
+  static constexpr int BX = S == 0 ? 72 : (S == 1 ? 68 : 36), BY = 36;   // staged box (source pixels x rows)
+  static constexpr int PITCH = S == 2 ? 144 : 240;        // staged row pitch in bytes
   static_assert(PITCH % 16 == 0, "cp.async destinations must be 16-byte aligned");
   static_assert(PITCH >= 15 + 3 * (BX - 1) + 12, "a tap read (3 words from the pair's word) stays in its row");
   static_assert(BY >= TH + 1 && BX >= TW + 2, "the box holds an unscaled tile");
@@ -503,25 +509,33 @@ ALB_D void r_load_img(const Plan& plan, const ImgList& in, const ImgList& out, c
   k.sstride = si.row_stride; k.dstride = so.row_stride;
 }
 
-// Tile geometry; per lane: vcol = Q5 coordinate of tile column `lane`,
-// vrow = that of tile row `lane` (lanes < TH), both clamped to the tile.
+// Tile geometry; per lane: vcol[c] = Q5 coordinate of tile column
+// lane + 32 c, vrow = that of tile row `lane` (lanes < TH), both clamped to
+// the tile.
 template <int MAP, int S>
-ALB_D void r_tile_geo(const RImg& k, const PrmList& prm, int32_t item, int lane, RTile& g, int32_t& vcol,
-                      int32_t& vrow) {
+ALB_D void r_tile_geo(const RImg& k, const PrmList& prm, int32_t item, int lane, RTile& g,
+                      int32_t (&vcol)[RShape<S>::NC], int32_t& vrow) {
   using SH = RShape<S>;
   const int32_t t = item - k.prefix, ty = t / k.tiles_x, tx = t - ty * k.tiles_x;
   g.ox0 = tx * SH::TW; g.oy0 = ty * SH::TH;
   g.tw = imin(SH::TW, k.OW - g.ox0); g.th = imin(SH::TH, k.OH - g.oy0);
-  const int32_t cx = g.ox0 + imin(lane, g.tw - 1), ry = g.oy0 + imin(lane & (SH::TH - 1), g.th - 1);
+  const int32_t ry = g.oy0 + imin(lane & (SH::TH - 1), g.th - 1);
   if (MAP == MAP_GRID) {
     const alb_params& p = prm.get(k.b);            // the cell factors stay in the record
-    vcol = p.apply ? grid_q5(p.q, p.k, 0, cx, k.cw) : 32 * cx;
+#pragma unroll
+    for (int c = 0; c < SH::NC; c++) {
+      const int32_t cx = g.ox0 + imin(lane + 32 * c, g.tw - 1);
+      vcol[c] = p.apply ? grid_q5(p.q, p.k, 0, cx, k.cw) : 32 * cx;
+    }
     vrow = p.apply ? grid_q5(p.q, p.k, 1, ry, k.ch) : 32 * ry;
   } else {
-    vcol = rs_q5(cx, k.cw, k.OW);
+#pragma unroll
+    for (int c = 0; c < SH::NC; c++) vcol[c] = rs_q5(g.ox0 + imin(lane + 32 * c, g.tw - 1), k.cw, k.OW);
     vrow = rs_q5(ry, k.ch, k.OH);
   }
-  const int32_t c0 = __shfl_sync(0xffffffffu, vcol, 0), c1 = __shfl_sync(0xffffffffu, vcol, g.tw - 1);
+  const int32_t last = g.tw - 1;
+  const int32_t vl = (SH::NC > 1 && last >= 32) ? vcol[SH::NC - 1] : vcol[0];
+  const int32_t c0 = __shfl_sync(0xffffffffu, vcol[0], 0), c1 = __shfl_sync(0xffffffffu, vl, last & 31);
   const int32_t r0 = __shfl_sync(0xffffffffu, vrow, 0), r1 = __shfl_sync(0xffffffffu, vrow, g.th - 1);
   g.bx0 = c0 >> 5; g.by0 = r0 >> 5;
   g.bw = imin((c1 >> 5) + 1, k.cw - 1) - g.bx0 + 1;
@@ -568,20 +582,47 @@ ALB_D void r_vert_store(const uint32_t (&ha)[3], const uint32_t (&hb)[3], uint32
   if (store) { od[0] = (uint8_t)r; od[1] = (uint8_t)g; od[2] = (uint8_t)b; }
 }
 
-ALB_D void r_tile_compute(const RImg& k, const RTile& g, int lane, int32_t vcol, int32_t vrow,
+// NC output columns per lane (lane, lane + 32): the per-row work that does not
+// depend on the column (the row's Q5 coordinate, its box row offset, the
+// advance test) is shared by the lane's columns.
+template <int NC>
+ALB_D void r_tile_compute(const RImg& k, const RTile& g, int lane, const int32_t (&vcol)[NC], int32_t vrow,
                           const uint8_t* __restrict__ box, const int32_t* __restrict__ rowoff) {
-  const int32_t fx = vcol & 31;
-  const uint32_t wx = (uint32_t)(32 + 255 * fx);       // (32 - fx) | fx << 8
-  const bool store = lane < g.tw;
+  uint32_t wx[NC];
+  bool store[NC];
+#pragma unroll
+  for (int c = 0; c < NC; c++) {
+    wx[c] = (uint32_t)(32 + 255 * (vcol[c] & 31));    // (32 - fx) | fx << 8
+    store[c] = lane + 32 * c < g.tw;
+  }
   uint8_t* od = k.dst + (int64_t)g.oy0 * k.dstride + 3 * (int64_t)(g.ox0 + lane);
-  uint32_t ha[3] = {0u, 0u, 0u}, hb[3] = {0u, 0u, 0u};
+  uint32_t ha[NC][3], hb[NC][3];
+#pragma unroll
+  for (int c = 0; c < NC; c++)
+#pragma unroll
+    for (int j = 0; j < 3; j++) ha[c][j] = hb[c][j] = 0u;
   int32_t ia = -2;                                   // box row whose h is in ha (hb: the row below)
+  auto vert = [&](int r, int32_t fy) {
+    const uint32_t wy = (uint32_t)(32 + 255 * fy);
+#pragma unroll
+    for (int c = 0; c < NC; c++)
+      r_vert_store(ha[c], hb[c], wy, store[c] && ALB_IN(g.oy0 + r < k.OH && g.ox0 + lane + 32 * c < k.OW),
+                   od + 96 * c);
+  };
   if (!g.big) {
-    const int32_t ocol = 3 * ((vcol >> 5) - g.bx0);
-    auto hrow = [&](int32_t i, uint32_t (&h)[3]) {
-      uint32_t lo = 0u, hi = 0u;
-      if (ALB_IN(i >= 0 && i < g.bh && ocol >= 0 && ocol < 3 * g.bw)) taps_row(box, rowoff[i] + ocol, lo, hi);
-      r_hrow(lo, hi, wx, h);
+    int32_t ocol[NC];
+#pragma unroll
+    for (int c = 0; c < NC; c++) ocol[c] = 3 * ((vcol[c] >> 5) - g.bx0);
+    // h of box row i for every column of the lane (one row offset load)
+    auto hrow = [&](int32_t i, uint32_t (&h)[NC][3]) {
+      const bool iok = ALB_IN(i >= 0 && i < g.bh);
+      const int32_t ro = iok ? rowoff[i] : 0;
+#pragma unroll
+      for (int c = 0; c < NC; c++) {
+        uint32_t lo = 0u, hi = 0u;
+        if (iok && ALB_IN(ocol[c] >= 0 && ocol[c] < 3 * g.bw)) taps_row(box, ro + ocol[c], lo, hi);
+        r_hrow(lo, hi, wx[c], h[c]);
+      }
     };
     // at a clamped bottom edge the row below the last tap row is not staged
     // and has weight fy = 0: the last staged row stands in for it
@@ -599,13 +640,18 @@ ALB_D void r_tile_compute(const RImg& k, const RTile& g, int lane, int32_t vcol,
       for (int r = 0; r < g.th; r++, od += k.dstride) {
         const int32_t rq = __shfl_sync(0xffffffffu, vrow, r);
         const int32_t iy = (rq >> 5) - g.by0, fy = rq & 31;
-        uint32_t hn[3];
+        uint32_t hn[NC][3];
         hrow(imin(iy + 1, last), hn);
         const bool adv = iy != ia;
-        ha[0] = adv ? hb[0] : ha[0]; ha[1] = adv ? hb[1] : ha[1]; ha[2] = adv ? hb[2] : ha[2];
-        hb[0] = hn[0]; hb[1] = hn[1]; hb[2] = hn[2];
+#pragma unroll
+        for (int c = 0; c < NC; c++)
+#pragma unroll
+          for (int j = 0; j < 3; j++) {
+            ha[c][j] = adv ? hb[c][j] : ha[c][j];
+            hb[c][j] = hn[c][j];
+          }
         ia = iy;
-        r_vert_store(ha, hb, (uint32_t)(32 + 255 * fy), store && ALB_IN(g.oy0 + r < k.OH && g.ox0 + lane < k.OW), od);
+        vert(r, fy);
       }
     } else {
       for (int r = 0; r < g.th; r++, od += k.dstride) {
@@ -613,14 +659,17 @@ ALB_D void r_tile_compute(const RImg& k, const RTile& g, int lane, int32_t vcol,
         const int32_t iy = (rq >> 5) - g.by0, fy = rq & 31;
         if (iy != ia) {                              // warp-uniform
           if (iy == ia + 1) {
-            ha[0] = hb[0]; ha[1] = hb[1]; ha[2] = hb[2];
+#pragma unroll
+            for (int c = 0; c < NC; c++)
+#pragma unroll
+              for (int j = 0; j < 3; j++) ha[c][j] = hb[c][j];
           } else {
             hrow(iy, ha);
           }
           hrow(imin(iy + 1, last), hb);
           ia = iy;
         }
-        r_vert_store(ha, hb, (uint32_t)(32 + 255 * fy), store && ALB_IN(g.oy0 + r < k.OH && g.ox0 + lane < k.OW), od);
+        vert(r, fy);
       }
     }
   } else {
@@ -628,19 +677,28 @@ ALB_D void r_tile_compute(const RImg& k, const RTile& g, int lane, int32_t vcol,
     // the pair (sx0, sx0 + 1) as aligned words (every word read holds a byte
     // of the pair); at the clamped last column (sx1 == sx0, weight fx = 0)
     // byte by byte
-    const int32_t sx0 = k.wx0 + (vcol >> 5), sx1 = k.wx0 + imin((vcol >> 5) + 1, k.cw - 1);
-    auto hrow = [&](int32_t sy, uint32_t (&h)[3]) {
+    int32_t sx0[NC], sx1[NC];
+#pragma unroll
+    for (int c = 0; c < NC; c++) {
+      sx0[c] = k.wx0 + (vcol[c] >> 5);
+      sx1[c] = k.wx0 + imin((vcol[c] >> 5) + 1, k.cw - 1);
+    }
+    auto hrow = [&](int32_t sy, uint32_t (&h)[NC][3]) {
       const uint8_t* row = k.src + (int64_t)sy * k.sstride;
-      uint32_t lo = 0u, hi = 0u;
-      if (!ALB_IN(sy >= k.wy0 && sy < k.wy0 + k.ch && sx0 >= k.wx0 && sx1 < k.wx0 + k.cw && sx1 >= sx0)) {
-      } else if (sx1 == sx0 + 1) {
-        ldg_pair(row + 3 * sx0, lo, hi);
-      } else {
-        lo = (uint32_t)row[3 * sx0] | ((uint32_t)row[3 * sx0 + 1] << 8) | ((uint32_t)row[3 * sx0 + 2] << 16) |
-             ((uint32_t)row[3 * sx1] << 24);
-        hi = (uint32_t)row[3 * sx1 + 1] | ((uint32_t)row[3 * sx1 + 2] << 8);
+#pragma unroll
+      for (int c = 0; c < NC; c++) {
+        uint32_t lo = 0u, hi = 0u;
+        if (!ALB_IN(sy >= k.wy0 && sy < k.wy0 + k.ch && sx0[c] >= k.wx0 && sx1[c] < k.wx0 + k.cw &&
+                    sx1[c] >= sx0[c])) {
+        } else if (sx1[c] == sx0[c] + 1) {
+          ldg_pair(row + 3 * sx0[c], lo, hi);
+        } else {
+          lo = (uint32_t)row[3 * sx0[c]] | ((uint32_t)row[3 * sx0[c] + 1] << 8) |
+               ((uint32_t)row[3 * sx0[c] + 2] << 16) | ((uint32_t)row[3 * sx1[c]] << 24);
+          hi = (uint32_t)row[3 * sx1[c] + 1] | ((uint32_t)row[3 * sx1[c] + 2] << 8);
+        }
+        r_hrow(lo, hi, wx[c], h[c]);
       }
-      r_hrow(lo, hi, wx, h);
     };
     for (int r = 0; r < g.th; r++, od += k.dstride) {
       const int32_t rq = __shfl_sync(0xffffffffu, vrow, r);
@@ -650,7 +708,7 @@ ALB_D void r_tile_compute(const RImg& k, const RTile& g, int lane, int32_t vcol,
         hrow(k.wy0 + imin(iy + 1, k.ch - 1), hb);
         ia = iy;
       }
-      r_vert_store(ha, hb, (uint32_t)(32 + 255 * fy), store && ALB_IN(g.oy0 + r < k.OH && g.ox0 + lane < k.OW), od);
+      vert(r, fy);
     }
   }
 }
@@ -679,7 +737,7 @@ __global__ void __launch_bounds__(32 * RWARP) k_resize_rows(Plan plan, ImgList i
       r_load_img<MAP>(plan, in, out, prm, b, k);
     }
     RTile g;
-    int32_t ccol, crow;
+    int32_t ccol[RShape<S>::NC], crow;
     r_tile_geo<MAP, S>(k, prm, item, lane, g, ccol, crow);
     __syncwarp();
     r_tile_stage<S>(k, g, lane, sm.box[w], sm.rowoff[w]);
@@ -1117,20 +1175,11 @@ alb_status launch_tile_geometric(int32_t tid, const Plan& plan, const ImgList& i
   int32_t* prefix = const_cast<int32_t*>(plan.prefix);
   int32_t* tiles_x = const_cast<int32_t*>(plan.rows_per_item);
   if ((resize || grid) && !mask) {
-    // resizes with a second plan: reductions beyond 17/16 on an axis that fit
-    // the 68 x 36 box (32 x 16 tiles) through it, the rest through the 36 x 36 box
+    // resizes with a second plan: three classes by the window's scale, each
+    // through its own tile shape (see k_plan_tiles); the first plan's arrays
+    // are rebuilt for the third class once the first class's kernel has read
+    // them (stream order)
     const bool split = resize && plan.prefix2 && plan.rows2;
-    PlanCheck c0 = chk;
-    c0.reduce = split ? -1 : 0;
-    if (grid) {
-      // grid distortion: cell factors up to ~1.9 stretch many tiles' footprints
-      // past the small box, so every image takes the 68 x 36 box
-      k_plan_tiles<<<1, 1024, 0, st>>>(out, plan.n, RShape<1>::TW, RShape<1>::TH, prefix, tiles_x, c0);
-      ALB_CUDA(cudaGetLastError());
-    } else {
-      k_plan_tiles<<<1, 1024, 0, st>>>(out, plan.n, RShape<0>::TW, RShape<0>::TH, prefix, tiles_x, c0);
-      ALB_CUDA(cudaGetLastError());
-    }
     auto run = [&](auto kern, int smem, const Plan& pl) -> alb_status {
       ALB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
       int per_sm = 0;
@@ -1139,13 +1188,32 @@ alb_status launch_tile_geometric(int32_t tid, const Plan& plan, const ImgList& i
       ALB_CUDA(cudaGetLastError());
       return ALB_OK;
     };
-    if (grid) return run(k_resize_rows<MAP_GRID, 1>, (int)sizeof(RShared<1>), plan);
-    alb_status rc = run(k_resize_rows<MAP_RESIZE, 0>, (int)sizeof(RShared<0>), plan);
-    if (rc != ALB_OK || !split) return rc;
-    PlanCheck c1 = chk;
-    c1.reduce = 1;
-    k_plan_tiles<<<1, 1024, 0, st>>>(out, plan.n, RShape<1>::TW, RShape<1>::TH, plan.prefix2, plan.rows2, c1);
-    ALB_CUDA(cudaGetLastError());
+    auto tiles = [&](int tw, int th, int32_t* pf, int32_t* tx, int32_t cls) -> alb_status {
+      PlanCheck c = chk;
+      c.reduce = cls;
+      k_plan_tiles<<<1, 1024, 0, st>>>(out, plan.n, tw, th, pf, tx, c);
+      ALB_CUDA(cudaGetLastError());
+      return ALB_OK;
+    };
+    alb_status rc;
+    if (grid) {
+      // grid distortion: cell factors up to ~1.9 stretch many tiles' footprints
+      // past the small box, so every image takes the 68 x 36 box
+      rc = tiles(RShape<1>::TW, RShape<1>::TH, prefix, tiles_x, 0);
+      if (rc != ALB_OK) return rc;
+      return run(k_resize_rows<MAP_GRID, 1>, (int)sizeof(RShared<1>), plan);
+    }
+    if (!split) {
+      rc = tiles(RShape<2>::TW, RShape<2>::TH, prefix, tiles_x, 0);
+      if (rc != ALB_OK) return rc;
+      return run(k_resize_rows<MAP_RESIZE, 2>, (int)sizeof(RShared<2>), plan);
+    }
+    rc = tiles(RShape<0>::TW, RShape<0>::TH, prefix, tiles_x, 2);
+    if (rc == ALB_OK) rc = run(k_resize_rows<MAP_RESIZE, 0>, (int)sizeof(RShared<0>), plan);
+    if (rc == ALB_OK) rc = tiles(RShape<2>::TW, RShape<2>::TH, prefix, tiles_x, 3);
+    if (rc == ALB_OK) rc = run(k_resize_rows<MAP_RESIZE, 2>, (int)sizeof(RShared<2>), plan);
+    if (rc == ALB_OK) rc = tiles(RShape<1>::TW, RShape<1>::TH, plan.prefix2, plan.rows2, 1);
+    if (rc != ALB_OK) return rc;
     const Plan p2{plan.prefix2, plan.rows2, plan.n};
     return run(k_resize_rows<MAP_RESIZE, 1>, (int)sizeof(RShared<1>), p2);
   }
