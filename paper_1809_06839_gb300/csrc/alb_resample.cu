@@ -484,7 +484,6 @@ constexpr int RWARP = 4;              // warps per CTA
 struct RImg {          // per-image values of a warp's current image (warp-uniform)
   int32_t b, prefix, ntiles, tiles_x;
   int32_t OH, OW, cw, ch, wx0, wy0;
-  int32_t steps1;      // the tap rows advance by at most one source row per output row
   const uint8_t* src;
   uint8_t* dst;
   int64_t sstride, dstride;
@@ -501,9 +500,9 @@ ALB_D void r_load_img(const Plan& plan, const ImgList& in, const ImgList& out, c
   k.b = b; k.prefix = plan.prefix[b]; k.ntiles = plan.prefix[b + 1] - k.prefix; k.tiles_x = plan.rows_per_item[b];
   k.OH = so.h; k.OW = so.w;
   if (MAP == MAP_GRID) {
-    k.cw = si.w; k.ch = si.h; k.wx0 = 0; k.wy0 = 0; k.steps1 = 0;
+    k.cw = si.w; k.ch = si.h; k.wx0 = 0; k.wy0 = 0;
   } else {
-    k.cw = p.cw; k.ch = p.ch; k.wx0 = p.x0; k.wy0 = p.y0; k.steps1 = p.ch <= so.h;
+    k.cw = p.cw; k.ch = p.ch; k.wx0 = p.x0; k.wy0 = p.y0;
   }
   k.src = (const uint8_t*)si.data; k.dst = (uint8_t*)so.data;
   k.sstride = si.row_stride; k.dstride = so.row_stride;
@@ -627,50 +626,24 @@ ALB_D void r_tile_compute(const RImg& k, const RTile& g, int lane, const int32_t
     // at a clamped bottom edge the row below the last tap row is not staged
     // and has weight fy = 0: the last staged row stands in for it
     const int32_t last = g.bh - 1;
-    if (k.steps1) {
-      // enlargement: the top tap row advances by 0 or 1 per output row, so
-      // one new h row per output row, selected without branches
-      {
-        const int32_t rq = __shfl_sync(0xffffffffu, vrow, 0);
-        ia = (rq >> 5) - g.by0;
-        hrow(ia, ha);
-        hrow(imin(ia + 1, last), hb);
-      }
-#pragma unroll 2
-      for (int r = 0; r < g.th; r++, od += k.dstride) {
-        const int32_t rq = __shfl_sync(0xffffffffu, vrow, r);
-        const int32_t iy = (rq >> 5) - g.by0, fy = rq & 31;
-        uint32_t hn[NC][3];
-        hrow(imin(iy + 1, last), hn);
-        const bool adv = iy != ia;
+    // the tap rows advance warp-uniformly: a row of h is computed only when
+    // the top tap row moves (enlargements reuse it for the next output rows)
+    for (int r = 0; r < g.th; r++, od += k.dstride) {
+      const int32_t rq = __shfl_sync(0xffffffffu, vrow, r);
+      const int32_t iy = (rq >> 5) - g.by0, fy = rq & 31;
+      if (iy != ia) {                              // warp-uniform
+        if (iy == ia + 1) {
 #pragma unroll
-        for (int c = 0; c < NC; c++)
+          for (int c = 0; c < NC; c++)
 #pragma unroll
-          for (int j = 0; j < 3; j++) {
-            ha[c][j] = adv ? hb[c][j] : ha[c][j];
-            hb[c][j] = hn[c][j];
-          }
-        ia = iy;
-        vert(r, fy);
-      }
-    } else {
-      for (int r = 0; r < g.th; r++, od += k.dstride) {
-        const int32_t rq = __shfl_sync(0xffffffffu, vrow, r);
-        const int32_t iy = (rq >> 5) - g.by0, fy = rq & 31;
-        if (iy != ia) {                              // warp-uniform
-          if (iy == ia + 1) {
-#pragma unroll
-            for (int c = 0; c < NC; c++)
-#pragma unroll
-              for (int j = 0; j < 3; j++) ha[c][j] = hb[c][j];
-          } else {
-            hrow(iy, ha);
-          }
-          hrow(imin(iy + 1, last), hb);
-          ia = iy;
+            for (int j = 0; j < 3; j++) ha[c][j] = hb[c][j];
+        } else {
+          hrow(iy, ha);
         }
-        vert(r, fy);
+        hrow(imin(iy + 1, last), hb);
+        ia = iy;
       }
+      vert(r, fy);
     }
   } else {
     // footprint larger than the box: taps straight from the source window,
