@@ -453,19 +453,24 @@ __global__ void __launch_bounds__(32 * NWARP, 5) k_resample_warp(Plan plan, ImgL
 // separability of the Q5 weights: out = ((32 - fy) h(iy) + fy h(iy + 1) + 512)
 // >> 10 with h(i) = (32 - fx) p(i, ix) + fx p(i, ix + 1) exact in integers, so
 // h of a source row is computed once per output column and reused by every
-// output row whose tap rows include it.  A warp owns a 32 x 32 output tile,
-// lane j = output column j; it walks the tile's rows top to bottom keeping the
-// two current tap rows' h in registers (for an enlargement most output rows
-// reuse both, or shift by one source row).  The tile's source box (up to
-// BX x BY pixels of its shape) is staged per warp in shared memory by
-// cp.async, one buffer per warp (the per-tile image and geometry stay in
-// registers).  Measured trade-off: a taller
-// tile amortises the per-tile geometry, a larger box costs warps per SM (the
-// row chain is latency-bound); 32 x 32 with a 36 x 36 box beat 32 x 16 with
-// 36 x 20 and 32 x 32 with 36 x 28.  Larger footprints read global memory.
-// Two tile shapes: S = 0, 32 x 32 output tiles with a 36 x 36 box
-// (enlargements and reductions to ~0.95); S = 1, 32 x 16 tiles with a 68 x 36
-// box (reductions by up to ~2, routed there per image).
+// output row whose tap rows include it.  A warp owns an output tile, lane j =
+// output column j (and j + 32 in the 64-wide shape); it walks the tile's rows
+// top to bottom keeping the two current tap rows' h in registers and computes
+// a new row of h only when the warp-uniform top tap row moves (for an
+// enlargement most output rows reuse both, or shift by one source row).  The
+// tile's source box (up to BX x BY pixels of its shape) is staged per warp in
+// shared memory by cp.async, one buffer per warp (the per-tile image and
+// geometry stay in registers).  Measured trade-off: a taller tile amortises
+// the per-tile geometry, a larger box costs warps per SM (the row chain is
+// latency-bound); with one column per lane 32 x 32 with a 36 x 36 box beat
+// 32 x 16 with 36 x 20 and 32 x 32 with 36 x 28; two columns per lane (the
+// row's coordinate, box row offset and advance test shared) beat one.
+// Larger footprints read global memory.  Three tile shapes, one per scale
+// class of the window (routed per image by the tile plans): S = 0, 64 x 32
+// tiles with a 72 x 36 box, two columns per lane (windows within 17/16 of the
+// output on both axes); S = 1, 32 x 16 tiles with a 68 x 36 box (reductions
+// past 17/16 up to ~2); S = 2, 32 x 32 tiles with a 36 x 36 box (stronger
+// reductions, whose tiles read global memory at the highest residency).
 template <int S>
 struct RShape {
   // S = 0: windows within 17/16 of the output; 1: reductions up to ~2x;
