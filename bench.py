@@ -42,7 +42,7 @@ UNIT = "images/s"
 # suite workload (same H, W distribution), scaled per image; the roofline's
 # traffic figure is this times the images of one launch.  Only kernels whose
 # code is unchanged since that capture are listed.
-NCU_DRAM_BYTES_PER_IMAGE = {"Rotate": 1048317.0, "PadToSize512": 1172000.0}
+NCU_DRAM_BYTES_PER_IMAGE = {"Rotate": 1048317.0, "ShiftHSV": 849437.0, "PadToSize512": 1172000.0}
 SUITE_N, SUITE_LO, SUITE_HI = 2000, 333, 500
 FUSED_N, FUSED_LO, FUSED_HI = 4096, 256, 1024
 DET_N, DET_HW = 256, 1024
