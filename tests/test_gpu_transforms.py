@@ -38,8 +38,8 @@ def dev():
     return torch.device("cuda")
 
 
-def run_ragged(name, sizes, seed, dev, with_mask=True, with_boxes=True):
-    oc = ALL[name]
+def run_ragged(name, sizes, seed, dev, with_mask=True, with_boxes=True, oc=None):
+    oc = oc if oc is not None else ALL[name]
     rb = synth.ragged_noise(sizes, seed=seed)
     masks = synth.ragged_masks(sizes, seed=seed)
     ops = [O.sample_params(oc, seed, oc.tid, i, h, w) for i, (h, w) in enumerate(sizes)]
@@ -96,6 +96,27 @@ def test_ragged_transform_matches_oracle(dev, name):
             continue
         bref = O.apply_boxes(ops[i], h, w, boxes[i, :nb[i]])
         assert nbo[i] == len(bref), (name, "boxes", i)
+        assert np.abs(bo[i, :nbo[i]] - bref).max(initial=0) <= 1e-4
+
+
+def test_resize_scale_classes_in_one_batch(dev):
+    """One ragged Resize batch whose images fall in the three scale classes
+    that the tile plans route apart -- windows within 17/16 of the output
+    (enlargements and mild reductions), reductions up to about 2x, and
+    stronger ones (on either axis) -- each through its own tile shape, checked
+    against the oracle bit for bit with masks and boxes."""
+    oc = O.make_cfg(O.RESIZE, out_h=200, out_w=160)
+    sizes = [(150, 120), (210, 168), (200, 160), (1, 1), (380, 300), (250, 170), (1000, 150), (120, 700),
+             (700, 20), (433, 351)]
+    rb, masks, ops, dout, dmo, boxes, nb, bo, nbo = run_ragged("Resize200x160", sizes, 7, dev, oc=oc)
+    for i, (h, w) in enumerate(sizes):
+        ref = O.apply_image(ops[i], rb.image(i).numpy())
+        got = dout.rb.image(i).cpu().numpy()
+        assert got.shape == ref.shape == (200, 160, 3)
+        assert np.array_equal(got, ref), (sizes[i], (got != ref).sum())
+        assert np.array_equal(dmo.rb.image(i).cpu().numpy(), O.apply_mask(ops[i], masks.image(i).numpy())), sizes[i]
+        bref = O.apply_boxes(ops[i], h, w, boxes[i, :nb[i]])
+        assert nbo[i] == len(bref), sizes[i]
         assert np.abs(bo[i, :nbo[i]] - bref).max(initial=0) <= 1e-4
 
 
