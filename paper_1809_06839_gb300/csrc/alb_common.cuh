@@ -237,8 +237,8 @@ struct PlanCheck {
   PrmList prm;
   int32_t* status;
   int32_t filter_c;   // 0: all images; k > 0: only images with c == k; k < 0: only c != -k (others: no items, no error)
-  int32_t reduce = 0; // resizes: 0 all images; else only one scale class: 2 windows within 17/16 of the
-                      // output, 1 reductions past 17/16 that fit the 68 x 36 box, 3 the stronger ones
+  int32_t reduce = 0; // resizes: 0 all images; else only one scale class: 2 windows no larger than the
+                      // output, 1 reductions that fit the 68 x 36 box, 3 the stronger ones
 };
 
 ALB_D bool plan_filtered_out(const PlanCheck& chk, const alb_image& im) {
