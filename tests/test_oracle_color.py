@@ -135,6 +135,63 @@ def test_shift_hsv_matches_colorsys(shift):
     assert bad <= 3
 
 
+def _hsv_shift_exact(shift, r, g, b):
+    """The hexcone shift of one pixel in exact rationals (Smith's hexcone; hue
+    shifted by 2 * shift[0] degrees, saturation and value by shift / 255,
+    both clamped to [0, 1]); returns the three unrounded channel values."""
+    F = Fraction
+    mx, mn = max(r, g, b), min(r, g, b)
+    chroma = mx - mn
+    hue = F(0)
+    if chroma > 0:
+        if mx == r:
+            hue = 60 * F(g - b, chroma)
+        elif mx == g:
+            hue = 60 * (F(b - r, chroma) + 2)
+        else:
+            hue = 60 * (F(r - g, chroma) + 4)
+        if hue < 0:
+            hue += 360
+    sat = F(chroma, mx) if mx > 0 else F(0)
+    val = F(mx, 255)
+    h2 = (hue + 2 * F(shift[0])) % 360
+    s2 = min(F(1), max(F(0), sat + F(shift[1]) / 255))
+    v2 = min(F(1), max(F(0), val + F(shift[2]) / 255))
+    c2 = v2 * s2
+    hp = h2 / 60
+    sector = int(hp)                       # hp >= 0
+    fr = hp - 2 * (hp // 2)
+    x = c2 * (1 - abs(fr - 1))
+    m = v2 - c2
+    rgb1 = [(c2, x, 0), (x, c2, 0), (0, c2, x), (0, x, c2), (x, 0, c2), (c2, 0, x)][min(sector, 5)]
+    return [255 * (c + m) for c in rgb1]
+
+
+@pytest.mark.parametrize("shift", [(10.0, 0.0, 0.0), (-20.0, 25.0, -15.0), (7.5, -30.0, 20.0), (-90.0, 60.0, 0.0),
+                                   (33.3, -255.0, 40.0)])
+def test_shift_hsv_matches_exact_rationals(shift):
+    """Every pixel equals the exact rational result rounded to nearest (ties to
+    even) and saturated, except where that exact value lies within 1e-9 of a
+    half-integer: there the float64 oracle may round either way."""
+    rng = np.random.default_rng(11)
+    px = np.concatenate([lattice16().reshape(-1, 3), rng.integers(0, 256, (6000, 3))]).astype(np.uint8)
+    n = (len(px) // 100) * 100
+    px = px[:n]
+    got = O.apply_image(P(O.SHIFT_HSV, shift=shift), px.reshape(-1, 100, 3)).reshape(-1, 3)
+    ties = 0
+    for i, (r, g, b) in enumerate(px.tolist()):
+        for c, e in enumerate(_hsv_shift_exact(shift, r, g, b)):
+            lo = int(e)                            # e >= 0
+            near_tie = abs(e - lo - Fraction(1, 2)) < Fraction(1, 10 ** 9)
+            ref = min(255, max(0, round(e)))       # Fraction.__round__: ties to even
+            if near_tie:
+                ties += 1
+                assert int(got[i, c]) in (min(255, lo), min(255, lo + 1)), (shift, (r, g, b), c)
+            else:
+                assert int(got[i, c]) == ref, (shift, (r, g, b), c, float(e))
+    assert ties <= 3 * len(px) // 100             # exact half-integers: under 1 % of the channel values
+
+
 def test_equalize_uniform_histogram_is_identity():
     hist = np.full(256, 7, dtype=np.uint64)
     assert np.array_equal(O.equalize_lut(hist), V.astype(np.uint8))
