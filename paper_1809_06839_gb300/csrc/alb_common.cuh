@@ -238,7 +238,7 @@ struct PlanCheck {
   int32_t* status;
   int32_t filter_c;   // 0: all images; k > 0: only images with c == k; k < 0: only c != -k (others: no items, no error)
   int32_t reduce = 0; // resizes: 0 all images; else only one scale class: 2 windows no larger than the
-                      // output, 1 reductions that fit the 68 x 36 box, 3 the stronger ones
+                      // output, 1 reductions that fit the 66 x 34 box of 32 x 16 tiles, 3 the stronger ones
 };
 
 ALB_D bool plan_filtered_out(const PlanCheck& chk, const alb_image& im) {

@@ -59,11 +59,11 @@ __global__ void k_plan_tiles(ImgList out, int32_t n, int32_t tile_w, int32_t til
         const alb_params& pr = chk.prm.get(i);
         // class 2: windows no larger than the output on either axis (64 x 32
         // tiles fit the 66 x 34 box: 63 f + 2 <= 65 columns, 31 f + 2 <= 33 rows);
-        // class 1: reductions whose 32 x 16 tiles fit the 68 x 36 box (31 f + 2
-        // <= 67 columns, 15 f + 2 <= 35 rows); class 3: stronger reductions,
+        // class 1: reductions whose 32 x 16 tiles fit the 66 x 34 box (31 f + 3
+        // <= 66 columns, 15 f + 3 <= 34 rows); class 3: stronger reductions,
         // whose 32 x 32 tiles read global memory
         const bool past = pr.cw > im.w || pr.ch > im.h;
-        const bool fits = 100 * (int64_t)pr.cw <= 209 * (int64_t)im.w && 10 * (int64_t)pr.ch <= 22 * (int64_t)im.h;
+        const bool fits = 1000 * (int64_t)pr.cw <= 2032 * (int64_t)im.w && 1000 * (int64_t)pr.ch <= 2066 * (int64_t)im.h;
         const int32_t cls = !past ? 2 : (fits ? 1 : 3);
         if (cls != chk.reduce) cnt = 0;
       }
@@ -469,7 +469,7 @@ __global__ void __launch_bounds__(32 * NWARP, 5) k_resample_warp(Plan plan, ImgL
 // class of the window (routed per image by the tile plans): S = 0, 64 x 32
 // tiles with a 66 x 34 box, two columns per lane (windows no larger than the
 // output on either axis; the small box keeps 7 CTAs per SM); S = 1, 32 x 16
-// tiles with a 68 x 36 box (reductions up to ~2); S = 2, 32 x 32 tiles with a
+// tiles with a 66 x 34 box (reductions up to ~2); S = 2, 32 x 32 tiles with a
 // 36 x 36 box (stronger reductions, whose tiles read global memory at the
 // highest residency).
 template <int S>
@@ -478,8 +478,8 @@ struct RShape {
   // 2: the rest (and every image when there is no second plan)
   static constexpr int TW = S == 0 ? 64 : 32, TH = S == 1 ? 16 : 32;   // output tile (columns x rows)
   static constexpr int NC = TW / 32;                      // output columns per lane: lane, lane + 32
-  static constexpr int BX = S == 0 ? 66 : (S == 1 ? 68 : 36), BY = S == 0 ? 34 : 36;   // staged box (pixels x rows)
-  static constexpr int PITCH = S == 0 ? 224 : (S == 1 ? 240 : 144);   // staged row pitch in bytes
+  static constexpr int BX = S == 2 ? 36 : 66, BY = S == 2 ? 36 : 34;   // staged box (pixels x rows)
+  static constexpr int PITCH = S == 2 ? 144 : 224;        // staged row pitch in bytes
   static_assert(PITCH % 16 == 0, "cp.async destinations must be 16-byte aligned");
   static_assert(PITCH >= 15 + 3 * (BX - 1) + 12, "a tap read (3 words from the pair's word) stays in its row");
   static_assert(BY >= TH + 1 && BX >= TW + 2, "the box holds an unscaled tile");
@@ -1177,7 +1177,7 @@ alb_status launch_tile_geometric(int32_t tid, const Plan& plan, const ImgList& i
     alb_status rc;
     if (grid) {
       // grid distortion: cell factors up to ~1.9 stretch many tiles' footprints
-      // past the small box, so every image takes the 68 x 36 box
+      // past the small box, so every image takes the 66 x 34 box of the 32 x 16 tiles
       rc = tiles(RShape<1>::TW, RShape<1>::TH, prefix, tiles_x, 0);
       if (rc != ALB_OK) return rc;
       return run(k_resize_rows<MAP_GRID, 1>, (int)sizeof(RShared<1>), plan);
