@@ -101,14 +101,23 @@ class ClockSampler:
         self.proc = None
 
     def start(self):
+        """Start sampling every 50 ms and return once the first sample has
+        arrived (at most 3 s), so that the samples cover the timed region that
+        follows rather than nvidia-smi's own start-up."""
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except (OSError, ValueError):
             self.proc = None
+            return
+        t0 = time.time()
+        while not self.samples and time.time() - t0 < 3.0 and self.proc.poll() is None:
+            time.sleep(0.01)
+        self.first = list(self.samples)      # taken before the timed region
+        self.samples.clear()
 
     def _read(self):
         for line in self.proc.stdout:
@@ -125,6 +134,8 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.thread.join(timeout=2)
+        if not self.samples:                 # a region shorter than one interval: the sample just before it
+            self.samples = list(getattr(self, "first", []))
         sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
         mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
